@@ -1,0 +1,610 @@
+"""Plain FP64 CPU oracle of the staggered FFT scheme for gradient-regularised
+ductile damage (Magri, Lucarini, Lemoine, Adam, Segurado, "An FFT framework
+for simulating non-local ductile failure in heterogeneous materials").
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+benchmark's CPU-baseline leg may import this module.  It shares no code with
+the CUDA path: it uses numpy's full complex FFT as a library step and applies
+every operator by its definition, vectorised over voxels or Fourier modes,
+with no blocking or fusion.
+
+Field layout: numpy shape ``(N2, N1, c)`` in 2D or ``(N3, N2, N1, c)`` in 3D
+(x1 fastest), strain/stress components in Mandel notation (order 11, 22, 33,
+23, 13, 12, shears times sqrt 2), so that double contractions are plain dot
+products.  In 2D (plane strain) the mechanical fields carry the in-plane
+components 11, 22, 12 only; the local state is kept in full 3D with
+eps33 = eps13 = eps23 = 0.
+
+Readings where the paper is silent or ambiguous (each is a numbered reading
+R1..R24 of the design notes):
+  R1  Algorithm 1 loops while ERR > TOL.
+  R2  ERR uses Mandel components and the Frobenius norm of <eps>; the
+      non-local term counts 0 when ||abar|| < 1e-30; at least 2 staggered
+      iterations run.
+  R4  Newton stops when the residual ||G*(sigma - Sigma_bar)||_2 /
+      (sqrt(V) ||<sigma>||) and the last correction max|d eps| / ||<eps>||
+      are both below TOL_N.
+  R5  Willot rotated-scheme discrete derivative (voxel-corner differences).
+  R6  Small-strain Galerkin projection = orthogonal projection onto
+      compatible symmetric strains.
+  R7  Zero-frequency projector = diagonal projector on the stress-controlled
+      components.
+  R8  sqrt(2/3) in both the yield function and the eps_p rate.
+  R9  Total-form stress update sigma = (1 - D) sigma_eff.
+  R10 D = D(abar) without irreversibility, capped at D_max.
+  R11 D frozen during the mechanical Newton loop.
+  R12 <l^2> = voxel average of l_j^2(x).
+  R14 Initial guess eps_n + dE on strain-controlled components, abar_n.
+  R15 Helmholtz operator a + conj(k).F(l^2 F^-1(k a)), l^2 taken at the
+      voxel index of the corner gradient.
+  R24 No clamp on abar.
+
+Parity: every function below is pinned by the CPU tests (closed forms,
+invariants, dense brute-force solves built from real-space stencils, finite
+differences); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SQ2 = math.sqrt(2.0)
+# Mandel component -> tensor index pair
+MANDEL_PAIRS = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+MANDEL_W = np.array([1.0, 1.0, 1.0, SQ2, SQ2, SQ2])
+IDX2D = [0, 1, 5]          # carried Mandel components in plane strain
+IVEC = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+
+
+# ============================================================ tensor helpers
+def mandel_to_tensor(v):
+    """(..., 6) Mandel -> (..., 3, 3) symmetric tensor."""
+    t = np.zeros(v.shape[:-1] + (3, 3), dtype=v.dtype)
+    for m, (i, j) in enumerate(MANDEL_PAIRS):
+        val = v[..., m] / MANDEL_W[m]
+        t[..., i, j] = val
+        t[..., j, i] = val
+    return t
+
+
+def tensor_to_mandel(t):
+    """(..., 3, 3) -> (..., 6) Mandel (symmetric part)."""
+    out = np.empty(t.shape[:-2] + (6,), dtype=t.dtype)
+    for m, (i, j) in enumerate(MANDEL_PAIRS):
+        out[..., m] = 0.5 * (t[..., i, j] + t[..., j, i]) * MANDEL_W[m]
+    return out
+
+
+def carried(d):
+    """Mandel components carried by the mechanical fields (d = 2 or 3)."""
+    return list(range(6)) if d == 3 else IDX2D
+
+
+def embed(vc, d):
+    """Carried components (..., nc) -> full Mandel (..., 6)."""
+    if d == 3:
+        return vc
+    out = np.zeros(vc.shape[:-1] + (6,), dtype=vc.dtype)
+    out[..., IDX2D] = vc
+    return out
+
+
+# ============================================================ grid (Sec 3.2.1)
+class Grid:
+    """Regular N1 x N2 (x N3) voxel grid of a periodic cell L1 x L2 (x L3)
+    (Section 3.2.1).  ``n`` and ``L`` are in physical axis order."""
+
+    def __init__(self, n, L=None):
+        self.n = tuple(int(x) for x in n)
+        self.d = len(self.n)
+        self.L = tuple(float(x) for x in (L if L is not None else self.n))
+        self.h = [self.L[j] / self.n[j] for j in range(self.d)]
+        self.shape = tuple(reversed(self.n))       # numpy shape, x1 last
+        self.V = int(np.prod(self.n))
+
+    def axis(self, j):
+        """numpy axis index of physical axis j."""
+        return self.d - 1 - j
+
+    def signed_index(self, j):
+        """Signed frequency index q of each FFT mode along axis j: the set
+        n - N/2 (even N) or n - (N-1)/2 (odd N), n in [0, N-1], of Eq.
+        (frequencies), in numpy's FFT storage order."""
+        N = self.n[j]
+        return np.rint(np.fft.fftfreq(N) * N).astype(np.int64)
+
+    def xi(self, j):
+        """Continuous frequency xi_j = 2 pi q / L_j (Eq. frequencies)."""
+        return 2.0 * np.pi * self.signed_index(j) / self.L[j]
+
+    def bcast(self, v, j):
+        s = [1] * self.d
+        s[self.axis(j)] = -1
+        return v.reshape(s)
+
+
+# ========================================= discrete derivative (R5, Sec 3.2.1)
+def half_angle(grid, j):
+    """sin and cos of theta_j / 2, theta_j = 2 pi q / N_j, with the cosine
+    set to exactly zero at the Nyquist index of an even axis."""
+    N = grid.n[j]
+    q = grid.signed_index(j)
+    s = np.sin(np.pi * q / N)
+    c = np.cos(np.pi * q / N)
+    c[2 * np.abs(q) == N] = 0.0
+    return s, c
+
+
+def willot_k(grid):
+    """Modified frequencies of the rotated finite-difference scheme (R5):
+
+        k_j = (2 i / h_j) sin(theta_j/2) prod_{m != j} cos(theta_m/2)
+              * prod_m exp(i theta_m / 2)
+
+    i.e. the Fourier symbol of the derivative along x_j evaluated at the
+    voxel corner n + 1/2 as the mean of the 2^(d-1) forward differences along
+    the cube edges parallel to x_j.  Returns a list of d complex arrays of
+    the grid shape."""
+    d = grid.d
+    S = [grid.bcast(half_angle(grid, j)[0], j) for j in range(d)]
+    C = [grid.bcast(half_angle(grid, j)[1], j) for j in range(d)]
+    phase = np.ones(grid.shape, dtype=np.complex128)
+    for m in range(d):
+        phase = phase * (C[m] + 1j * S[m])
+    ks = []
+    for j in range(d):
+        mag = (2.0 / grid.h[j]) * S[j] * np.ones(grid.shape)
+        for m in range(d):
+            if m != j:
+                mag = mag * C[m]
+        ks.append(1j * mag * phase)
+    return ks
+
+
+def willot_a(grid):
+    """Real direction vector a with k = i exp(i phi) a (same R5 symbol
+    without its common phase); Gamma depends on k only through a."""
+    d = grid.d
+    S = [grid.bcast(half_angle(grid, j)[0], j) for j in range(d)]
+    C = [grid.bcast(half_angle(grid, j)[1], j) for j in range(d)]
+    out = []
+    for j in range(d):
+        mag = (2.0 / grid.h[j]) * S[j] * np.ones(grid.shape)
+        for m in range(d):
+            if m != j:
+                mag = mag * C[m]
+        out.append(mag)
+    return out
+
+
+def zero_mode_mask(grid):
+    """True at xi = 0."""
+    m = np.ones(grid.shape, dtype=bool)
+    for j in range(grid.d):
+        m &= grid.bcast(grid.signed_index(j) == 0, j)
+    return m
+
+
+# ======================================== Galerkin projection (R6, R7, Eq. 41)
+def gamma_hat_apply(tau_hat, grid, stress_mask):
+    """Apply the modified projection symbol G*(xi) to complex Mandel fields
+    tau_hat of shape grid.shape + (nc,).
+
+    xi != 0 with a != 0: orthogonal projection onto compatible strains
+        G(T) = n (x) (T n) + (T n) (x) n - (n.T.n) n (x) n,  n = a / |a|
+    (R6); hidden zeros (a = 0, xi != 0): 0; xi = 0: diagonal projector on the
+    stress-controlled components (R7).  ``stress_mask`` is a length-nc 0/1
+    vector over the carried components."""
+    d = grid.d
+    comps = carried(d)
+    a = willot_a(grid)
+    a2 = sum(x * x for x in a)
+    nz = a2 > 0.0
+    inv = np.where(nz, 1.0 / np.sqrt(np.where(nz, a2, 1.0)), 0.0)
+    nvec = np.zeros(grid.shape + (3,))
+    for j in range(d):
+        nvec[..., j] = a[j] * inv
+    T = mandel_to_tensor(embed(tau_hat, d))
+    Tn = np.einsum("...ij,...j->...i", T, nvec)
+    nTn = np.einsum("...i,...i->...", nvec, Tn)
+    G = (np.einsum("...i,...j->...ij", nvec, Tn)
+         + np.einsum("...i,...j->...ij", Tn, nvec)
+         - nTn[..., None, None] * np.einsum("...i,...j->...ij", nvec, nvec))
+    out = tensor_to_mandel(G)[..., comps]
+    out[~nz] = 0.0
+    z = zero_mode_mask(grid)
+    out[z] = tau_hat[z] * np.asarray(stress_mask, dtype=np.float64)
+    return out
+
+
+def fft_fields(f, grid):
+    axes = tuple(range(grid.d))
+    return np.fft.fftn(f, axes=axes)
+
+
+def ifft_fields(fh, grid):
+    axes = tuple(range(grid.d))
+    return np.fft.ifftn(fh, axes=axes)
+
+
+def G_apply(tau, grid, stress_mask):
+    """G*(tau) = F^-1 { G*(xi) : F(tau) } (Eq. eqdiscrete2) for a real
+    field tau of shape grid.shape + (nc,)."""
+    th = fft_fields(tau, grid)
+    return ifft_fields(gamma_hat_apply(th, grid, stress_mask), grid).real
+
+
+# ======================================== constitutive update (Sec 2.1.2, App A)
+@dataclass
+class Phase:
+    E: float
+    nu: float
+    sigma_y: float = 0.0
+    H: float = 0.0
+    law: int = 0            # 0 linear elastic, 1 J2 + Lemaitre damage
+    eps_C: float = 0.0
+    eps_R: float = 1.0
+    D_max: float = 0.0
+    var: int = -1           # non-local variable fed/read by this phase
+
+    @property
+    def K(self):
+        return self.E / (3.0 * (1.0 - 2.0 * self.nu))
+
+    @property
+    def mu(self):
+        return self.E / (2.0 * (1.0 + self.nu))
+
+
+def phases_from_dicts(ds):
+    return [Phase(**{k: d[k] for k in ("E", "nu", "sigma_y", "H", "law", "eps_C",
+                                       "eps_R", "D_max", "var")}) for d in ds]
+
+
+def damage_of(abar, ph):
+    """Linear damage law driven by the non-local equivalent plastic strain
+    (Eq. non-local_damage_lemaitre), capped at D_max (Section 4.1, R10)."""
+    if ph.law != 1:
+        return np.zeros_like(abar)
+    D = (abar - ph.eps_C) / (ph.eps_R - ph.eps_C)
+    return np.clip(D, 0.0, ph.D_max)
+
+
+def return_map(eps, epsp_n, ep_n, abar, phase, phases):
+    """Backward-Euler update of the Lemaitre model (Appendix A.2 with R8-R11)
+    at every voxel.
+
+    eps, epsp_n: (V, 6) Mandel; ep_n: (V,); abar: (J, V) non-local variables
+    held fixed; phase: (V,) int.  Returns a dict with sigma (V,6), tangent
+    C (V,6,6), epsp (V,6), ep (V,), D (V,), alpha (J,V).
+
+      sigma_eff_trial = K tr(e) I + 2 mu dev(e),  e = eps - epsp_n
+      f = ||dev sigma_eff_trial|| - sqrt(2/3) (sigma_y + H ep_n)
+      f > 0: dlambda = f / (2 mu + 2 H / 3), nhat = dev / ||dev||,
+             epsp = epsp_n + dlambda nhat, ep = ep_n + sqrt(2/3) dlambda,
+             sigma_eff = sigma_eff_trial - 2 mu dlambda nhat
+      D = clamp((abar - eps_C) / (eps_R - eps_C), 0, D_max)
+      sigma = (1 - D) sigma_eff
+      C = (1 - D) [K I(x)I + 2 mu theta P_dev - 2 mu thetabar nhat(x)nhat]
+          theta = 1 - 2 mu dlambda / q, thetabar = 1/(1 + H/(3 mu)) - (1 - theta)
+    (the consistent tangent of radial return with linear isotropic hardening).
+    """
+    Vn = eps.shape[0]
+    J = abar.shape[0]
+    sigma = np.zeros((Vn, 6))
+    C = np.zeros((Vn, 6, 6))
+    epsp = epsp_n.copy()
+    ep = ep_n.copy()
+    D = np.zeros(Vn)
+    alpha = np.zeros((J, Vn))
+    Pdev = np.eye(6) - np.outer(IVEC, IVEC) / 3.0
+    for q, ph in enumerate(phases):
+        sel = phase == q
+        if not np.any(sel):
+            continue
+        K, mu = ph.K, ph.mu
+        e = eps[sel] - epsp_n[sel]
+        tr = e[:, 0] + e[:, 1] + e[:, 2]
+        dev = e - tr[:, None] * IVEC[None, :] / 3.0
+        s_tr = 2.0 * mu * dev
+        sig_tr = K * tr[:, None] * IVEC[None, :] + s_tr
+        qn = np.sqrt(np.einsum("ij,ij->i", s_tr, s_tr))
+        theta = np.ones(qn.shape)
+        thetabar = np.zeros(qn.shape)
+        nhat = np.zeros_like(s_tr)
+        sig_eff = sig_tr
+        if ph.law == 1:
+            f = qn - math.sqrt(2.0 / 3.0) * (ph.sigma_y + ph.H * ep_n[sel])
+            pl = f > 0.0
+            dl = np.where(pl, f / (2.0 * mu + 2.0 * ph.H / 3.0), 0.0)
+            safe_q = np.where(pl, qn, 1.0)
+            nhat = np.where(pl[:, None], s_tr / safe_q[:, None], 0.0)
+            epsp[sel] = epsp_n[sel] + dl[:, None] * nhat
+            ep[sel] = ep_n[sel] + math.sqrt(2.0 / 3.0) * dl
+            sig_eff = sig_tr - 2.0 * mu * dl[:, None] * nhat
+            theta = np.where(pl, 1.0 - 2.0 * mu * dl / safe_q, 1.0)
+            thetabar = np.where(pl, 1.0 / (1.0 + ph.H / (3.0 * mu)) - (1.0 - theta), 0.0)
+            Dq = damage_of(abar[ph.var][sel], ph) if ph.var >= 0 else np.zeros(qn.shape)
+            D[sel] = Dq
+            if ph.var >= 0:
+                alpha[ph.var, sel] = ep[sel]
+        Dq = D[sel]
+        sigma[sel] = (1.0 - Dq)[:, None] * sig_eff
+        Cq = (K * np.outer(IVEC, IVEC)[None] + 2.0 * mu * theta[:, None, None] * Pdev[None]
+              - 2.0 * mu * thetabar[:, None, None] * np.einsum("vi,vj->vij", nhat, nhat))
+        C[sel] = (1.0 - Dq)[:, None, None] * Cq
+    return dict(sigma=sigma, C=C, epsp=epsp, ep=ep, D=D, alpha=alpha)
+
+
+# ============================================================ Krylov solvers
+def cg(A, b, rtol, maxit, dot=None):
+    """Textbook conjugate gradients from x0 = 0; stops when ||r|| <=
+    rtol ||b|| (the criterion of Algorithm 2).  Returns (x, iterations)."""
+    if dot is None:
+        def dot(u, v):
+            return float(np.sum(u * v))
+    x = np.zeros_like(b)
+    bn = math.sqrt(dot(b, b))
+    if bn == 0.0:
+        return x, 0
+    r = b.copy()
+    p = r.copy()
+    rr = dot(r, r)
+    it = 0
+    while it < maxit:
+        Ap = A(p)
+        alpha = rr / dot(p, Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        it += 1
+        rr_new = dot(r, r)
+        if math.sqrt(rr_new) <= rtol * bn:
+            break
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, it
+
+
+def pcg(A, M, b, rtol, maxit):
+    """Preconditioned conjugate gradients on complex vectors with the
+    Hermitian inner product (ConjGrad of Algorithm 2), x0 = 0, stop when
+    ||A x - b|| <= rtol ||b|| (recursive residual)."""
+    def dot(u, v):
+        return complex(np.vdot(u, v)).real
+    x = np.zeros_like(b)
+    bn = math.sqrt(dot(b, b))
+    if bn == 0.0:
+        return x, 0
+    r = b.copy()
+    z = M(r)
+    p = z.copy()
+    rz = dot(r, z)
+    it = 0
+    while it < maxit:
+        Ap = A(p)
+        alpha = rz / dot(p, Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        it += 1
+        if math.sqrt(dot(r, r)) <= rtol * bn:
+            break
+        z = M(r)
+        rz_new = dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it
+
+
+# ============================================== Helmholtz (Sec 3.2.3, Alg. 2)
+def helmholtz_apply_hat(a_hat, ell2, grid, ks=None):
+    """GC of Algorithm 2 with the discrete derivative (R15):
+        L(a) = a + sum_j conj(k_j) F( l^2(x) F^-1(k_j a) )."""
+    if ks is None:
+        ks = willot_k(grid)
+    out = a_hat.copy()
+    for j in range(grid.d):
+        g = ifft_fields(ks[j] * a_hat, grid).real
+        out = out + np.conj(ks[j]) * fft_fields(ell2 * g, grid)
+    return out
+
+
+def helmholtz_precond(grid, ell2_mean, ks=None):
+    """M of Algorithm 2 / Eq. (preconditioner): 1 / (1 + <l^2> |k|^2), with
+    the discrete |k|^2 so that M is the exact inverse for uniform l."""
+    if ks is None:
+        ks = willot_k(grid)
+    k2 = sum(np.abs(k) ** 2 for k in ks)
+    return 1.0 / (1.0 + ell2_mean * k2)
+
+
+def helmholtz_solve(alpha, ell2, grid, rtol, maxit):
+    """Algorithm 2: b = F(alpha); x = ConjGrad(GC, M, b, TOL); abar = F^-1 x.
+    ``alpha`` and ``ell2`` are real fields of the grid shape.  Returns
+    (abar, iterations)."""
+    ks = willot_k(grid)
+    b = fft_fields(alpha, grid)
+    m = helmholtz_precond(grid, float(np.mean(ell2)), ks)
+    xh, it = pcg(lambda v: helmholtz_apply_hat(v, ell2, grid, ks), lambda v: m * v,
+                 b, rtol, maxit)
+    return ifft_fields(xh, grid).real, it
+
+
+# ========================================= mechanics (Sec 3.2.2, Eq. lin_stress)
+@dataclass
+class Options:
+    tol_stag: float = 1e-6
+    tol_newton: float = 1e-6
+    cg_rtol: float = 1e-8
+    pcg_rtol: float = 1e-8
+    max_stag: int = 50
+    max_newton: int = 30
+    max_cg: int = 2000
+    max_pcg: int = 2000
+    min_stag: int = 2
+
+
+PARITY_OPTIONS = Options(tol_stag=1e-11, tol_newton=1e-12, cg_rtol=1e-13, pcg_rtol=1e-13)
+
+
+def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_bar_c, opt):
+    """Newton-Raphson on the Galerkin residual at fixed abar (step (i) of
+    Algorithm 1, Eq. lin_stress and the CG solve after it):
+
+        CG:  G*(C_T : d eps) = -G*(sigma - Sigma_bar),   eps <- eps + d eps
+
+    eps_c holds the carried components; returns the updated strain, the
+    last return-map output and iteration counts."""
+    d = grid.d
+    comps = carried(d)
+    sh = grid.shape
+    Vn = grid.V
+    eps_c = eps_c.copy()
+    newton = 0
+    cg_total = 0
+    de_rel = None
+    while True:
+        rm = return_map(embed(eps_c, d).reshape(Vn, 6), epsp_n, ep_n, abar, phase, phases)
+        sig_c = rm["sigma"][:, comps].reshape(sh + (len(comps),))
+        Cc = rm["C"][:, comps][:, :, comps].reshape(sh + (len(comps), len(comps)))
+        res = -G_apply(sig_c - sig_bar_c, grid, stress_mask)
+        smean = np.linalg.norm(sig_c.reshape(-1, len(comps)).mean(axis=0))
+        res_rel = np.linalg.norm(res) / (math.sqrt(Vn) * max(smean, 1e-300))
+        if res_rel < opt.tol_newton and (de_rel is None or de_rel < opt.tol_newton):
+            break
+        if newton >= opt.max_newton:
+            raise RuntimeError("Newton did not converge")
+        dx, it = cg(lambda x: G_apply(np.einsum("...ij,...j->...i", Cc, x), grid, stress_mask),
+                    res, opt.cg_rtol, opt.max_cg)
+        eps_c = eps_c + dx
+        cg_total += it
+        newton += 1
+        emean = np.linalg.norm(eps_c.reshape(-1, len(comps)).mean(axis=0))
+        de_rel = float(np.max(np.abs(dx))) / max(emean, 1e-300)
+    return eps_c, rm, newton, cg_total
+
+
+# ========================================================= staggered (Alg. 1)
+@dataclass
+class State:
+    grid: Grid
+    phase: np.ndarray           # (V,) int
+    phases: list
+    ell: np.ndarray             # (J, n_phases)
+    eps: np.ndarray             # (V, nc) carried Mandel
+    epsp: np.ndarray            # (V, 6)
+    ep: np.ndarray              # (V,)
+    abar: np.ndarray            # (J, V)
+    sigma: np.ndarray           # (V, 6)
+    D: np.ndarray               # (V,)
+    n_done: int = 0
+    curve: list = field(default_factory=list)
+
+
+def make_state(grid, phase_map, phases, ell):
+    Vn = grid.V
+    nc = len(carried(grid.d))
+    J = np.asarray(ell).shape[0]
+    return State(grid, np.asarray(phase_map).reshape(Vn).astype(np.int64), phases,
+                 np.asarray(ell, dtype=np.float64), np.zeros((Vn, nc)), np.zeros((Vn, 6)),
+                 np.zeros(Vn), np.zeros((J, Vn)), np.zeros((Vn, 6)), np.zeros(Vn))
+
+
+def to_mandel_target(t6):
+    """Tensor-shear component vector (11,22,33,23,13,12) -> Mandel."""
+    return np.asarray(t6, dtype=np.float64) * MANDEL_W
+
+
+def ell2_field(st, j):
+    return (st.ell[j][st.phase] ** 2).reshape(st.grid.shape)
+
+
+def step_increment(st, strain_ctrl, target_prev, target, opt):
+    """One load increment n -> n+1 of Algorithm 1 (iterated staggered scheme).
+
+    strain_ctrl: 6-vector, 1 where E_hk is prescribed, 0 where Sigma_HK is;
+    target_prev / target: tensor-shear 6-vectors of increment n and n+1."""
+    g = st.grid
+    d = g.d
+    comps = carried(d)
+    nc = len(comps)
+    sh = g.shape
+    Vn = g.V
+    ctrl_c = np.asarray(strain_ctrl, dtype=np.float64)[comps]
+    stress_mask = 1.0 - ctrl_c
+    tm = to_mandel_target(target)[comps]
+    tpm = to_mandel_target(target_prev)[comps]
+    sig_bar = stress_mask * tm
+    # initial guess (R14)
+    eps_k = st.eps + ctrl_c * (tm - tpm)
+    abar_k = st.abar.copy()
+    J = st.abar.shape[0]
+    stag = 0
+    newton_tot = 0
+    cg_tot = 0
+    pcg_tot = 0
+    err = math.inf
+    while True:
+        eps_new, rm, nn, nc_it = mech_solve(g, eps_k.reshape(sh + (nc,)), st.epsp, st.ep,
+                                            abar_k, st.phase, st.phases, stress_mask,
+                                            sig_bar, opt)
+        eps_new = eps_new.reshape(Vn, nc)
+        newton_tot += nn
+        cg_tot += nc_it
+        abar_new = np.zeros_like(abar_k)
+        for j in range(J):
+            sol, it = helmholtz_solve(rm["alpha"][j].reshape(sh), ell2_field(st, j), g,
+                                      opt.pcg_rtol, opt.max_pcg)
+            abar_new[j] = sol.reshape(Vn)
+            pcg_tot += it
+        emean = np.linalg.norm(eps_new.mean(axis=0))
+        err = float(np.max(np.abs(eps_new - eps_k))) / max(emean, 1e-300)
+        for j in range(J):
+            an = np.linalg.norm(abar_new[j])
+            if an >= 1e-30:
+                err = max(err, float(np.linalg.norm(abar_new[j] - abar_k[j]) / an))
+        eps_k = eps_new
+        abar_k = abar_new
+        stag += 1
+        if stag >= opt.min_stag and err <= opt.tol_stag:
+            break
+        if stag >= opt.max_stag:
+            raise RuntimeError("staggered scheme did not converge")
+    # commit (the last mechanics solve was made at abar_k of the previous
+    # iteration; its internal variables are the increment's result)
+    st.eps = eps_k
+    st.epsp = rm["epsp"]
+    st.ep = rm["ep"]
+    st.abar = abar_k
+    st.sigma = rm["sigma"]
+    st.D = rm["D"]
+    st.n_done += 1
+    rec = dict(E=homogenized_strain(st), S=homogenized_stress(st),
+               D_mean=float(st.D.mean()), D_max=float(st.D.max()), stag=stag,
+               newton=newton_tot, cg=cg_tot, pcg=pcg_tot, err=err,
+               voxel_iterations=Vn * (cg_tot + pcg_tot))
+    st.curve.append(rec)
+    return rec
+
+
+def homogenized_stress(st):
+    """<sigma> as a tensor-shear 6-vector (order 11,22,33,23,13,12)."""
+    return st.sigma.mean(axis=0) / MANDEL_W
+
+
+def homogenized_strain(st):
+    e = embed(st.eps, st.grid.d).mean(axis=0)
+    return e / MANDEL_W
+
+
+def run_load_path(grid, phase_map, phase_dicts, ell, strain_ctrl, target, opt, n_incr=None):
+    """Algorithm 1's time loop over a load path; returns the state."""
+    st = make_state(grid, phase_map, phases_from_dicts(phase_dicts), ell)
+    tgt = np.asarray(target, dtype=np.float64)
+    n = len(tgt) if n_incr is None else n_incr
+    prev = np.zeros(6)
+    for i in range(n):
+        step_increment(st, strain_ctrl, prev, tgt[i], opt)
+        prev = tgt[i]
+    return st

@@ -1,0 +1,251 @@
+"""Seeded synthetic inputs for voxelised RVEs: phase maps, load paths,
+material sets and random fields.
+
+This module holds geometry, schedules and random numbers only; none of the
+method's arithmetic (no return map, no spectral operator, no solver) lives
+here.  Both the CPU oracle's tests and the CUDA path's tests and benchmark
+draw their inputs from it, so the two sides see identical data.
+
+Conventions
+-----------
+* A grid is given in physical axis order ``n = (N1, N2)`` (2D) or
+  ``(N1, N2, N3)`` (3D); arrays are stored C-contiguous with x1 fastest, so
+  a phase map has numpy shape ``(N2, N1)`` or ``(N3, N2, N1)``.
+* Voxel centres sit at ``x_i = (1/2 + n_i) L_i / N_i`` (Section 3.2.1,
+  "Discretization").  Lengths are in voxel units unless stated otherwise.
+* Phase 0 is the damaging elasto-plastic matrix, phase 1 the elastic
+  particles.
+* Macroscopic components are ordered 11, 22, 33, 23, 13, 12 with tensor (not
+  engineering) shears.  Stresses are in MPa.
+"""
+from __future__ import annotations
+
+import hashlib
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------- materials
+# Matrix: aluminium-like Lemaitre matrix of the paper's 3D examples
+# (Section 4.2: E_M = 70 GPa, nu_M = 0.33; damage thresholds eps_C = 0.03,
+# eps_R = 0.2, cap D = 0.99) with sigma_y = 100 MPa and H = 500 MPa.
+MATRIX = dict(E=70000.0, nu=0.33, sigma_y=100.0, H=500.0, law=1,
+              eps_C=0.03, eps_R=0.2, D_max=0.99, var=0)
+# Particle: elastic reinforcement of Section 4.2 (E_I = 400 GPa, nu_I = 0.2).
+PARTICLE = dict(E=400000.0, nu=0.2, sigma_y=0.0, H=0.0, law=0,
+                eps_C=0.0, eps_R=1.0, D_max=0.0, var=-1)
+
+# ratio between the own-phase and other-phase characteristic length
+# (Section 4.1: l_M / l_I = 50)
+ELL_CONTRAST = 50.0
+
+
+def phase_params(matrix=None, particle=None):
+    """Return the two-phase parameter list ``[matrix, particle]``."""
+    return [dict(MATRIX if matrix is None else matrix),
+            dict(PARTICLE if particle is None else particle)]
+
+
+# ------------------------------------------------------------ phase maps
+def _centres(n):
+    """Voxel-centre coordinates (voxel units) per physical axis."""
+    return [np.arange(N, dtype=np.float64) + 0.5 for N in n]
+
+
+def disc_phase_map(n, area_fraction=0.2):
+    """One centred circular particle in a 2D cell (Section 4.1 geometry).
+
+    Radius R = L sqrt(f / pi) in each axis' voxel units (square cells only).
+    A voxel is particle iff its centre lies inside the disc (periodic images
+    included; a centred disc never reaches them for f < pi/4).
+    """
+    n1, n2 = n
+    if n1 != n2:
+        raise ValueError("disc_phase_map expects a square grid")
+    R = n1 * math.sqrt(area_fraction / math.pi)
+    x1, x2 = _centres(n)
+    c = n1 / 2.0
+    d2 = (x1[None, :] - c) ** 2 + (x2[:, None] - c) ** 2
+    return (d2 < R * R).astype(np.uint8)
+
+
+def rsa_sphere_centres(n, radius, count, seed, max_rejects=1_000_000):
+    """Random sequential addition of ``count`` non-overlapping spheres.
+
+    Centres are uniform in [0, N_i) per axis, drawn from
+    ``numpy.random.default_rng(seed)``; a candidate is accepted when its
+    periodic minimum-image distance to every accepted centre is >= 2 r.
+    Raises ``RuntimeError`` after ``max_rejects`` consecutive rejections.
+    """
+    rng = np.random.default_rng(seed)
+    box = np.asarray(n, dtype=np.float64)
+    acc = np.empty((count, 3))
+    k = 0
+    rejects = 0
+    dmin2 = (2.0 * radius) ** 2
+    while k < count:
+        c = rng.random(3) * box
+        if k:
+            d = acc[:k] - c
+            d -= box * np.round(d / box)
+            if np.min(np.einsum("ij,ij->i", d, d)) < dmin2:
+                rejects += 1
+                if rejects > max_rejects:
+                    raise RuntimeError("RSA jammed: %d of %d spheres placed" % (k, count))
+                continue
+        acc[k] = c
+        k += 1
+        rejects = 0
+    return acc
+
+
+def voxelize_spheres(n, centres, radius):
+    """Phase map (uint8, shape (N3, N2, N1)) of periodic spheres.
+
+    A voxel is particle (1) iff its centre lies within ``radius`` of a sphere
+    centre under the periodic minimum image.
+    """
+    n1, n2, n3 = n
+    ph = np.zeros((n3, n2, n1), dtype=np.uint8)
+    r = float(radius)
+    span = int(math.ceil(r)) + 1
+    off = np.arange(-span, span + 1)
+    for c in centres:
+        i1 = (np.floor(c[0]).astype(int) + off) % n1
+        i2 = (np.floor(c[1]).astype(int) + off) % n2
+        i3 = (np.floor(c[2]).astype(int) + off) % n3
+        d1 = i1 + 0.5 - c[0]
+        d1 -= n1 * np.round(d1 / n1)
+        d2 = i2 + 0.5 - c[1]
+        d2 -= n2 * np.round(d2 / n2)
+        d3 = i3 + 0.5 - c[2]
+        d3 -= n3 * np.round(d3 / n3)
+        inside = (d3[:, None, None] ** 2 + d2[None, :, None] ** 2
+                  + d1[None, None, :] ** 2) < r * r
+        sub = ph[np.ix_(i3, i2, i1)]
+        ph[np.ix_(i3, i2, i1)] = np.maximum(sub, inside.astype(np.uint8))
+    return ph
+
+
+def sphere_count_for_fraction(n, radius, vf):
+    """Number of spheres of ``radius`` giving volume fraction ``vf``."""
+    V = float(np.prod(n))
+    return int(round(vf * V / (4.0 / 3.0 * math.pi * radius ** 3)))
+
+
+def sphere_radius_for_count(n, count, vf):
+    """Radius giving volume fraction ``vf`` with ``count`` spheres."""
+    V = float(np.prod(n))
+    return (3.0 * vf * V / (4.0 * math.pi * count)) ** (1.0 / 3.0)
+
+
+def laminate_phase_map(n, fractions_x1):
+    """Layers normal to x1: ``fractions_x1`` is a list of (start, stop) voxel
+    index ranges along x1 that belong to phase 1; the rest is phase 0."""
+    ph = np.zeros(tuple(reversed(n)), dtype=np.uint8)
+    for a, b in fractions_x1:
+        ph[..., a:b] = 1
+    return ph
+
+
+def phase_sha256(ph):
+    return hashlib.sha256(np.ascontiguousarray(ph).tobytes()).hexdigest()
+
+
+# ------------------------------------------------------------ load paths
+def uniaxial_path(n_incr, dE11):
+    """Uniaxial tension: E11 prescribed, the other five Sigma = 0.
+
+    Returns ``(strain_ctrl[6] uint8, target[n_incr, 6] float64)`` in the
+    component order 11, 22, 33, 23, 13, 12 (tensor shears).  In 2D the
+    out-of-plane components 33, 23, 13 are strain-controlled at zero (plane
+    strain), so the same mask works once those entries are set to 1.
+    """
+    ctrl = np.array([1, 0, 0, 0, 0, 0], dtype=np.uint8)
+    tgt = np.zeros((n_incr, 6))
+    tgt[:, 0] = dE11 * np.arange(1, n_incr + 1)
+    return ctrl, tgt
+
+
+def plane_strain_mask(ctrl):
+    c = np.array(ctrl, dtype=np.uint8).copy()
+    c[2] = c[3] = c[4] = 1
+    return c
+
+
+# ------------------------------------------------------------ random fields
+def random_strain(shape, seed, amp=2e-3, ncomp=6):
+    """Seeded random strain field (Mandel components last) around a uniaxial
+    mean, amplitude ``amp``; used for kernel-level parity cases."""
+    rng = np.random.default_rng(seed)
+    e = amp * rng.standard_normal(tuple(shape) + (ncomp,))
+    e[..., 0] += 3 * amp
+    return e
+
+
+def random_field(shape, seed, ncomp=None, scale=1.0):
+    rng = np.random.default_rng(seed)
+    s = tuple(shape) + ((ncomp,) if ncomp else ())
+    return scale * rng.standard_normal(s)
+
+
+# ------------------------------------------------------------ configs
+@dataclass
+class RVEConfig:
+    """A synthetic workload: grid, cell size, phases, lengths and load path."""
+    name: str
+    n: tuple
+    L: tuple
+    phase: np.ndarray
+    params: list
+    ell: np.ndarray            # [J][n_phases] characteristic lengths, L units
+    strain_ctrl: np.ndarray    # [6] uint8
+    target: np.ndarray         # [n_incr, 6]
+    precision: int = 0         # 0 FP64, 1 mixed FP32/FP64
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def dim(self):
+        return len(self.n)
+
+
+def _ell_table(ell_matrix, n_phases=2):
+    """Single non-local variable (matrix eps_p): l_M in the matrix and
+    l_M / 50 elsewhere (Section 4.1)."""
+    e = np.full((1, n_phases), ell_matrix / ELL_CONTRAST)
+    e[0, 0] = ell_matrix
+    return e
+
+
+def config_2d_disc(N=64, ell_vox=4.0, n_incr=50, dE=1e-3, precision=0):
+    """2D plane strain, one centred particle (area fraction 0.2), uniaxial
+    tension to n_incr * dE.  ``ell_vox`` is the matrix length in voxels."""
+    n = (N, N)
+    ph = disc_phase_map(n, 0.2)
+    ctrl, tgt = uniaxial_path(n_incr, dE)
+    ctrl = plane_strain_mask(ctrl)
+    return RVEConfig("2d_disc_%d" % N, n, (float(N), float(N)), ph,
+                     phase_params(), _ell_table(ell_vox), ctrl, tgt, precision,
+                     dict(area_fraction=0.2, sha256=phase_sha256(ph)))
+
+
+def config_mesh_objectivity(N, n_incr=50, dE=1e-3):
+    """Same cell at N x N with l = L/16 fixed in physical units."""
+    return config_2d_disc(N, ell_vox=N / 16.0, n_incr=n_incr, dE=dE)
+
+
+def config_3d_spheres(N=256, radius=10.0, vf=0.25, seed=0, ell_vox=4.0,
+                      n_incr=40, dE=1e-3, precision=1, count=None):
+    """3D RVE of random non-overlapping elastic spheres (random sequential
+    addition) in the damaging matrix; uniaxial tension under mixed control."""
+    n = (N, N, N)
+    if count is None:
+        count = sphere_count_for_fraction(n, radius, vf)
+    cen = rsa_sphere_centres(n, radius, count, seed)
+    ph = voxelize_spheres(n, cen, radius)
+    ctrl, tgt = uniaxial_path(n_incr, dE)
+    return RVEConfig("3d_spheres_%d" % N, n, (float(N),) * 3, ph, phase_params(),
+                     _ell_table(ell_vox), ctrl, tgt, precision,
+                     dict(radius=radius, count=count, seed=seed,
+                          vf_voxel=float(ph.mean()), sha256=phase_sha256(ph)))
