@@ -16,7 +16,7 @@ components 11, 22, 12 only; the local state is kept in full 3D with
 eps33 = eps13 = eps23 = 0.
 
 Readings where the paper is silent or ambiguous (each is a numbered reading
-R1..R24 of the design notes):
+R1..R25 of the design notes):
   R1  Algorithm 1 loops while ERR > TOL.
   R2  ERR uses Mandel components and the Frobenius norm of <eps>; the
       non-local term counts 0 when ||abar|| < 1e-30; at least 2 staggered
@@ -38,6 +38,9 @@ R1..R24 of the design notes):
   R15 Helmholtz operator a + conj(k).F(l^2 F^-1(k a)), l^2 taken at the
       voxel index of the corner gradient.
   R24 No clamp on abar.
+  R25 CG and PCG stop when (p, A p) <= 0: the operators are symmetric
+      positive definite in exact arithmetic, so this only happens once the
+      residual has reached the round-off floor; the current iterate is kept.
 
 Parity: every function below is pinned by the CPU tests (closed forms,
 invariants, dense brute-force solves built from real-space stencils, finite
@@ -187,7 +190,7 @@ def zero_mode_mask(grid):
     return m
 
 
-# ======================================== Galerkin projection (R6, R7, Eq. 41)
+# =========================== Galerkin projection (R6, R7, Eq. eqdiscrete2)
 def gamma_hat_apply(tau_hat, grid, stress_mask):
     """Apply the modified projection symbol G*(xi) to complex Mandel fields
     tau_hat of shape grid.shape + (nc,).
@@ -341,7 +344,8 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
 # ============================================================ Krylov solvers
 def cg(A, b, rtol, maxit, dot=None):
     """Textbook conjugate gradients from x0 = 0; stops when ||r|| <=
-    rtol ||b|| (the criterion of Algorithm 2).  Returns (x, iterations)."""
+    rtol ||b|| (the criterion of Algorithm 2) or when (p, A p) <= 0 (R25).
+    Returns (x, iterations)."""
     if dot is None:
         def dot(u, v):
             return float(np.sum(u * v))
@@ -355,7 +359,10 @@ def cg(A, b, rtol, maxit, dot=None):
     it = 0
     while it < maxit:
         Ap = A(p)
-        alpha = rr / dot(p, Ap)
+        pAp = dot(p, Ap)
+        if not pAp > 0.0:
+            break
+        alpha = rr / pAp
         x = x + alpha * p
         r = r - alpha * Ap
         it += 1
@@ -370,7 +377,7 @@ def cg(A, b, rtol, maxit, dot=None):
 def pcg(A, M, b, rtol, maxit):
     """Preconditioned conjugate gradients on complex vectors with the
     Hermitian inner product (ConjGrad of Algorithm 2), x0 = 0, stop when
-    ||A x - b|| <= rtol ||b|| (recursive residual)."""
+    ||A x - b|| <= rtol ||b|| (recursive residual) or (p, A p) <= 0 (R25)."""
     def dot(u, v):
         return complex(np.vdot(u, v)).real
     x = np.zeros_like(b)
@@ -384,7 +391,10 @@ def pcg(A, M, b, rtol, maxit):
     it = 0
     while it < maxit:
         Ap = A(p)
-        alpha = rz / dot(p, Ap)
+        pAp = dot(p, Ap)
+        if not pAp > 0.0:
+            break
+        alpha = rz / pAp
         x = x + alpha * p
         r = r - alpha * Ap
         it += 1
