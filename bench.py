@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the staggered FFT non-local damage scheme on one GB300.
+
+Workload: a 256^3 periodic RVE of 1001 random non-overlapping elastic spheres
+(radius 10 voxels, 25 % volume fraction, random sequential addition, seed 0)
+in the damaging Lemaitre matrix, uniaxial tension under mixed control
+(E11 prescribed, the other five Sigma = 0) in increments of 1e-3.  A step is
+one load increment: the full iterated staggered scheme (return maps, Newton /
+CG FFT-Galerkin mechanics, preconditioned Helmholtz solves, ERR) through the
+C ABI.  Metric: voxel-iterations/s = voxels x (mechanical CG iterations +
+Helmholtz PCG iterations) / wall time of the timed increments.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica (a single RVE does not shard); value sums the ranks' work over the
+slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iterations/s at 256^3 (mixed FP32/FP64 form; plain FP64 GPU form alongside)"
+UNIT = "voxel-iterations/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload(n):
+    import rve_inputs as I
+    cfg = I.config_3d_spheres(N=n, radius=10.0, vf=0.25, seed=0, ell_vox=4.0, n_incr=40, dE=1e-3)
+    return cfg
+
+
+def workload_config(cfg, precision):
+    return {"workload": "3d_spheres_%d" % cfg.n[0], "grid": list(cfg.n), "voxels": int(np.prod(cfg.n)),
+            "spheres": cfg.meta["count"], "radius_vox": cfg.meta["radius"],
+            "vf": round(cfg.meta["vf_voxel"], 4), "seed": cfg.meta["seed"], "ell_matrix_vox": 4.0,
+            "load": "uniaxial E11, 40 x 1e-3, Sigma_other = 0", "precision": precision,
+            "phase_sha256": cfg.meta["sha256"][:16],
+            "l2": "inputs larger than L2 (>= 5 GB touched per CG iteration)"}
+
+
+# ------------------------------------------------------------------ ranks
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        import torch
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+def allreduce(dist, x, op="max"):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self, device_index=0):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, ws, dist):
+    import torch
+    import paper_2103_04770_gb300 as pkg
+
+    torch.cuda.init()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    cfg = workload(args.n)
+    V = int(np.prod(cfg.n))
+    prec = pkg.RVE_MIXED if args.precision == "mixed" else pkg.RVE_FP64
+
+    # -------- device-resident timing
+    r = pkg.RVE(cfg, precision=prec, stream=stream)
+    for _ in range(args.warmup):
+        r.step()
+    pkg.rve_profile_reset(r.h)
+    pkg.rve_profile(r.h, True)
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start(dev)
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [r.step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ck = clocks.stop() if rank == 0 else None
+    ms = e0.elapsed_time(e1)
+    prof = pkg.rve_profile_read(r.h)
+    pkg.rve_profile(r.h, False)
+    vi = sum(i["voxel_iterations"] for i in infos)
+    ms_max = allreduce(dist, ms, "max")
+    vi_sum = allreduce(dist, vi, "sum")
+    r.close()
+
+    # -------- roofline of the dominant kernel class (live CUDA events)
+    dom = max((k for k in prof if k not in ("finalize",)), key=lambda k: prof[k][0])
+    dms, dlaunch, dbytes = prof[dom]
+    peak, peak_src = HBM_FALLBACK_GBS, "fallback"
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        try:
+            peak, peak_src = float(json.load(open(pk))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": None, "bytes_per_launch": dbytes / max(dlaunch, 1),
+                "avg_launch_ms": dms / max(dlaunch, 1), "launches": dlaunch,
+                "classes": {k: {"ms": round(v[0], 3), "launches": v[1],
+                                "GBps": round(v[2] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None}
+                            for k, v in prof.items() if v[1] > 0}}
+    gpu_launches = int(sum(v[1] for v in prof.values()))
+
+    out = {"metric": METRIC, "value": vi_sum / (ms_max * 1e-3), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if prec == pkg.RVE_MIXED else "f64", "data": "synthetic",
+           "config": workload_config(cfg, args.precision), "roofline": roofline,
+           "gpu_launches": gpu_launches, "clocks": ck,
+           "increments": [{"incr": i["increment"], "stag": i["staggered_iters"], "newton": i["newton_iters"],
+                           "cg": i["cg_iters"], "pcg": i["pcg_iters"], "S11": i["sigma"][0],
+                           "D_max": i["D_max"]} for i in infos]}
+
+    # -------- end to end through the public API with host buffers
+    if not args.no_e2e:
+        r2 = pkg.RVE(cfg, precision=prec, stream=stream)
+        for _ in range(args.warmup):
+            r2.step()
+        phase_host = np.ascontiguousarray(cfg.phase)
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.rve_set_phases(r2.h, phase_host, cfg.params, cfg.ell)          # H2D of the microstructure
+        pkg.rve_set_load_path(r2.h, cfg.strain_ctrl, cfg.target)
+        vi2 = 0.0
+        for _ in range(args.steps):
+            inf = pkg.rve_step_increment(r2.h)                             # D2H step record
+            s = pkg.rve_homogenized_stress(r2.h)                           # D2H result
+            vi2 += inf["voxel_iterations"]
+        torch.cuda.synchronize()
+        t2 = time.perf_counter() - t0
+        t2 = allreduce(dist, t2, "max")
+        vi2 = allreduce(dist, vi2, "sum")
+        r2.close()
+        h2d = V + 6 * 8 * cfg.target.shape[0] + 64 * len(cfg.params) + 8 * cfg.ell.size
+        d2h = 208 + 48
+        out["e2e"] = {"value": vi2 / t2, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                      "d2h_bytes_per_step": d2h, "includes": "rve_set_phases(host map) + "
+                      "rve_set_load_path + steps + rve_homogenized_stress per step", "s": t2}
+
+    # -------- plain FP64 GPU form on the same workload
+    if not args.no_fp64 and prec == pkg.RVE_MIXED and args.fp64_steps > 0:
+        r3 = pkg.RVE(cfg, precision=pkg.RVE_FP64, stream=stream)
+        for _ in range(args.warmup):
+            r3.step()
+        barrier(dist)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        inf3 = [r3.step() for _ in range(args.fp64_steps)]
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = allreduce(dist, f0.elapsed_time(f1), "max")
+        vi3 = allreduce(dist, sum(i["voxel_iterations"] for i in inf3), "sum")
+        s64 = [i["sigma"][0] for i in inf3]
+        r3.close()
+        # homogenised-stress error of the mixed form against the FP64 form on
+        # the same increments (the mixed run's increments warmup+1..)
+        s_mixed = [i["sigma"][0] for i in infos[:args.fp64_steps]]
+        err = max(abs(a - b) for a, b in zip(s_mixed, s64)) / max(abs(x) for x in s64)
+        out["fp64_form"] = {"value": vi3 / (ms3 * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
+                            "ms_per_step": ms3 / args.fp64_steps,
+                            "mixed_over_fp64": out["value"] / (vi3 / (ms3 * 1e-3)),
+                            "sigma11_rel_err_mixed_vs_fp64": err}
+    return out, cfg
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(cfg, iters):
+    """Bounded sample of the same workload on the host with the FP64 oracle:
+    the first increment's return map and residual, then `iters` mechanical
+    CG iterations at full size.  Returns (voxel-iterations/s, seconds)."""
+    from oracle import rve_oracle as O
+    g = O.Grid(cfg.n, cfg.L)
+    st = O.make_state(g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
+    ctrl_c = cfg.strain_ctrl.astype(float)
+    mask = 1.0 - ctrl_c
+    tm = O.to_mandel_target(cfg.target[0])
+    eps = (st.eps + ctrl_c * tm).reshape(g.shape + (6,))
+    rm = O.return_map(eps.reshape(g.V, 6), st.epsp, st.ep, st.abar, st.phase, st.phases)
+    sig = rm["sigma"].reshape(g.shape + (6,))
+    C = rm["C"].reshape(g.shape + (6, 6))
+    res = -O.G_apply(sig - mask * tm, g, mask)
+    t0 = time.perf_counter()
+    O.cg(lambda x: O.G_apply(np.einsum("...ij,...j->...i", C, x), g, mask), res, 1e-30, iters)
+    t = time.perf_counter() - t0
+    return g.V * iters / t, t
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, ws, dist):
+    """The oracle, as it stands, on the host cores: each step is one
+    mechanical CG iteration of the oracle on the full workload."""
+    cfg = workload(args.n)
+    if rank != 0:
+        return None, cfg
+    from oracle import rve_oracle as O
+    g = O.Grid(cfg.n, cfg.L)
+    st = O.make_state(g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
+    ctrl_c = cfg.strain_ctrl.astype(float)
+    mask = 1.0 - ctrl_c
+    tm = O.to_mandel_target(cfg.target[0])
+    eps = (st.eps + ctrl_c * tm).reshape(g.shape + (6,))
+    rm = O.return_map(eps.reshape(g.V, 6), st.epsp, st.ep, st.abar, st.phase, st.phases)
+    sig = rm["sigma"].reshape(g.shape + (6,))
+    C = rm["C"].reshape(g.shape + (6, 6))
+    res = -O.G_apply(sig - mask * tm, g, mask)
+    A = lambda x: O.G_apply(np.einsum("...ij,...j->...i", C, x), g, mask)  # noqa: E731
+    for _ in range(args.warmup):
+        O.cg(A, res, 1e-30, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.cg(A, res, 1e-30, 1)
+    t = time.perf_counter() - t0
+    v = g.V * args.steps / t
+    sample = "one FP64 oracle CG iteration (G*(C_T:p) + update) per step on the full 256^3 workload"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(cfg, "fp64 (CPU oracle)"),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "host_threads": cpu_threads()},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return out, cfg
+
+
+def main():
+    args = parse()
+    rank, ws, dist = dist_init()
+    if args.impl == "reference":
+        out, _ = run_reference(args, rank, ws, dist)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    out, cfg = run_ours(args, rank, ws, dist)
+    if rank == 0:
+        if not args.no_cpu and ws == 1:
+            v, t = oracle_sample(cfg, args.cpu_iters)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": "%d FP64 oracle CG iteration(s) of the first increment on the "
+                                             "full 256^3 workload (%.1f s; numpy FFT, single thread)"
+                                             % (args.cpu_iters, t),
+                                   "host_threads": cpu_threads()}
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

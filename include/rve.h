@@ -1,0 +1,234 @@
+/*
+ * rve.h -- C ABI of the GB300 library for non-local ductile damage in
+ * voxelised periodic RVEs (Magri, Lucarini, Lemoine, Adam, Segurado, "An FFT
+ * framework for simulating non-local ductile failure in heterogeneous
+ * materials").
+ *
+ * The library solves, for every load increment, the coupled problem of the
+ * paper's Section 3.1 (Eq. governing_non-local): equilibrium div sigma = 0
+ * under mixed macroscopic control (E_hk prescribed, Sigma_HK prescribed) and
+ * one generalised Helmholtz equation abar_j - div(l_j^2(x) grad abar_j) =
+ * alpha_j per non-local variable, with periodic boundary conditions, by the
+ * iterated staggered scheme of Algorithm 1: a Newton / conjugate-gradient
+ * FFT-Galerkin solve of the mechanics (Section 3.2.2) and a preconditioned
+ * CG solve of each Helmholtz equation in Fourier space (Algorithm 2).  The
+ * constitutive law is the non-local Lemaitre model (Section 2.2.3, Appendix
+ * A.2): J2 plasticity with linear hardening on the effective stress and a
+ * linear damage law driven by the non-local equivalent plastic strain.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status (rve_status); none aborts or throws.
+ *  - Grid sizes n = {N1, N2, N3} (N3 ignored in 2D); fields are stored
+ *    component-major, x1 fastest: f[c][N3][N2][N1].
+ *  - Strain/stress vectors exchanged through the handle-level calls
+ *    (targets, homogenised values) use the component order 11, 22, 33, 23,
+ *    13, 12 with TENSOR shears.  Fields passed to the operator-level calls
+ *    (rve_op_*) carry Mandel components (shears times sqrt 2): 6 in 3D,
+ *    the in-plane 11, 22, 12 in 2D (plane strain).
+ *  - Pointers documented as "device" are CUDA device pointers valid on the
+ *    handle's device; calls are enqueued on the handle's stream and are
+ *    ordered with each other.  Calls that return host values synchronise
+ *    that stream.  Inputs are copied; the caller keeps ownership of every
+ *    buffer it passes.
+ *  - One handle must not be used from two threads at once.
+ *  - Stresses are in the units of the elastic moduli given (MPa in the
+ *    shipped workloads); lengths in the units of L.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rve rve_t;
+
+typedef enum {
+  RVE_OK = 0,
+  RVE_ERR_ARG = -1,            /* invalid argument (null, size, range) */
+  RVE_ERR_STATE = -2,          /* call out of order (e.g. no phases set) */
+  RVE_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+  RVE_ERR_OOM = -4,            /* device allocation failed */
+  RVE_ERR_NOT_CONVERGED = -5,  /* an iteration budget ran out; the state is
+                                  left at the last converged increment */
+  RVE_ERR_NUMERIC = -6,        /* NaN/Inf or Krylov breakdown */
+  RVE_ERR_LOAD_PATH_END = -7   /* every increment of the load path is done */
+} rve_status;
+
+/* Per-phase constitutive parameters (Section 2.1.2; Section 4 for the damage
+ * cap).  damage_law: 0 = linear elastic (E, nu only); 1 = J2 plasticity with
+ * linear hardening sigma_0 = sigma_y + H eps_p on the effective stress and
+ * Lemaitre damage D = clamp((abar - eps_C)/(eps_R - eps_C), 0, D_max)
+ * (Eq. non-local_damage_lemaitre).  nonlocal_var: index j of the non-local
+ * variable this phase feeds with alpha_j = eps_p and reads abar_j from, or -1
+ * (Section 3.1: alpha_j = 0 outside the damaging phase). */
+typedef struct {
+  double E, nu, sigma_y, H;
+  int damage_law;
+  int nonlocal_var;
+  double eps_C, eps_R, D_max;
+} rve_phase_params;
+
+/* Solver tolerances and budgets.  The paper prints no values (Algorithm 1,
+ * Algorithm 2 use a symbolic TOL); rve_default_options fills the production
+ * set (tol_stag = tol_newton = 1e-6, cg_rtol 1e-6 mixed / 1e-8 FP64,
+ * pcg_rtol 1e-8). */
+typedef struct {
+  double tol_stag;     /* staggered ERR tolerance (Algorithm 1 (iii)) */
+  double tol_newton;   /* Newton residual and correction tolerance */
+  double cg_rtol;      /* mechanical CG: ||r|| <= cg_rtol ||b|| */
+  double pcg_rtol;     /* Helmholtz PCG: ||r|| <= pcg_rtol ||b|| (Algorithm 2) */
+  int max_stag, max_newton, max_cg, max_pcg;
+  int min_stag;        /* minimum staggered iterations (>= 2 so ERR compares
+                          two solutions) */
+  int check_every;     /* Krylov iterations launched between host checks */
+} rve_solver_options;
+
+/* Result of one load increment. */
+typedef struct {
+  int status;                /* rve_status of the increment */
+  int increment;             /* 1-based index of the increment just solved */
+  int staggered_iters;
+  int newton_iters;          /* summed over staggered iterations */
+  long long cg_iters;        /* mechanical CG iterations, summed */
+  long long pcg_iters;       /* Helmholtz PCG iterations, summed over j */
+  double err;                /* last staggered ERR */
+  double voxel_iterations;   /* V * (cg_iters + pcg_iters) */
+  double sigma[6];           /* <sigma>, tensor shears */
+  double eps[6];             /* <eps>, tensor shears */
+  double D_mean, D_max;
+  int fail_stage;            /* on failure: 1 Newton budget, 2 CG, 3 PCG,
+                                4 staggered budget, 5 numeric; 0 on success */
+  int reserved;
+} rve_step_info;
+
+/* Precision modes: RVE_FP64 runs every operator in double precision;
+ * RVE_MIXED runs FFTs, the projection, Krylov vectors and matvecs in FP32
+ * while reductions (dot products, norms), the return map, the strain and
+ * internal-variable state and the zero-frequency macroscopic block stay in
+ * FP64. */
+enum { RVE_FP64 = 0, RVE_MIXED = 1 };
+
+/* ----------------------------------------------------------------- handle */
+
+/* Fills *opt with the production defaults for the given precision. */
+int rve_default_options(int precision, rve_solver_options* opt);
+
+/* Creates a handle for a dim-dimensional grid n[0..dim-1] of a periodic cell
+ * of size L[0..dim-1] (Section 3.2.1: voxel centres at (1/2 + n_i) L_i/N_i).
+ * N1 must be even (real-to-complex transform along x1); every N_i must be a
+ * product of 2, 3 and 5.  n_nonlocal = J non-local variables (0..4).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  Allocates all
+ * device memory of the handle (cudaMalloc) on the current device.
+ * Errors: RVE_ERR_ARG, RVE_ERR_OOM, RVE_ERR_CUDA. */
+int rve_create(rve_t** out, int dim, const int n[3], const double L[3], int precision,
+               int n_nonlocal, void* cuda_stream);
+
+/* Releases every resource of the handle.  Accepts NULL. */
+void rve_free(rve_t* h);
+
+int rve_set_options(rve_t* h, const rve_solver_options* opt);
+
+/* Phase map and per-phase laws (Sections 2.2.1 and 3.1).  phase: N3*N2*N1
+ * uint8 (x1 fastest), host or device pointer, values < n_phases (<= 8).
+ * ell: [J][n_phases] characteristic lengths l_j of each phase (the piecewise
+ * l(x) of Eq. piecewiseell, with l_j small but nonzero outside the phase that
+ * carries variable j, Section 2.2.1 remark).  Resets the state to the
+ * undeformed one.  Errors: RVE_ERR_ARG (phase id out of range, bad
+ * parameters), RVE_ERR_CUDA. */
+int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase_params* params,
+                   const double* ell);
+
+/* Macroscopic load history (Section 3.1): strain_ctrl[6] = 1 where E_hk is
+ * prescribed, 0 where Sigma_HK is; target[n_incr][6] holds the prescribed
+ * value of each component at the end of each increment (host pointer).  In
+ * 2D, components 33, 23, 13 must be strain-controlled with target 0 (plane
+ * strain).  Resets the increment counter (not the state). */
+int rve_set_load_path(rve_t* h, int n_incr, const uint8_t strain_ctrl[6], const double* target);
+
+/* Solves the next load increment by Algorithm 1 and commits it.  info may be
+ * NULL.  Synchronises the stream.  On RVE_ERR_NOT_CONVERGED or
+ * RVE_ERR_NUMERIC the state stays at the last converged increment. */
+int rve_step_increment(rve_t* h, rve_step_info* info);
+
+/* Homogenised stress / strain (volume averages, Section 3.1) of the last
+ * converged increment, tensor shears, host output. */
+int rve_homogenized_stress(const rve_t* h, double sigma[6]);
+int rve_homogenized_strain(const rve_t* h, double eps[6]);
+
+/* Copies a field of the last converged increment to dst (device pointer),
+ * FP64, component-major.  which: 0 strain (Mandel, nc comps), 1 stress
+ * (Mandel, 6 comps), 2 damage D (1), 3 non-local abar (J comps), 4 eps_p (1),
+ * 5 plastic strain (Mandel, 6 comps). */
+int rve_get_field(const rve_t* h, int which, double* dst, size_t n_doubles);
+
+/* Number of voxels and carried Mandel components of a handle. */
+int rve_get_sizes(const rve_t* h, long long* n_voxels, int* n_comp, int* n_nonlocal);
+
+/* Kernel-launch accounting of a handle (a profiling aid, not part of the
+ * method).  Launches are counted per kernel class at all times, together
+ * with their algorithmic bytes (every operand read once, every result
+ * written once); with rve_profile(h, 1) each launch is also bracketed by a
+ * pair of CUDA events recorded on the handle's stream and its device time
+ * accumulated.  rve_profile_read fills total_ms[k], launches[k] and
+ * bytes[k] for k < n_classes (any may be NULL), synchronising the stream
+ * first, and returns the number of classes; rve_profile_reset zeroes them.
+ * Class names come from rve_profile_class_name(k) (NULL past the last). */
+int rve_profile(rve_t* h, int enable);
+int rve_profile_read(rve_t* h, int n_classes, double* total_ms, long long* launches, double* bytes);
+int rve_profile_reset(rve_t* h);
+const char* rve_profile_class_name(int k);
+
+/* Human-readable name of a status code (static string). */
+const char* rve_status_string(int status);
+
+/* ------------------------------------------------ operator-level calls
+ * One step of the hot path each, on caller-owned DEVICE buffers in FP64
+ * (converted to the handle's working precision inside).  They use the
+ * handle's phase map, parameters and load-path stress mask (or pure strain
+ * control if no load path is set) and do not change its increment state.
+ */
+
+/* Backward-Euler Lemaitre return map at every voxel (Appendix A.2, Eq.
+ * non-local_damage_lemaitre, with the non-local variables frozen as in
+ * Algorithm 1 (i)).  eps: [nc][V] Mandel total strain; epsp_n: [6][V] Mandel
+ * plastic strain of the last converged increment; ep_n: [V] equivalent
+ * plastic strain; abar: [J][V] non-local variables.  Outputs sigma [6][V],
+ * epsp [6][V], ep [V], D [V], alpha [J][V].  Stores the tangent for
+ * rve_op_tangent_apply / rve_op_matvec. */
+int rve_op_return_map(rve_t* h, const double* eps, const double* epsp_n, const double* ep_n,
+                      const double* abar, double* sigma, double* epsp, double* ep, double* D,
+                      double* alpha);
+
+/* tau = C_T : p with the tangent of the last rve_op_return_map (Eq.
+ * lin_stress); p, tau: [nc][V]. */
+int rve_op_tangent_apply(rve_t* h, const double* p, double* tau);
+
+/* out = G*(tau) = F^-1 { G*(xi) : F(tau) } (Eq. eqdiscrete2): the Galerkin
+ * projection with the rotated-scheme derivative and the zero frequency
+ * projected on the stress-controlled components.  tau, out: [nc][V]. */
+int rve_op_apply_gamma(rve_t* h, const double* tau, double* out);
+
+/* Ap = G*(C_T : p), the operator of the mechanical CG (Section 3.2.2). */
+int rve_op_matvec(rve_t* h, const double* p, double* Ap);
+
+/* Solves G*(C_T : x) = b by conjugate gradients from x = 0, stopping when
+ * ||r|| <= rtol ||b|| or after maxit iterations; *iters receives the count. */
+int rve_op_cg(rve_t* h, const double* b, double* x, double rtol, int maxit, int* iters);
+
+/* out = L(a) = a - div(l_j^2 grad a) evaluated spectrally (Eq.
+ * LhelmFourier); a, out: [V]. */
+int rve_op_helmholtz_apply(rve_t* h, int j, const double* a, double* out);
+
+/* Algorithm 2: abar = F^-1 ConjGrad(GC, M, F(alpha), rtol) for variable j;
+ * alpha, abar: [V]. */
+int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, double rtol,
+                           int maxit, int* iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

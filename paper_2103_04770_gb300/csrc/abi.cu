@@ -1,0 +1,1129 @@
+// C ABI and host drivers of the GB300 non-local damage RVE library.
+//
+// Host side of Algorithm 1 (iterated staggered scheme), the Newton /
+// conjugate-gradient FFT-Galerkin mechanics of Section 3.2.2 and the
+// preconditioned CG Helmholtz solve of Algorithm 2.  Every arithmetic step
+// runs in the device operators of ops.cuh; the host only sequences launches,
+// reads back a few scalars per Newton iteration and per chunk of Krylov
+// iterations, and decides convergence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ops.h"
+#include "rve.h"
+
+using namespace rvk;
+
+namespace {
+
+constexpr int kSlots = 8;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kScal = 64;
+enum {
+  OFF_SIGMEAN = 0,    // 6 (+ D mean at 6)
+  OFF_DMEAN = 6,
+  OFF_DMAX = 7,
+  OFF_EPSMEAN = 8,    // 6
+  OFF_MAXDX = 14,
+  OFF_ERRMEAN = 16,   // 6
+  OFF_ERRMAX = 22,
+  OFF_ABAR = 24,      // 2 per variable
+};
+
+// kernel classes of the launch accounting
+enum {
+  KC_RETURN_MAP = 0,
+  KC_X_FWD_TANGENT,
+  KC_X_FWD_FIELD,
+  KC_Y_PASS,
+  KC_GAMMA,
+  KC_X_INV_MATVEC,
+  KC_X_INV_RESIDUAL,
+  KC_X_INV_STORE,
+  KC_HELM_EXPAND,
+  KC_HELM_XMID,
+  KC_HELM_CONTRACT,
+  KC_CG_UPDATE,
+  KC_PCG_UPDATE,
+  KC_FINALIZE,
+  KC_MISC,
+  KC_COUNT
+};
+const char* const kClassNames[KC_COUNT] = {
+    "return_map", "x1_fwd_tangent", "x1_fwd_field", "y_pass", "gamma_last_axis", "x1_inv_matvec",
+    "x1_inv_residual", "x1_inv_store", "helmholtz_expand", "helmholtz_x1_mid", "helmholtz_contract",
+    "cg_update", "pcg_update", "finalize", "misc"};
+
+struct PendingEv {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct rve {
+  int dim = 0, prec = 0, J = 0;
+  int n[3] = {1, 1, 1};
+  double L[3] = {1, 1, 1};
+  cudaStream_t st = nullptr;
+  Geo g{};
+  LaunchCfg lc{};
+  rve_solver_options opt{};
+  // phases
+  int n_phases = 0;
+  bool phases_set = false;
+  PhaseTable pt_host{};
+  PhaseTable* pt_dev = nullptr;
+  double ell2_mean[kMaxVars] = {0, 0, 0, 0};
+  void* ell2R = nullptr;         // [kMaxVars][kMaxPhases] in working precision
+  // load path
+  int n_incr = 0, n_done = 0;
+  bool path_set = false;
+  uint8_t ctrl[6] = {1, 1, 1, 1, 1, 1};
+  std::vector<double> target;    // tensor shears
+  double E_prev[6] = {0, 0, 0, 0, 0, 0};
+  double smask_d[6] = {0, 0, 0, 0, 0, 0};
+  float smask_f[6] = {0, 0, 0, 0, 0, 0};
+  // FP64 state
+  uint8_t* phase = nullptr;
+  double *eps = nullptr, *eps_conv = nullptr, *eps_prev = nullptr;
+  double *epsp_n = nullptr, *epsp = nullptr, *ep_n = nullptr, *ep = nullptr;
+  double *sigma = nullptr, *D = nullptr, *alpha = nullptr;
+  double *abar_n = nullptr, *abar_k = nullptr, *abar_new = nullptr;
+  // working precision
+  void *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *desc = nullptr;
+  void* S = nullptr;
+  void *hx = nullptr, *hr = nullptr, *hp = nullptr, *hy = nullptr;
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  void* ts[3] = {nullptr, nullptr, nullptr};
+  void* tc[3] = {nullptr, nullptr, nullptr};
+  FftPlan plan[3]{};
+  // reductions and control
+  double* part = nullptr;
+  KrylovCtl* ctl = nullptr;
+  double* dscal = nullptr;
+  KrylovCtl* hctl = nullptr;     // pinned
+  double* hscal = nullptr;       // pinned
+  // results of the last converged increment
+  double sig_mean[6] = {0, 0, 0, 0, 0, 0};
+  double eps_mean[6] = {0, 0, 0, 0, 0, 0};
+  double D_mean = 0, D_max = 0;
+  std::vector<void*> allocs;
+  // launch accounting / profiling
+  bool prof = false;
+  long long launches[KC_COUNT] = {};
+  double prof_ms[KC_COUNT] = {};
+  double prof_bytes[KC_COUNT] = {};
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<PendingEv> ev_pending;
+  cudaEvent_t ev_cur_a = nullptr;
+  int fail_stage = 0;
+  int verbose = 0;      // RVE_VERBOSE=1: trace solver progress on stderr
+};
+
+namespace {
+
+#define CK(call)                                \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return RVE_ERR_CUDA; \
+  } while (0)
+
+bool factor_plan(int N, FftPlan& pl) {
+  pl.N = N;
+  pl.nst = 0;
+  int m = N;
+  const int rad[5] = {8, 4, 2, 5, 3};
+  while (m > 1) {
+    bool found = false;
+    for (int r : rad) {
+      if (m % r == 0) {
+        if (pl.nst >= kMaxRadixStages) return false;
+        pl.radix[pl.nst++] = r;
+        m /= r;
+        found = true;
+        break;
+      }
+    }
+    if (!found) return false;
+  }
+  return true;
+}
+
+int dalloc(rve* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? RVE_ERR_OOM : RVE_ERR_CUDA;
+  }
+  h->allocs.push_back(*p);
+  return RVE_OK;
+}
+
+template <typename T>
+int dalloc_t(rve* h, T** p, size_t count) {
+  void* v = nullptr;
+  int s = dalloc(h, &v, count * sizeof(T));
+  *p = (T*)v;
+  return s;
+}
+
+size_t rsize(const rve* h) { return h->prec == RVE_MIXED ? sizeof(float) : sizeof(double); }
+
+template <typename R>
+Tables<R> tables(const rve* h) {
+  Tables<R> t;
+  for (int j = 0; j < 3; j++) {
+    t.tw[j] = (C2<R>*)h->tw[j];
+    t.s[j] = (R*)h->ts[j];
+    t.c[j] = (R*)h->tc[j];
+    t.two_over_h[j] = (R)(2.0 / h->g.h[j]);
+  }
+  t.plan_x = h->plan[0];
+  t.plan_y = h->plan[1];
+  t.plan_z = h->plan[2];
+  return t;
+}
+
+// resolve recorded event pairs (the stream must be synchronised)
+void prof_resolve(rve* h) {
+  for (const PendingEv& e : h->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) h->prof_ms[e.cls] += ms;
+    h->ev_free.push_back(e.a);
+    h->ev_free.push_back(e.b);
+  }
+  h->ev_pending.clear();
+  cudaGetLastError();
+}
+
+cudaEvent_t prof_event(rve* h) {
+  if (h->ev_free.empty()) {
+    if (h->ev_pending.size() >= 2048) {
+      cudaStreamSynchronize(h->st);
+      prof_resolve(h);
+    }
+    if (h->ev_free.empty()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      return e;
+    }
+  }
+  cudaEvent_t e = h->ev_free.back();
+  h->ev_free.pop_back();
+  return e;
+}
+
+inline void prof_begin(rve* h, int cls, double bytes) {
+  h->launches[cls]++;
+  h->prof_bytes[cls] += bytes;
+  if (!h->prof) return;
+  h->ev_cur_a = prof_event(h);
+  if (h->ev_cur_a) cudaEventRecord(h->ev_cur_a, h->st);
+}
+
+inline void prof_end(rve* h, int cls) {
+  if (!h->prof || !h->ev_cur_a) return;
+  cudaEvent_t b = prof_event(h);
+  if (!b) return;
+  cudaEventRecord(b, h->st);
+  h->ev_pending.push_back(PendingEv{cls, h->ev_cur_a, b});
+  h->ev_cur_a = nullptr;
+}
+
+// every launch is counted with its algorithmic bytes (each operand read
+// once, each result written once) and, when profiling, timed by events
+#define LAUNCHB(h, cls, bytes, call)     \
+  do {                                   \
+    prof_begin((h), (cls), (bytes));     \
+    call;                                \
+    prof_end((h), (cls));                \
+  } while (0)
+
+int sync_read(rve* h) {
+  CK(cudaMemcpyAsync(h->hscal, h->dscal, kScal * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
+  if (h->prof) prof_resolve(h);
+  return RVE_OK;
+}
+
+int xblocks(const rve* h, int nc) {
+  return (int)((h->g.nlines + h->lc.nrows_c[nc] - 1) / h->lc.nrows_c[nc]);
+}
+
+int last_blocks(const rve* h) {
+  const int nt = (h->g.P1 + h->lc.tx - 1) / h->lc.tx;
+  return nt * (h->g.d == 3 ? h->g.n2 : 1);
+}
+
+template <typename R>
+struct Alg {
+  using Op = Ops<R>;
+  static constexpr double RS = sizeof(R);
+  static constexpr double CS = 2.0 * sizeof(R);
+  static double VS(const rve* h) { return (double)h->g.P1 * (double)h->g.nlines; }
+  static double VV(const rve* h) { return (double)h->g.V; }
+
+  // G* on the x1-transformed spectrum S: y forward, last-axis G*, y inverse.
+  static void gamma_sweep(rve* h, const Tables<R>& t, int dc_mode, const KrylovCtl* ctl) {
+    C2<R>* S = (C2<R>*)h->S;
+    if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)h->g.nc * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, S, h->g.nc, 1, -1, ctl));
+    LAUNCHB(h, KC_GAMMA, 2.0 * (double)h->g.nc * VS(h) * CS, Op::gamma(h->g, t, h->lc, h->st, S, h->smask_f, dc_mode, ctl));
+    if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)h->g.nc * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, S, h->g.nc, 1, +1, ctl));
+  }
+
+  static void return_map(rve* h, const double* abar_use) {
+    LAUNCHB(h, KC_RETURN_MAP, VV(h) * (8.0 * h->g.nc + 169.0 + 16.0 * h->J + (2.0 + h->g.nc) * RS), Op::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, h->eps, h->epsp_n, h->ep_n, abar_use,
+                   h->sigma, h->epsp, h->ep, h->D, h->alpha, (R*)h->desc, h->part));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 7, FIN_SUMS, nullptr,
+               h->dscal + OFF_SIGMEAN, 1.0 / (double)h->g.V));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 7 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
+               FIN_MAXS, nullptr, h->dscal + OFF_DMAX, 1.0));
+  }
+
+  // b = -G*(sigma - Sigma_bar) into r, ctl initialised for CG.
+  static void residual(rve* h, const Tables<R>& t, const double* sbar_c, double rtol, int maxit) {
+    LAUNCHB(h, KC_X_FWD_FIELD, (double)h->g.nc * (8.0 * VV(h) + VS(h) * CS), Op::xfwd_field64(h->g, t, h->lc, h->st, h->sigma, h->g.nc, h->g.cmap, h->dscal + OFF_SIGMEAN,
+                     (C2<R>*)h->S));
+    gamma_sweep(h, t, 1, nullptr);
+    LAUNCHB(h, KC_X_INV_RESIDUAL, (double)h->g.nc * (VS(h) * CS + VV(h) * RS), Op::xinv_residual(h->g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->r, h->dscal + OFF_SIGMEAN,
+                      h->smask_d, sbar_c, h->part));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, h->g.nc), h->lc.max_blocks, 1, FIN_CG_INIT, h->ctl, nullptr,
+               rtol * rtol, maxit));
+  }
+
+  // CG on G*(C_T : x) = b (r holds b, ctl initialised, x zeroed by caller).
+  static int cg_loop(rve* h, const Tables<R>& t, int* iters) {
+    const Geo& g = h->g;
+    const int chunk = std::max(1, h->opt.check_every);
+    const int nbx = xblocks(h, g.nc);
+    for (;;) {
+      for (int i = 0; i < chunk; i++) {
+        LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S,
+                         h->ctl));
+        gamma_sweep(h, t, 0, h->ctl);
+        LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 2.0 * VV(h) * RS), Op::xinv_matvec(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, h->ctl));
+        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+        LAUNCHB(h, KC_CG_UPDATE, 6.0 * g.nc * VV(h) * RS, Op::cg_update(g, h->lc, h->st, (R*)h->x, (R*)h->r, (const R*)h->p, (const R*)h->Ap, h->part, h->ctl));
+        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
+      }
+      int s = sync_read(h);
+      if (s) return s;
+      if (h->hctl->done) break;
+    }
+    *iters = h->hctl->iter;
+    if (h->hctl->status == 3) { h->fail_stage = 5; return RVE_ERR_NUMERIC; }
+    if (h->hctl->status == 2) { h->fail_stage = 2; return RVE_ERR_NOT_CONVERGED; }
+    return RVE_OK;
+  }
+
+  // Newton-Raphson on the Galerkin residual at fixed abar (Algorithm 1 (i)).
+  static int mech_solve(rve* h, const Tables<R>& t, const double* abar_use, const double* sbar_c,
+                        int* newton_out, long long* cg_out) {
+    const Geo& g = h->g;
+    double de_rel = -1.0;
+    int newton = 0;
+    for (;;) {
+      return_map(h, abar_use);
+      residual(h, t, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
+      int s = sync_read(h);
+      if (s) return s;
+      double sm = 0.0;
+      for (int c = 0; c < g.nc; c++) sm += h->hscal[OFF_SIGMEAN + g.cmap[c]] * h->hscal[OFF_SIGMEAN + g.cmap[c]];
+      sm = std::sqrt(sm);
+      const double b2 = h->hctl->b2;
+      if (!(b2 == b2)) { h->fail_stage = 5; return RVE_ERR_NUMERIC; }
+      const double res_rel = std::sqrt(b2) / (std::sqrt((double)g.V) * std::max(sm, 1e-300));
+      if (h->verbose)
+        std::fprintf(stderr, "[rve] newton %d res_rel %.3e de_rel %.3e |<sigma>| %.6e\n", newton, res_rel,
+                     de_rel, sm);
+      if (res_rel < h->opt.tol_newton && (de_rel < 0.0 || de_rel < h->opt.tol_newton)) break;
+      if (newton >= h->opt.max_newton) { h->fail_stage = 1; *newton_out += newton; return RVE_ERR_NOT_CONVERGED; }
+      CK(cudaMemsetAsync(h->x, 0, (size_t)g.nc * g.V * rsize(h), h->st));
+      int it = 0;
+      s = cg_loop(h, t, &it);
+      *cg_out += it;
+      if (h->verbose)
+        std::fprintf(stderr, "[rve]   cg iters %d status %d pAp %.3e rnorm2 %.3e b2 %.3e -> %d\n", it,
+                     h->hctl->status, h->hctl->pAp, h->hctl->rnorm2, h->hctl->b2, s);
+      if (s) return s;
+      LAUNCHB(h, KC_MISC, g.nc * VV(h) * (16.0 + RS), Op::eps_update(g, h->lc, h->st, h->eps, (const R*)h->x, h->part));
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 6, FIN_SUMS, nullptr,
+                 h->dscal + OFF_EPSMEAN, 1.0 / (double)g.V));
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 6 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
+                 FIN_MAXS, nullptr, h->dscal + OFF_MAXDX, 1.0));
+      s = sync_read(h);
+      if (s) return s;
+      newton++;
+      double em = 0.0;
+      for (int c = 0; c < g.nc; c++) em += h->hscal[OFF_EPSMEAN + c] * h->hscal[OFF_EPSMEAN + c];
+      de_rel = h->hscal[OFF_MAXDX] / std::max(std::sqrt(em), 1e-300);
+    }
+    *newton_out += newton;
+    return RVE_OK;
+  }
+
+  // Forward transform of one real FP64 field into the 1-component spectrum out.
+  static void forward1(rve* h, const Tables<R>& t, const double* f, C2<R>* out) {
+    const int map0[6] = {0, 0, 0, 0, 0, 0};
+    LAUNCHB(h, KC_X_FWD_FIELD, 1.0 * (8.0 * VV(h) + VS(h) * CS), Op::xfwd_field64(h->g, t, h->lc, h->st, f, 1, map0, nullptr, out));
+    LAUNCHB(h, KC_Y_PASS, 2.0 * 1.0 * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, out, 1, 1, -1, nullptr));
+    if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * 1.0 * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, out, 1, 2, -1, nullptr));
+  }
+
+  static void inverse1(rve* h, const Tables<R>& t, C2<R>* in, double* f) {
+    if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * 1.0 * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, in, 1, 2, +1, nullptr));
+    LAUNCHB(h, KC_Y_PASS, 2.0 * 1.0 * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, in, 1, 1, +1, nullptr));
+    LAUNCHB(h, KC_X_INV_STORE, 1.0 * (VS(h) * CS + 8.0 * VV(h)), Op::xinv_store64(h->g, t, h->lc, h->st, in, 1, f));
+  }
+
+  // Helmholtz operator application on the spectrum: y = p + conj(k).F(l^2 F^-1(k p)).
+  static void helm_matvec(rve* h, const Tables<R>& t, int j, C2<R>* pvec, const C2<R>* rsrc, C2<R>* y,
+                          const KrylovCtl* ctl, int raw) {
+    const Geo& g = h->g;
+    C2<R>* W = (C2<R>*)h->S;
+    LAUNCHB(h, KC_HELM_EXPAND, (raw ? 1.0 + g.d : 3.0 + g.d) * VS(h) * CS, Op::helm_expand(g, t, h->lc, h->st, W, pvec, rsrc, h->ell2_mean[j], ctl, raw));
+    if (g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)g.d * VS(h) * CS, Op::strided_plain(g, t, h->lc, h->st, W, g.d, 1, +1, ctl));
+    LAUNCHB(h, KC_HELM_XMID, 2.0 * g.d * VS(h) * CS + VV(h), Op::xmid_ell(g, t, h->lc, h->st, W, h->phase, (const R*)h->ell2R + j * kMaxPhases, ctl));
+    if (g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)g.d * VS(h) * CS, Op::strided_plain(g, t, h->lc, h->st, W, g.d, 1, -1, ctl));
+    LAUNCHB(h, KC_HELM_CONTRACT, (g.d + 2.0) * VS(h) * CS, Op::helm_contract(g, t, h->lc, h->st, W, raw ? rsrc : pvec, y, h->part, ctl));
+  }
+
+  // Algorithm 2 for variable j: abar = F^-1 PCG(GC, M, F(alpha)).
+  static int helm_solve(rve* h, const Tables<R>& t, int j, const double* alpha_j, double* abar_out,
+                        double rtol, int maxit, int* iters) {
+    const Geo& g = h->g;
+    C2<R>* hx = (C2<R>*)h->hx;
+    C2<R>* hr = (C2<R>*)h->hr;
+    C2<R>* hp = (C2<R>*)h->hp;
+    C2<R>* hy = (C2<R>*)h->hy;
+    forward1(h, t, alpha_j, hr);
+    LAUNCHB(h, KC_PCG_UPDATE, 2.0 * VS(h) * CS, Op::pcg_init(g, t, h->lc, h->st, hx, hr, h->ell2_mean[j], h->part));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_INIT, h->ctl, nullptr,
+               rtol * rtol, maxit));
+    const int chunk = std::max(1, h->opt.check_every);
+    const int nbl = last_blocks(h);
+    for (;;) {
+      for (int i = 0; i < chunk; i++) {
+        helm_matvec(h, t, j, hp, hr, hy, h->ctl, 0);
+        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbl, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+        LAUNCHB(h, KC_CG_UPDATE, 6.0 * g.nc * VV(h) * RS, Op::pcg_update(g, t, h->lc, h->st, hx, hr, hp, hy, h->ell2_mean[j], h->part, h->ctl));
+        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_BETA, h->ctl, nullptr, 1.0));
+      }
+      int s = sync_read(h);
+      if (s) return s;
+      if (h->hctl->done) break;
+    }
+    *iters = h->hctl->iter;
+    inverse1(h, t, hx, abar_out);
+    if (h->hctl->status == 3) { h->fail_stage = 5; return RVE_ERR_NUMERIC; }
+    if (h->hctl->status == 2) { h->fail_stage = 3; return RVE_ERR_NOT_CONVERGED; }
+    return RVE_OK;
+  }
+
+  // One load increment (Algorithm 1).
+  static int step(rve* h, rve_step_info* info) {
+    const Geo& g = h->g;
+    const Tables<R> t = tables<R>(h);
+    const double sq2 = std::sqrt(2.0);
+    const double W6[6] = {1, 1, 1, sq2, sq2, sq2};
+    const double* tg = &h->target[(size_t)h->n_done * 6];
+    double dE[6] = {0, 0, 0, 0, 0, 0}, sbar[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < g.nc; c++) {
+      const int m = g.cmap[c];
+      const double tm = tg[m] * W6[m], tp = h->E_prev[m] * W6[m];
+      dE[c] = h->ctrl[m] ? tm - tp : 0.0;
+      sbar[c] = h->ctrl[m] ? 0.0 : tm;
+    }
+    // initial guess (eps_n + dE on strain-controlled components; abar_n)
+    LAUNCHB(h, KC_MISC, 16.0 * g.nc * VV(h), k_copy_add(h->st, g.V, g.nc, h->eps_conv, h->eps, dE));
+    CK(cudaMemcpyAsync(h->abar_k, h->abar_n, sizeof(double) * h->J * g.V, cudaMemcpyDeviceToDevice, h->st));
+    int stag = 0, newton = 0;
+    long long cg = 0, pcg = 0;
+    double err = 0.0;
+    int status = RVE_OK;
+    h->fail_stage = 0;
+    for (;;) {
+      CK(cudaMemcpyAsync(h->eps_prev, h->eps, sizeof(double) * g.nc * g.V, cudaMemcpyDeviceToDevice, h->st));
+      status = mech_solve(h, t, h->abar_k, sbar, &newton, &cg);
+      if (status) break;
+      for (int j = 0; j < h->J; j++) {
+        int it = 0;
+        status = helm_solve(h, t, j, h->alpha + (size_t)j * g.V, h->abar_new + (size_t)j * g.V,
+                            h->opt.pcg_rtol, h->opt.max_pcg, &it);
+        pcg += it;
+        if (h->verbose)
+          std::fprintf(stderr, "[rve]   pcg j=%d iters %d status %d b2 %.3e -> %d\n", j, it, h->hctl->status,
+                       h->hctl->b2, status);
+        if (status) break;
+      }
+      if (status) break;
+      LAUNCHB(h, KC_MISC, 16.0 * g.nc * VV(h), k_err_eps(g, h->lc, h->st, h->eps, h->eps_prev, h->part));
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 6, FIN_SUMS, nullptr,
+                 h->dscal + OFF_ERRMEAN, 1.0 / (double)g.V));
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 6 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
+                 FIN_MAXS, nullptr, h->dscal + OFF_ERRMAX, 1.0));
+      for (int j = 0; j < h->J; j++) {
+        LAUNCHB(h, KC_MISC, 16.0 * VV(h), k_err_abar(g, h->lc, h->st, h->abar_new + (size_t)j * g.V, h->abar_k + (size_t)j * g.V, h->part));
+        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_SUMS, nullptr,
+                   h->dscal + OFF_ABAR + 2 * j, 1.0));
+      }
+      status = sync_read(h);
+      if (status) break;
+      double em = 0.0;
+      for (int c = 0; c < g.nc; c++) em += h->hscal[OFF_ERRMEAN + c] * h->hscal[OFF_ERRMEAN + c];
+      err = h->hscal[OFF_ERRMAX] / std::max(std::sqrt(em), 1e-300);
+      for (int j = 0; j < h->J; j++) {
+        const double an = std::sqrt(h->hscal[OFF_ABAR + 2 * j + 1]);
+        if (an >= 1e-30) err = std::max(err, std::sqrt(h->hscal[OFF_ABAR + 2 * j]) / an);
+      }
+      if (h->verbose) std::fprintf(stderr, "[rve] staggered %d err %.3e\n", stag, err);
+      if (!(err == err)) { h->fail_stage = 5; status = RVE_ERR_NUMERIC; break; }
+      std::swap(h->abar_k, h->abar_new);
+      stag++;
+      if (stag >= h->opt.min_stag && err <= h->opt.tol_stag) break;
+      if (stag >= h->opt.max_stag) { h->fail_stage = 4; status = RVE_ERR_NOT_CONVERGED; break; }
+    }
+    if (status) {
+      // roll back to the last converged increment
+      cudaMemcpyAsync(h->eps, h->eps_conv, sizeof(double) * g.nc * g.V, cudaMemcpyDeviceToDevice, h->st);
+      cudaStreamSynchronize(h->st);
+      if (info) {
+        info->status = status;
+        info->increment = h->n_done + 1;
+        info->staggered_iters = stag;
+        info->newton_iters = newton;
+        info->cg_iters = cg;
+        info->pcg_iters = pcg;
+        info->err = err;
+        info->fail_stage = h->fail_stage;
+      }
+      return status;
+    }
+    // commit
+    CK(cudaMemcpyAsync(h->eps_conv, h->eps, sizeof(double) * g.nc * g.V, cudaMemcpyDeviceToDevice, h->st));
+    std::swap(h->epsp_n, h->epsp);
+    std::swap(h->ep_n, h->ep);
+    std::swap(h->abar_n, h->abar_k);
+    CK(cudaStreamSynchronize(h->st));
+    for (int c = 0; c < 6; c++) h->sig_mean[c] = h->hscal[OFF_SIGMEAN + c] / W6[c];
+    for (int c = 0; c < 6; c++) h->eps_mean[c] = 0.0;
+    for (int c = 0; c < g.nc; c++) h->eps_mean[g.cmap[c]] = h->hscal[OFF_ERRMEAN + c] / W6[g.cmap[c]];
+    for (int c = 0; c < 6; c++)
+      if (h->ctrl[c]) h->E_prev[c] = tg[c];
+    h->D_mean = h->hscal[OFF_DMEAN];
+    h->D_max = h->hscal[OFF_DMAX];
+    h->n_done++;
+    if (info) {
+      info->status = RVE_OK;
+      info->increment = h->n_done;
+      info->staggered_iters = stag;
+      info->newton_iters = newton;
+      info->cg_iters = cg;
+      info->pcg_iters = pcg;
+      info->err = err;
+      info->voxel_iterations = (double)g.V * (double)(cg + pcg);
+      for (int c = 0; c < 6; c++) {
+        info->sigma[c] = h->sig_mean[c];
+        info->eps[c] = h->eps_mean[c];
+      }
+      info->D_mean = h->D_mean;
+      info->D_max = h->D_max;
+    }
+    return RVE_OK;
+  }
+
+  // -------------------------------------------------------- operator level
+  static int op_apply_gamma(rve* h, const double* tau, double* out) {
+    const Tables<R> t = tables<R>(h);
+    int map[6] = {0, 1, 2, 3, 4, 5};
+    LAUNCHB(h, KC_X_FWD_FIELD, (double)h->g.nc * (8.0 * VV(h) + VS(h) * CS), Op::xfwd_field64(h->g, t, h->lc, h->st, tau, h->g.nc, map, nullptr, (C2<R>*)h->S));
+    gamma_sweep(h, t, 0, nullptr);
+    LAUNCHB(h, KC_X_INV_STORE, (double)h->g.nc * (VS(h) * CS + 8.0 * VV(h)), Op::xinv_store64(h->g, t, h->lc, h->st, (const C2<R>*)h->S, h->g.nc, out));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return RVE_OK;
+  }
+
+  static int op_matvec(rve* h, const double* p, double* Ap) {
+    const Tables<R> t = tables<R>(h);
+    const long long n = (long long)h->g.nc * h->g.V;
+    LAUNCHB(h, KC_MISC, (double)n * (8.0 + RS), Op::to_r(h->st, n, p, (R*)h->p));
+    LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (2.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(h->g, t, h->lc, h->st, (R*)h->p, nullptr, (const R*)h->desc, (C2<R>*)h->S, nullptr));
+    gamma_sweep(h, t, 0, nullptr);
+    LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 2.0 * VV(h) * RS), Op::xinv_matvec(h->g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, nullptr));
+    LAUNCHB(h, KC_MISC, (double)n * (8.0 + RS), Op::from_r(h->st, n, (const R*)h->Ap, Ap));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return RVE_OK;
+  }
+
+  static int op_cg(rve* h, const double* b, double* x, double rtol, int maxit, int* iters) {
+    const Tables<R> t = tables<R>(h);
+    const long long n = (long long)h->g.nc * h->g.V;
+    LAUNCHB(h, KC_MISC, (double)n * (8.0 + RS), Op::to_r(h->st, n, b, (R*)h->r));
+    LAUNCHB(h, KC_CG_UPDATE, 2.0 * h->g.nc * VV(h) * RS, Op::cg_init(h->g, h->lc, h->st, (R*)h->x, (const R*)h->r, h->part));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_INIT, h->ctl, nullptr,
+               rtol * rtol, maxit));
+    int it = 0;
+    int s = cg_loop(h, t, &it);
+    if (iters) *iters = it;
+    LAUNCHB(h, KC_MISC, (double)n * (8.0 + RS), Op::from_r(h->st, n, (const R*)h->x, x));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return s;
+  }
+
+  static int op_helm_apply(rve* h, int j, const double* a, double* out) {
+    const Tables<R> t = tables<R>(h);
+    forward1(h, t, a, (C2<R>*)h->hr);
+    helm_matvec(h, t, j, (C2<R>*)h->hp, (const C2<R>*)h->hr, (C2<R>*)h->hy, nullptr, 1);
+    inverse1(h, t, (C2<R>*)h->hy, out);
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return RVE_OK;
+  }
+
+  static int op_helm_solve(rve* h, int j, const double* alpha, double* abar, double rtol, int maxit,
+                           int* iters) {
+    const Tables<R> t = tables<R>(h);
+    int it = 0;
+    int s = helm_solve(h, t, j, alpha, abar, rtol, maxit, &it);
+    if (iters) *iters = it;
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    return s;
+  }
+};
+
+template <typename R>
+int build_tables(rve* h) {
+  const int Ns[3] = {h->g.n1, h->g.n2, h->g.n3};
+  for (int j = 0; j < 3; j++) {
+    const int N = Ns[j];
+    std::vector<C2<R>> tw(N);
+    std::vector<R> s(N), c(N);
+    for (int m = 0; m < N; m++) {
+      const double ang = -2.0 * kPi * (double)m / (double)N;
+      tw[m] = mk<R>((R)std::cos(ang), (R)std::sin(ang));
+      const int q = m < (N + 1) / 2 ? m : m - N;
+      const double half = kPi * (double)q / (double)N;
+      s[m] = (R)std::sin(half);
+      c[m] = (2 * std::abs(q) == N) ? R(0) : (R)std::cos(half);
+    }
+    int st;
+    if ((st = dalloc(h, &h->tw[j], N * sizeof(C2<R>)))) return st;
+    if ((st = dalloc(h, &h->ts[j], N * sizeof(R)))) return st;
+    if ((st = dalloc(h, &h->tc[j], N * sizeof(R)))) return st;
+    CK(cudaMemcpy(h->tw[j], tw.data(), N * sizeof(C2<R>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->ts[j], s.data(), N * sizeof(R), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->tc[j], c.data(), N * sizeof(R), cudaMemcpyHostToDevice));
+  }
+  return RVE_OK;
+}
+
+int upload_ell2(rve* h) {
+  if (h->prec == RVE_MIXED) {
+    std::vector<float> v(kMaxVars * kMaxPhases, 0.f);
+    for (int j = 0; j < kMaxVars; j++)
+      for (int q = 0; q < kMaxPhases; q++) v[j * kMaxPhases + q] = (float)h->pt_host.ell2[j][q];
+    CK(cudaMemcpy(h->ell2R, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> v(kMaxVars * kMaxPhases, 0.0);
+    for (int j = 0; j < kMaxVars; j++)
+      for (int q = 0; q < kMaxPhases; q++) v[j * kMaxPhases + q] = h->pt_host.ell2[j][q];
+    CK(cudaMemcpy(h->ell2R, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return RVE_OK;
+}
+
+int reset_state(rve* h) {
+  const size_t V = (size_t)h->g.V, nc = h->g.nc;
+  CK(cudaMemsetAsync(h->eps, 0, nc * V * 8, h->st));
+  CK(cudaMemsetAsync(h->eps_conv, 0, nc * V * 8, h->st));
+  CK(cudaMemsetAsync(h->eps_prev, 0, nc * V * 8, h->st));
+  CK(cudaMemsetAsync(h->epsp_n, 0, 6 * V * 8, h->st));
+  CK(cudaMemsetAsync(h->epsp, 0, 6 * V * 8, h->st));
+  CK(cudaMemsetAsync(h->ep_n, 0, V * 8, h->st));
+  CK(cudaMemsetAsync(h->ep, 0, V * 8, h->st));
+  CK(cudaMemsetAsync(h->sigma, 0, 6 * V * 8, h->st));
+  CK(cudaMemsetAsync(h->D, 0, V * 8, h->st));
+  const size_t JV = (size_t)std::max(h->J, 1) * V * 8;
+  CK(cudaMemsetAsync(h->alpha, 0, JV, h->st));
+  CK(cudaMemsetAsync(h->abar_n, 0, JV, h->st));
+  CK(cudaMemsetAsync(h->abar_k, 0, JV, h->st));
+  CK(cudaMemsetAsync(h->abar_new, 0, JV, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->n_done = 0;
+  for (int c = 0; c < 6; c++) { h->E_prev[c] = 0; h->sig_mean[c] = 0; h->eps_mean[c] = 0; }
+  h->D_mean = h->D_max = 0;
+  return RVE_OK;
+}
+
+void free_all(rve* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->hctl) cudaFreeHost(h->hctl);
+  if (h->hscal) cudaFreeHost(h->hscal);
+  h->hctl = nullptr;
+  h->hscal = nullptr;
+}
+
+int create_impl(rve** out, int dim, const int n[3], const double L[3], int precision, int J, void* stream) {
+  if (!out || !n || !L) return RVE_ERR_ARG;
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return RVE_ERR_ARG;
+  if (precision != RVE_FP64 && precision != RVE_MIXED) return RVE_ERR_ARG;
+  if (J < 0 || J > kMaxVars) return RVE_ERR_ARG;
+  int nn[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+  double LL[3] = {L[0], L[1], dim == 3 ? L[2] : 1.0};
+  for (int j = 0; j < dim; j++)
+    if (nn[j] < 1 || !(LL[j] > 0.0)) return RVE_ERR_ARG;
+  if (nn[0] < 2 || nn[0] % 2) return RVE_ERR_ARG;
+  const int ET = (precision == RVE_MIXED ? 8 : 4) * kThreads;
+  if (std::max(nn[1], nn[2]) > ET) return RVE_ERR_ARG;
+  const int nc = dim == 3 ? 6 : 3;
+  if ((nn[0] / 2) * nc > 16 * kThreads) return RVE_ERR_ARG;
+  FftPlan pl[3];
+  if (!factor_plan(nn[0] / 2, pl[0]) || !factor_plan(nn[1], pl[1]) || !factor_plan(nn[2], pl[2]))
+    return RVE_ERR_ARG;
+
+  rve* h = new (std::nothrow) rve();
+  if (!h) return RVE_ERR_OOM;
+  h->dim = dim;
+  h->prec = precision;
+  h->J = J;
+  for (int j = 0; j < 3; j++) { h->n[j] = nn[j]; h->L[j] = LL[j]; h->plan[j] = pl[j]; }
+  h->st = (cudaStream_t)stream;
+  rve_default_options(precision, &h->opt);
+  {
+    const char* v = std::getenv("RVE_VERBOSE");
+    h->verbose = (v && v[0] && v[0] != '0') ? 1 : 0;
+  }
+
+  Geo& g = h->g;
+  g.d = dim;
+  g.n1 = nn[0]; g.n2 = nn[1]; g.n3 = nn[2];
+  g.M = nn[0] / 2;
+  g.P1 = g.M + 1;
+  const int align = precision == RVE_MIXED ? 16 : 8;
+  g.ps = ((g.P1 + align - 1) / align) * align;
+  g.nc = nc;
+  const int cm3[6] = {0, 1, 2, 3, 4, 5}, cm2[6] = {0, 1, 5, 0, 0, 0};
+  for (int c = 0; c < 6; c++) g.cmap[c] = dim == 3 ? cm3[c] : cm2[c];
+  g.V = (long long)nn[0] * nn[1] * nn[2];
+  g.nlines = (long long)nn[1] * nn[2];
+  g.sstride = (long long)g.ps * nn[1] * nn[2];
+  for (int j = 0; j < 3; j++) g.h[j] = LL[j] / nn[j];
+
+  LaunchCfg& lc = h->lc;
+  for (int c = 1; c <= 6; c++) lc.nrows_c[c] = std::max(1, std::min(32, (16 * kThreads) / (c * g.M)));
+  lc.nrows_c[0] = 1;
+  int tx = 1;
+  const int nmax = std::max(nn[1], nn[2]);
+  while (tx * 2 * nmax <= ET && tx * 2 <= 32) tx *= 2;
+  lc.tx = tx;
+  long long ew = (g.V + kThreads - 1) / kThreads;
+  lc.n_ew_blocks = (int)std::min<long long>(ew, 152LL * 16);
+  long long mb = lc.n_ew_blocks;
+  for (int c = 1; c <= 6; c++) mb = std::max<long long>(mb, (g.nlines + lc.nrows_c[c] - 1) / lc.nrows_c[c]);
+  mb = std::max<long long>(mb, (long long)((g.P1 + tx - 1) / tx) * std::max(nn[1], 1));
+  lc.max_blocks = (int)mb;
+
+  int s = RVE_OK;
+  const size_t V = (size_t)g.V;
+  const size_t JV = (size_t)std::max(J, 1) * V;
+  const size_t rs = rsize(h);
+  const size_t cs = 2 * rs;
+#define AL(expr)                 \
+  if ((s = (expr)) != RVE_OK) {  \
+    free_all(h);                 \
+    delete h;                    \
+    return s;                    \
+  }
+  AL(dalloc_t(h, &h->phase, V));
+  AL(dalloc_t(h, &h->eps, nc * V));
+  AL(dalloc_t(h, &h->eps_conv, nc * V));
+  AL(dalloc_t(h, &h->eps_prev, nc * V));
+  AL(dalloc_t(h, &h->epsp_n, 6 * V));
+  AL(dalloc_t(h, &h->epsp, 6 * V));
+  AL(dalloc_t(h, &h->ep_n, V));
+  AL(dalloc_t(h, &h->ep, V));
+  AL(dalloc_t(h, &h->sigma, 6 * V));
+  AL(dalloc_t(h, &h->D, V));
+  AL(dalloc_t(h, &h->alpha, JV));
+  AL(dalloc_t(h, &h->abar_n, JV));
+  AL(dalloc_t(h, &h->abar_k, JV));
+  AL(dalloc_t(h, &h->abar_new, JV));
+  AL(dalloc(h, &h->x, nc * V * rs));
+  AL(dalloc(h, &h->r, nc * V * rs));
+  AL(dalloc(h, &h->p, nc * V * rs));
+  AL(dalloc(h, &h->Ap, nc * V * rs));
+  AL(dalloc(h, &h->desc, (2 + nc) * V * rs));
+  AL(dalloc(h, &h->S, (size_t)nc * g.sstride * cs));
+  AL(dalloc(h, &h->hx, (size_t)g.sstride * cs));
+  AL(dalloc(h, &h->hr, (size_t)g.sstride * cs));
+  AL(dalloc(h, &h->hp, (size_t)g.sstride * cs));
+  AL(dalloc(h, &h->hy, (size_t)g.sstride * cs));
+  AL(dalloc(h, &h->ell2R, kMaxVars * kMaxPhases * rs));
+  AL(dalloc_t(h, &h->pt_dev, 1));
+  AL(dalloc_t(h, &h->part, (size_t)kSlots * lc.max_blocks));
+  AL(dalloc_t(h, &h->ctl, 1));
+  AL(dalloc_t(h, &h->dscal, kScal));
+  AL(precision == RVE_MIXED ? build_tables<float>(h) : build_tables<double>(h));
+#undef AL
+  if (cudaMallocHost((void**)&h->hctl, sizeof(KrylovCtl)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->hscal, kScal * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return RVE_ERR_OOM;
+  }
+  // a (spectral) buffer that is never written in the padding stays defined
+  cudaMemset(h->S, 0, (size_t)nc * g.sstride * cs);
+  cudaMemset(h->hx, 0, (size_t)g.sstride * cs);
+  cudaMemset(h->hr, 0, (size_t)g.sstride * cs);
+  cudaMemset(h->hp, 0, (size_t)g.sstride * cs);
+  cudaMemset(h->hy, 0, (size_t)g.sstride * cs);
+  cudaMemset(h->dscal, 0, kScal * sizeof(double));
+  cudaMemset(h->ctl, 0, sizeof(KrylovCtl));
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return RVE_ERR_CUDA;
+  }
+  // default load path: pure strain control (operator-level calls)
+  for (int c = 0; c < 6; c++) { h->smask_d[c] = 0.0; h->smask_f[c] = 0.f; }
+  if ((s = reset_state(h)) != RVE_OK) {
+    free_all(h);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return RVE_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int rve_profile(rve_t* h, int enable) {
+  if (!h) return RVE_ERR_ARG;
+  if (h->prof && !enable) {
+    cudaStreamSynchronize(h->st);
+    prof_resolve(h);
+  }
+  h->prof = enable != 0;
+  return RVE_OK;
+}
+
+int rve_profile_read(rve_t* h, int n, double* ms, long long* launches, double* bytes) {
+  if (!h || n < 0) return RVE_ERR_ARG;
+  CK(cudaStreamSynchronize(h->st));
+  prof_resolve(h);
+  const int m = std::min(n, (int)KC_COUNT);
+  for (int k = 0; k < m; k++) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->launches[k];
+    if (bytes) bytes[k] = h->prof_bytes[k];
+  }
+  return KC_COUNT;
+}
+
+int rve_profile_reset(rve_t* h) {
+  if (!h) return RVE_ERR_ARG;
+  cudaStreamSynchronize(h->st);
+  prof_resolve(h);
+  for (int k = 0; k < KC_COUNT; k++) { h->prof_ms[k] = 0.0; h->launches[k] = 0; h->prof_bytes[k] = 0.0; }
+  return RVE_OK;
+}
+
+const char* rve_profile_class_name(int k) { return (k >= 0 && k < KC_COUNT) ? kClassNames[k] : nullptr; }
+
+const char* rve_status_string(int s) {
+  switch (s) {
+    case RVE_OK: return "ok";
+    case RVE_ERR_ARG: return "invalid argument";
+    case RVE_ERR_STATE: return "call out of order";
+    case RVE_ERR_CUDA: return "CUDA runtime error";
+    case RVE_ERR_OOM: return "out of device memory";
+    case RVE_ERR_NOT_CONVERGED: return "iteration budget exhausted";
+    case RVE_ERR_NUMERIC: return "non-finite value or Krylov breakdown";
+    case RVE_ERR_LOAD_PATH_END: return "load path finished";
+    default: return "unknown status";
+  }
+}
+
+int rve_default_options(int precision, rve_solver_options* o) {
+  if (!o) return RVE_ERR_ARG;
+  o->tol_stag = 1e-6;
+  o->tol_newton = 1e-6;
+  o->cg_rtol = precision == RVE_MIXED ? 1e-6 : 1e-8;
+  o->pcg_rtol = 1e-8;
+  o->max_stag = 50;
+  o->max_newton = 30;
+  o->max_cg = 2000;
+  o->max_pcg = 2000;
+  o->min_stag = 2;
+  o->check_every = 8;
+  return RVE_OK;
+}
+
+int rve_create(rve_t** out, int dim, const int n[3], const double L[3], int precision, int n_nonlocal,
+               void* cuda_stream) {
+  try {
+    return create_impl(out, dim, n, L, precision, n_nonlocal, cuda_stream);
+  } catch (...) {
+    return RVE_ERR_OOM;
+  }
+}
+
+void rve_free(rve_t* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  prof_resolve(h);
+  for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
+  h->ev_free.clear();
+  free_all(h);
+  delete h;
+}
+
+int rve_set_options(rve_t* h, const rve_solver_options* o) {
+  if (!h || !o) return RVE_ERR_ARG;
+  if (!(o->tol_stag > 0) || !(o->tol_newton > 0) || !(o->cg_rtol > 0) || !(o->pcg_rtol > 0)) return RVE_ERR_ARG;
+  if (o->max_stag < 1 || o->max_newton < 0 || o->max_cg < 1 || o->max_pcg < 1 || o->min_stag < 1 ||
+      o->check_every < 1)
+    return RVE_ERR_ARG;
+  h->opt = *o;
+  return RVE_OK;
+}
+
+int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase_params* params,
+                   const double* ell) {
+  if (!h || !phase || !params) return RVE_ERR_ARG;
+  if (n_phases < 1 || n_phases > kMaxPhases) return RVE_ERR_ARG;
+  if (h->J > 0 && !ell) return RVE_ERR_ARG;
+  const size_t V = (size_t)h->g.V;
+  std::vector<uint8_t> hp;
+  try {
+    hp.resize(V);
+  } catch (...) {
+    return RVE_ERR_OOM;
+  }
+  if (is_device_ptr(phase)) {
+    CK(cudaMemcpy(hp.data(), phase, V, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(hp.data(), phase, V);
+  }
+  std::vector<long long> count(n_phases, 0);
+  for (size_t v = 0; v < V; v++) {
+    if (hp[v] >= n_phases) return RVE_ERR_ARG;
+    count[hp[v]]++;
+  }
+  PhaseTable pt{};
+  pt.n_phases = n_phases;
+  for (int q = 0; q < n_phases; q++) {
+    const rve_phase_params& P = params[q];
+    if (!(P.E > 0.0) || !(P.nu > -1.0 && P.nu < 0.5)) return RVE_ERR_ARG;
+    if (P.damage_law != 0 && P.damage_law != 1) return RVE_ERR_ARG;
+    if (P.nonlocal_var < -1 || P.nonlocal_var >= h->J) return RVE_ERR_ARG;
+    if (P.damage_law == 1) {
+      if (!(P.sigma_y > 0.0) || !(P.H >= 0.0)) return RVE_ERR_ARG;
+      if (P.nonlocal_var >= 0 && (!(P.eps_R > P.eps_C) || !(P.D_max >= 0.0 && P.D_max < 1.0)))
+        return RVE_ERR_ARG;
+    }
+    PhaseDev& d = pt.p[q];
+    d.K = P.E / (3.0 * (1.0 - 2.0 * P.nu));
+    d.mu = P.E / (2.0 * (1.0 + P.nu));
+    d.sigma_y = P.sigma_y;
+    d.H = P.H;
+    d.eps_C = P.eps_C;
+    d.eps_R = P.eps_R;
+    d.D_max = P.D_max;
+    d.law = P.damage_law;
+    d.var = P.damage_law == 1 ? P.nonlocal_var : -1;
+  }
+  for (int j = 0; j < h->J; j++) {
+    double m = 0.0;
+    for (int q = 0; q < n_phases; q++) {
+      const double l = ell[j * n_phases + q];
+      if (!(l >= 0.0)) return RVE_ERR_ARG;
+      pt.ell2[j][q] = l * l;
+      pt.ell2f[j][q] = (float)(l * l);
+      m += (double)count[q] * l * l;
+    }
+    h->ell2_mean[j] = m / (double)V;
+  }
+  h->pt_host = pt;
+  h->n_phases = n_phases;
+  CK(cudaMemcpy(h->phase, hp.data(), V, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->pt_dev, &pt, sizeof(PhaseTable), cudaMemcpyHostToDevice));
+  int s = upload_ell2(h);
+  if (s) return s;
+  s = reset_state(h);
+  if (s) return s;
+  h->phases_set = true;
+  return RVE_OK;
+}
+
+int rve_set_load_path(rve_t* h, int n_incr, const uint8_t strain_ctrl[6], const double* target) {
+  if (!h || !strain_ctrl || !target || n_incr < 1) return RVE_ERR_ARG;
+  for (int c = 0; c < 6; c++)
+    if (strain_ctrl[c] > 1) return RVE_ERR_ARG;
+  if (h->dim == 2) {
+    for (int c = 2; c <= 4; c++) {
+      if (!strain_ctrl[c]) return RVE_ERR_ARG;
+      for (int i = 0; i < n_incr; i++)
+        if (target[i * 6 + c] != 0.0) return RVE_ERR_ARG;
+    }
+  }
+  for (int i = 0; i < 6 * n_incr; i++)
+    if (!std::isfinite(target[i])) return RVE_ERR_ARG;
+  h->target.assign(target, target + 6 * (size_t)n_incr);
+  h->n_incr = n_incr;
+  h->n_done = 0;
+  for (int c = 0; c < 6; c++) h->ctrl[c] = strain_ctrl[c];
+  for (int c = 0; c < 6; c++) {
+    const double m = (c < h->g.nc) ? (strain_ctrl[h->g.cmap[c]] ? 0.0 : 1.0) : 0.0;
+    h->smask_d[c] = m;
+    h->smask_f[c] = (float)m;
+  }
+  h->path_set = true;
+  return RVE_OK;
+}
+
+int rve_step_increment(rve_t* h, rve_step_info* info) {
+  if (!h) return RVE_ERR_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!h->phases_set || !h->path_set) return RVE_ERR_STATE;
+  if (h->n_done >= h->n_incr) return RVE_ERR_LOAD_PATH_END;
+  try {
+    return h->prec == RVE_MIXED ? Alg<float>::step(h, info) : Alg<double>::step(h, info);
+  } catch (...) {
+    return RVE_ERR_OOM;
+  }
+}
+
+int rve_homogenized_stress(const rve_t* h, double sigma[6]) {
+  if (!h || !sigma) return RVE_ERR_ARG;
+  for (int c = 0; c < 6; c++) sigma[c] = h->sig_mean[c];
+  return RVE_OK;
+}
+
+int rve_homogenized_strain(const rve_t* h, double eps[6]) {
+  if (!h || !eps) return RVE_ERR_ARG;
+  for (int c = 0; c < 6; c++) eps[c] = h->eps_mean[c];
+  return RVE_OK;
+}
+
+int rve_get_sizes(const rve_t* h, long long* nv, int* nc, int* J) {
+  if (!h) return RVE_ERR_ARG;
+  if (nv) *nv = h->g.V;
+  if (nc) *nc = h->g.nc;
+  if (J) *J = h->J;
+  return RVE_OK;
+}
+
+int rve_get_field(const rve_t* h, int which, double* dst, size_t n) {
+  if (!h || !dst) return RVE_ERR_ARG;
+  const size_t V = (size_t)h->g.V;
+  const double* src = nullptr;
+  size_t cnt = 0;
+  switch (which) {
+    case 0: src = h->eps_conv; cnt = h->g.nc * V; break;
+    case 1: src = h->sigma; cnt = 6 * V; break;
+    case 2: src = h->D; cnt = V; break;
+    case 3: src = h->abar_n; cnt = (size_t)h->J * V; break;
+    case 4: src = h->ep_n; cnt = V; break;
+    case 5: src = h->epsp_n; cnt = 6 * V; break;
+    default: return RVE_ERR_ARG;
+  }
+  if (n < cnt) return RVE_ERR_ARG;
+  if (cnt == 0) return RVE_OK;
+  CK(cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RVE_OK;
+}
+
+int rve_op_return_map(rve_t* h, const double* eps, const double* epsp_n, const double* ep_n,
+                      const double* abar, double* sigma, double* epsp, double* ep, double* D,
+                      double* alpha) {
+  if (!h || !eps || !epsp_n || !ep_n || !sigma || !epsp || !ep || !D) return RVE_ERR_ARG;
+  if (h->J > 0 && (!abar || !alpha)) return RVE_ERR_ARG;
+  if (!h->phases_set) return RVE_ERR_STATE;
+  double* alpha_use = alpha ? alpha : h->alpha;
+  const double* abar_use = abar ? abar : h->abar_n;
+  if (h->prec == RVE_MIXED)
+    Ops<float>::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, eps, epsp_n, ep_n, abar_use, sigma,
+                           epsp, ep, D, alpha_use, (float*)h->desc, h->part);
+  else
+    Ops<double>::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, eps, epsp_n, ep_n, abar_use,
+                            sigma, epsp, ep, D, alpha_use, (double*)h->desc, h->part);
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
+  return RVE_OK;
+}
+
+int rve_op_tangent_apply(rve_t* h, const double* p, double* tau) {
+  if (!h || !p || !tau) return RVE_ERR_ARG;
+  if (h->prec == RVE_MIXED)
+    Ops<float>::tangent_apply64(h->g, h->lc, h->st, (const float*)h->desc, p, tau);
+  else
+    Ops<double>::tangent_apply64(h->g, h->lc, h->st, (const double*)h->desc, p, tau);
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
+  return RVE_OK;
+}
+
+int rve_op_apply_gamma(rve_t* h, const double* tau, double* out) {
+  if (!h || !tau || !out) return RVE_ERR_ARG;
+  return h->prec == RVE_MIXED ? Alg<float>::op_apply_gamma(h, tau, out) : Alg<double>::op_apply_gamma(h, tau, out);
+}
+
+int rve_op_matvec(rve_t* h, const double* p, double* Ap) {
+  if (!h || !p || !Ap) return RVE_ERR_ARG;
+  return h->prec == RVE_MIXED ? Alg<float>::op_matvec(h, p, Ap) : Alg<double>::op_matvec(h, p, Ap);
+}
+
+int rve_op_cg(rve_t* h, const double* b, double* x, double rtol, int maxit, int* iters) {
+  if (!h || !b || !x || !(rtol > 0) || maxit < 1) return RVE_ERR_ARG;
+  return h->prec == RVE_MIXED ? Alg<float>::op_cg(h, b, x, rtol, maxit, iters)
+                              : Alg<double>::op_cg(h, b, x, rtol, maxit, iters);
+}
+
+int rve_op_helmholtz_apply(rve_t* h, int j, const double* a, double* out) {
+  if (!h || !a || !out || j < 0 || j >= h->J) return RVE_ERR_ARG;
+  if (!h->phases_set) return RVE_ERR_STATE;
+  return h->prec == RVE_MIXED ? Alg<float>::op_helm_apply(h, j, a, out) : Alg<double>::op_helm_apply(h, j, a, out);
+}
+
+int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, double rtol, int maxit,
+                           int* iters) {
+  if (!h || !alpha || !abar || j < 0 || j >= h->J || !(rtol > 0) || maxit < 1) return RVE_ERR_ARG;
+  if (!h->phases_set) return RVE_ERR_STATE;
+  return h->prec == RVE_MIXED ? Alg<float>::op_helm_solve(h, j, alpha, abar, rtol, maxit, iters)
+                              : Alg<double>::op_helm_solve(h, j, alpha, abar, rtol, maxit, iters);
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Shared device/host definitions of the GB300 non-local damage RVE library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rvk {
+
+constexpr int kThreads = 256;           // threads per CTA of every kernel here
+constexpr int kMaxPhases = 8;
+constexpr int kMaxVars = 4;             // non-local variables J
+constexpr int kMaxRadixStages = 16;
+
+template <typename R> struct C2 { R x, y; };
+
+template <typename R> __host__ __device__ __forceinline__ C2<R> mk(R a, R b) { C2<R> c; c.x = a; c.y = b; return c; }
+template <typename R> __device__ __forceinline__ C2<R> operator+(C2<R> a, C2<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ C2<R> operator-(C2<R> a, C2<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R> __device__ __forceinline__ C2<R> cscale(C2<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+template <typename R> __device__ __forceinline__ C2<R> conj_(C2<R> a) { return mk<R>(a.x, -a.y); }
+// multiply by sign * i
+template <typename R, int SIGN> __device__ __forceinline__ C2<R> mul_si(C2<R> a) {
+  return SIGN > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
+}
+
+// Radix plan of a 1D FFT of length N (product of radices 2, 3, 4, 5, 8).
+struct FftPlan {
+  int N;
+  int nst;
+  int radix[kMaxRadixStages];
+};
+
+// Per-phase constitutive constants (device copy of rve_phase_params).
+struct PhaseDev {
+  double K, mu, sigma_y, H;
+  double eps_C, eps_R, D_max;
+  int law;    // 0 elastic, 1 J2 + Lemaitre damage
+  int var;    // non-local variable fed / read, -1 none
+};
+
+struct PhaseTable {
+  PhaseDev p[kMaxPhases];
+  int n_phases;
+  float ell2f[kMaxVars][kMaxPhases];
+  double ell2[kMaxVars][kMaxPhases];
+};
+
+// Scalars of one Krylov solve, kept on the device between kernels.
+struct KrylovCtl {
+  double rr;       // (r, r) for CG / (r, M r) for PCG
+  double rnorm2;   // (r, r)
+  double b2;       // (b, b)
+  double pAp;
+  double alpha, beta;
+  double rtol2;
+  // status: 0 running, 1 converged, 2 budget, 3 non-finite, 4 stopped at
+  // the round-off floor ((p, Ap) <= 0)
+  int iter, maxit, done, status;
+};
+
+__host__ __device__ inline int grid_linear_block() {
+#ifdef __CUDA_ARCH__
+  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+#else
+  return 0;
+#endif
+}
+
+// Deterministic block sum of NS doubles (fixed tree, fixed thread order).
+template <int NS>
+__device__ __forceinline__ void block_sum_store(double (&v)[NS], double* part, int nblk_stride) {
+  __shared__ double red[kThreads / 32][NS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    double x = v[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][s] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) acc += red[w][threadIdx.x];
+    part[threadIdx.x * nblk_stride + grid_linear_block()] = acc;
+  }
+}
+
+// Block max of NS non-negative doubles.
+template <int NS>
+__device__ __forceinline__ void block_max_store(double (&v)[NS], double* part, int nblk_stride) {
+  __shared__ double red[kThreads / 32][NS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    double x = v[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if (lane == 0) red[warp][s] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) acc = fmax(acc, red[w][threadIdx.x]);
+    part[threadIdx.x * nblk_stride + grid_linear_block()] = acc;
+  }
+}
+
+}  // namespace rvk

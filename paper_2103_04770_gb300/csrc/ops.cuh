@@ -1,0 +1,938 @@
+// Device operators of the non-local damage RVE library (templated on the
+// precision R of the spectral and Krylov data).  See ops.h for the layout.
+//
+// Spectral sweeps (Section 3.2, Eq. eqdiscrete2 and Algorithm 2) are split
+// into passes that each make one HBM round trip:
+//   x1 pass   : R2C / C2R along the contiguous axis (half-length complex FFT
+//               plus split), fused with the per-voxel prologue (tangent
+//               C_T : p, residual source) or epilogue (store, dots, l^2)
+//   y pass    : plain transform along x2 (3D only)
+//   last pass : transform along the last axis fused with the pointwise
+//               Fourier operator (modified projection G*, Helmholtz symbol
+//               k, conj(k), preconditioner) and, for G*, the inverse.
+#pragma once
+#include <math.h>
+
+#include "fft.cuh"
+#include "ops.h"
+
+namespace rvk {
+
+template <typename R> struct StridedE;
+template <> struct StridedE<float> { static constexpr int E = 8; };
+template <> struct StridedE<double> { static constexpr int E = 4; };
+constexpr int kXE = 16;
+
+struct Mask6 { float m[6]; };
+
+__device__ __forceinline__ long long lmin_(long long a, long long b) { return a < b ? a : b; }
+
+template <typename K>
+static void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------- Fourier symbols
+// Rotated-scheme modified frequency (Willot): k_j = i e^{i phi} a_j with
+// a_j = (2/h_j) sin(theta_j/2) prod_{m != j} cos(theta_m/2) and
+// e^{i phi} = prod_m (cos(theta_m/2) + i sin(theta_m/2)).
+template <typename R>
+__device__ __forceinline__ void symbol(const Geo& g, const Tables<R>& t, int m0, int m1, int m2,
+                                       R a[3], C2<R>& ph) {
+  const R s0 = t.s[0][m0], c0 = t.c[0][m0];
+  const R s1 = t.s[1][m1], c1 = t.c[1][m1];
+  if (g.d == 3) {
+    const R s2 = t.s[2][m2], c2 = t.c[2][m2];
+    a[0] = t.two_over_h[0] * s0 * c1 * c2;
+    a[1] = t.two_over_h[1] * s1 * c0 * c2;
+    a[2] = t.two_over_h[2] * s2 * c0 * c1;
+    ph = cmul(cmul(mk<R>(c0, s0), mk<R>(c1, s1)), mk<R>(c2, s2));
+  } else {
+    a[0] = t.two_over_h[0] * s0 * c1;
+    a[1] = t.two_over_h[1] * s1 * c0;
+    a[2] = R(0);
+    ph = cmul(mk<R>(c0, s0), mk<R>(c1, s1));
+  }
+}
+
+// Orthogonal projection onto compatible symmetric strains at one mode
+// (Mandel components, real direction n):  G(T) = n(x)Tn + Tn(x)n - (nTn) n(x)n.
+template <typename R>
+__device__ __forceinline__ void gamma_mode(int d, const R n[3], C2<R>* t) {
+  const R is2 = R(0.70710678118654752440);
+  const R s2 = R(1.41421356237309504880);
+  if (d == 3) {
+    C2<R> v0 = cscale(t[0], n[0]) + cscale(cscale(t[5], n[1]) + cscale(t[4], n[2]), is2);
+    C2<R> v1 = cscale(cscale(t[5], n[0]) + cscale(t[3], n[2]), is2) + cscale(t[1], n[1]);
+    C2<R> v2 = cscale(cscale(t[4], n[0]) + cscale(t[3], n[1]), is2) + cscale(t[2], n[2]);
+    C2<R> nt = cscale(v0, n[0]) + cscale(v1, n[1]) + cscale(v2, n[2]);
+    t[0] = cscale(v0, R(2) * n[0]) - cscale(nt, n[0] * n[0]);
+    t[1] = cscale(v1, R(2) * n[1]) - cscale(nt, n[1] * n[1]);
+    t[2] = cscale(v2, R(2) * n[2]) - cscale(nt, n[2] * n[2]);
+    t[3] = cscale(cscale(v2, n[1]) + cscale(v1, n[2]) - cscale(nt, n[1] * n[2]), s2);
+    t[4] = cscale(cscale(v2, n[0]) + cscale(v0, n[2]) - cscale(nt, n[0] * n[2]), s2);
+    t[5] = cscale(cscale(v1, n[0]) + cscale(v0, n[1]) - cscale(nt, n[0] * n[1]), s2);
+  } else {
+    C2<R> v0 = cscale(t[0], n[0]) + cscale(t[2], n[1] * is2);
+    C2<R> v1 = cscale(t[2], n[0] * is2) + cscale(t[1], n[1]);
+    C2<R> nt = cscale(v0, n[0]) + cscale(v1, n[1]);
+    t[0] = cscale(v0, R(2) * n[0]) - cscale(nt, n[0] * n[0]);
+    t[1] = cscale(v1, R(2) * n[1]) - cscale(nt, n[1] * n[1]);
+    t[2] = cscale(cscale(v1, n[0]) + cscale(v0, n[1]) - cscale(nt, n[0] * n[1]), s2);
+  }
+}
+
+// ================================================================ x1 passes
+template <typename R, class PRO>
+__global__ void __launch_bounds__(kThreads)
+k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, int nc, int nrows,
+       PRO pro, const KrylovCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
+  R* rbuf = reinterpret_cast<R*>(tws + g.n1);
+  C2<R>* cbuf = reinterpret_cast<C2<R>*>(rbuf);
+  const long long row0 = (long long)blockIdx.x * nrows;
+  const int rows = (int)lmin_(nrows, g.nlines - row0);
+  for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
+  pro.begin(ctl);
+  const int nvox = rows * g.n1;
+  for (int e = threadIdx.x; e < nvox; e += kThreads) {
+    const int r = e / g.n1, x = e - r * g.n1;
+    const long long v = (row0 + r) * g.n1 + x;
+    R val[6];
+    pro(v, val);
+    for (int c = 0; c < nc; c++) rbuf[(r * nc + c) * g.n1 + x] = val[c];
+  }
+  __syncthreads();
+  fft_lines<R, kXE, -1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
+  const int nout = rows * nc * g.P1;
+  for (int e = threadIdx.x; e < nout; e += kThreads) {
+    const int l = e / g.P1, k = e - l * g.P1;
+    const int r = l / nc, c = l - r * nc;
+    const C2<R> zk = cbuf[l * g.M + (k == g.M ? 0 : k)];
+    const C2<R> zm = cbuf[l * g.M + (k == 0 ? 0 : g.M - k)];
+    const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+    const C2<R> Ok = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+    S[c * g.sstride + (row0 + r) * g.ps + k] = Ek + cmul(tws[k], Ok);
+  }
+}
+
+// Split of the half spectrum back to the half-length complex sequence.
+template <typename R>
+__device__ __forceinline__ void xinv_pre(const Geo& g, const C2<R>* __restrict__ S, long long row0,
+                                         int rows, int nc, const C2<R>* tws, C2<R>* cbuf) {
+  const int nin = rows * nc * g.M;
+  for (int e = threadIdx.x; e < nin; e += kThreads) {
+    const int l = e / g.M, k = e - l * g.M;
+    const int r = l / nc, c = l - r * nc;
+    const C2<R>* row = S + c * g.sstride + (row0 + r) * g.ps;
+    const C2<R> xk = row[k], xm = row[g.M - k];
+    const C2<R> E = mk<R>(R(0.5) * (xk.x + xm.x), R(0.5) * (xk.y - xm.y));
+    const C2<R> Dd = mk<R>(R(0.5) * (xk.x - xm.x), R(0.5) * (xk.y + xm.y));
+    const C2<R> O = cmul(Dd, conj_(tws[k]));
+    cbuf[l * g.M + k] = mk<R>(E.x - O.y, E.y + O.x);
+  }
+}
+
+template <typename R, class EPI, int NS>
+__global__ void __launch_bounds__(kThreads)
+k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict__ S, int nc,
+       int nrows, R scale, EPI epi, double* __restrict__ part, int pstride,
+       const KrylovCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
+  R* rbuf = reinterpret_cast<R*>(tws + g.n1);
+  C2<R>* cbuf = reinterpret_cast<C2<R>*>(rbuf);
+  const long long row0 = (long long)blockIdx.x * nrows;
+  const int rows = (int)lmin_(nrows, g.nlines - row0);
+  for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
+  __syncthreads();
+  xinv_pre(g, S, row0, rows, nc, tws, cbuf);
+  __syncthreads();
+  fft_lines<R, kXE, +1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
+  double acc[NS > 0 ? NS : 1];
+#pragma unroll
+  for (int s = 0; s < (NS > 0 ? NS : 1); s++) acc[s] = 0.0;
+  epi.begin(ctl);
+  const int nvox = rows * g.n1;
+  for (int e = threadIdx.x; e < nvox; e += kThreads) {
+    const int r = e / g.n1, x = e - r * g.n1;
+    const long long v = (row0 + r) * g.n1 + x;
+    R val[6];
+    for (int c = 0; c < nc; c++) val[c] = rbuf[(r * nc + c) * g.n1 + x] * scale;
+    epi(v, val, acc);
+  }
+  if (NS > 0) block_sum_store<(NS > 0 ? NS : 1)>(acc, part, pstride);
+}
+
+// C2R -> l^2(x) * scale -> R2C of the d gradient components (Algorithm 2, GC).
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, int nc, int nrows,
+       R scale, const uint8_t* __restrict__ phase, const R* __restrict__ ell2,
+       const KrylovCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
+  R* rbuf = reinterpret_cast<R*>(tws + g.n1);
+  C2<R>* cbuf = reinterpret_cast<C2<R>*>(rbuf);
+  const long long row0 = (long long)blockIdx.x * nrows;
+  const int rows = (int)lmin_(nrows, g.nlines - row0);
+  for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
+  __syncthreads();
+  xinv_pre(g, W, row0, rows, nc, tws, cbuf);
+  __syncthreads();
+  fft_lines<R, kXE, +1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
+  const int nvox = rows * g.n1;
+  for (int e = threadIdx.x; e < nvox; e += kThreads) {
+    const int r = e / g.n1, x = e - r * g.n1;
+    const long long v = (row0 + r) * g.n1 + x;
+    const R w = ell2[phase[v]] * scale;
+    for (int c = 0; c < nc; c++) rbuf[(r * nc + c) * g.n1 + x] *= w;
+  }
+  __syncthreads();
+  fft_lines<R, kXE, -1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
+  const int nout = rows * nc * g.P1;
+  for (int e = threadIdx.x; e < nout; e += kThreads) {
+    const int l = e / g.P1, k = e - l * g.P1;
+    const int r = l / nc, c = l - r * nc;
+    const C2<R> zk = cbuf[l * g.M + (k == g.M ? 0 : k)];
+    const C2<R> zm = cbuf[l * g.M + (k == 0 ? 0 : g.M - k)];
+    const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+    const C2<R> Ok = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+    W[c * g.sstride + (row0 + r) * g.ps + k] = Ek + cmul(tws[k], Ok);
+  }
+}
+
+// ------------------------------------------------------ x1 prologues / epilogues
+// tau = C_T : p with the compact tangent descriptor
+//   desc = [c1, c2, m_0 .. m_{nc-1}],  tau = c1 tr(p) 1 + c2 dev(p) - m (m . p)
+// (c1 = (1-D) K, c2 = (1-D) 2 mu theta, m = sqrt((1-D) 2 mu thetabar) nhat).
+// Inside CG the direction is refreshed first: p <- r (iter 0) or r + beta p.
+template <typename R>
+struct ProTangent {
+  R* p;
+  const R* r;
+  const R* desc;
+  long long V;
+  int nc, nnormal;
+  int update;
+  R beta;
+  bool first;
+  __device__ void begin(const KrylovCtl* ctl) {
+    if (ctl) { first = ctl->iter == 0; beta = (R)ctl->beta; }
+  }
+  __device__ __forceinline__ void operator()(long long v, R* out) const {
+    R pv[6];
+    if (update) {
+      for (int c = 0; c < nc; c++) {
+        const R rv = r[c * V + v];
+        pv[c] = first ? rv : rv + beta * p[c * V + v];
+        p[c * V + v] = pv[c];
+      }
+    } else {
+      for (int c = 0; c < nc; c++) pv[c] = p[c * V + v];
+    }
+    const R c1 = desc[v], c2 = desc[V + v];
+    R tr = R(0), mp = R(0);
+    for (int c = 0; c < nnormal; c++) tr += pv[c];
+    for (int c = 0; c < nc; c++) mp += desc[(2 + c) * V + v] * pv[c];
+    const R third = tr * R(1.0 / 3.0);
+    for (int c = 0; c < nc; c++) {
+      R o = c2 * pv[c] - desc[(2 + c) * V + v] * mp;
+      if (c < nnormal) o += c1 * tr - c2 * third;
+      out[c] = o;
+    }
+  }
+};
+
+// tau_c = f[map[c]][v] - mean[c]  (FP64 source fields)
+template <typename R>
+struct ProField64 {
+  const double* f;
+  const double* mean;   // device, may be null
+  long long V;
+  int nc;
+  int map[6];
+  __device__ void begin(const KrylovCtl*) {}
+  __device__ __forceinline__ void operator()(long long v, R* out) const {
+    for (int c = 0; c < nc; c++) {
+      double x = f[map[c] * V + v];
+      if (mean) x -= mean[map[c]];
+      out[c] = (R)x;
+    }
+  }
+};
+
+template <typename R>
+struct EpiMatvec {       // Ap = val; acc0 += p . Ap
+  R* Ap;
+  const R* p;
+  long long V;
+  int nc;
+  __device__ void begin(const KrylovCtl*) {}
+  __device__ __forceinline__ void operator()(long long v, const R* val, double* acc) const {
+    for (int c = 0; c < nc; c++) {
+      Ap[c * V + v] = val[c];
+      acc[0] += (double)p[c * V + v] * (double)val[c];
+    }
+  }
+};
+
+template <typename R>
+struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
+  R* b;
+  const double* mean_sig;   // full Mandel (6)
+  double mask[6];
+  double sbar[6];
+  int map[6];
+  long long V;
+  int nc;
+  double dc[6];
+  __device__ void begin(const KrylovCtl*) {
+    for (int c = 0; c < nc; c++) dc[c] = mask[c] * (mean_sig[map[c]] - sbar[c]);
+  }
+  __device__ __forceinline__ void operator()(long long v, const R* val, double* acc) const {
+    for (int c = 0; c < nc; c++) {
+      const double bv = -((double)val[c] + dc[c]);
+      const R br = (R)bv;
+      b[c * V + v] = br;
+      acc[0] += (double)br * (double)br;
+    }
+  }
+};
+
+template <typename R>
+struct EpiStore64 {
+  double* out;
+  long long V;
+  int nc;
+  __device__ void begin(const KrylovCtl*) {}
+  __device__ __forceinline__ void operator()(long long v, const R* val, double*) const {
+    for (int c = 0; c < nc; c++) out[c * V + v] = (double)val[c];
+  }
+};
+
+// ============================================================ strided passes
+template <typename R>
+struct StrideInfo { long long astride, ostride; int N; };
+
+template <typename R>
+static StrideInfo<R> stride_of(const Geo& g, int axis) {
+  StrideInfo<R> s;
+  if (axis == 1) { s.astride = g.ps; s.ostride = (long long)g.ps * g.n2; s.N = g.n2; }
+  else { s.astride = (long long)g.ps * g.n2; s.ostride = g.ps; s.N = g.n3; }
+  return s;
+}
+
+template <typename R, int SIGN>
+__global__ void __launch_bounds__(kThreads)
+k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
+                long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  constexpr int E = StridedE<R>::E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = pl.N;
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
+  C2<R>* buf = tws + N;
+  const int q0 = blockIdx.x * tx;
+  const int cols = min(tx, g.P1 - q0);
+  C2<R>* base = S + blockIdx.z * g.sstride + blockIdx.y * ostride + q0;
+  for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
+  for (int e = threadIdx.x; e < N * tx; e += kThreads) {
+    const int n = e / tx, col = e - n * tx;
+    if (col < cols) buf[e] = base[n * astride + col];
+  }
+  __syncthreads();
+  fft_lines<R, E, SIGN>(buf, pl, cols, tx, 1, false, tws, 1);
+  for (int e = threadIdx.x; e < N * tx; e += kThreads) {
+    const int n = e / tx, col = e - n * tx;
+    if (col < cols) base[n * astride + col] = buf[e];
+  }
+}
+
+// mode indices of element (n, col) of a last-axis tile
+__device__ __forceinline__ void last_modes(const Geo& g, int q0, int col, int n, int& m0, int& m1,
+                                           int& m2) {
+  m0 = q0 + col;
+  if (g.d == 3) { m1 = blockIdx.y; m2 = n; }
+  else { m1 = n; m2 = 0; }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
+        long long astride, long long ostride, Mask6 mask, int dc_mode,
+        const KrylovCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  constexpr int E = StridedE<R>::E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = pl.N, nc = g.nc;
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
+  C2<R>* buf = tws + N;
+  const int q0 = blockIdx.x * tx;
+  const int cols = min(tx, g.P1 - q0);
+  C2<R>* base = S + blockIdx.y * ostride + q0;
+  const int tile = N * tx;
+  for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
+  for (int e = threadIdx.x; e < nc * tile; e += kThreads) {
+    const int c = e / tile, rem = e - c * tile;
+    const int n = rem / tx, col = rem - n * tx;
+    if (col < cols) buf[e] = base[c * g.sstride + n * astride + col];
+  }
+  __syncthreads();
+  for (int c = 0; c < nc; c++) fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  for (int e = threadIdx.x; e < tile; e += kThreads) {
+    const int n = e / tx, col = e - n * tx;
+    if (col >= cols) continue;
+    int m0, m1, m2;
+    last_modes(g, q0, col, n, m0, m1, m2);
+    R a[3];
+    C2<R> ph;
+    symbol(g, t, m0, m1, m2, a, ph);
+    const R a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    C2<R> tv[6];
+    for (int c = 0; c < nc; c++) tv[c] = buf[c * tile + e];
+    if (a2 > R(0)) {
+      const R inv = R(1) / sqrt(a2);
+      R nv[3] = {a[0] * inv, a[1] * inv, a[2] * inv};
+      gamma_mode<R>(g.d, nv, tv);
+    } else {
+      const bool dc = (m0 == 0) && (m1 == 0) && (m2 == 0);
+      for (int c = 0; c < nc; c++) tv[c] = (dc && !dc_mode) ? cscale(tv[c], (R)mask.m[c]) : mk<R>(0, 0);
+    }
+    for (int c = 0; c < nc; c++) buf[c * tile + e] = tv[c];
+  }
+  __syncthreads();
+  for (int c = 0; c < nc; c++) fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  for (int e = threadIdx.x; e < nc * tile; e += kThreads) {
+    const int c = e / tile, rem = e - c * tile;
+    const int n = rem / tx, col = rem - n * tx;
+    if (col < cols) base[c * g.sstride + n * astride + col] = buf[e];
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
+  return (q1 == 0 || 2 * q1 == g.n1) ? R(1) : R(2);
+}
+
+// Helmholtz: p <- M r + beta p (M = 1/(1 + <l^2>|k|^2)); W_j = k_j p; inverse
+// transform along the last axis.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
+         C2<R>* __restrict__ p, const C2<R>* __restrict__ r, int tx, long long astride,
+         long long ostride, R ell2m, const KrylovCtl* __restrict__ ctl, int raw) {
+  if (ctl && ctl->done) return;
+  constexpr int E = StridedE<R>::E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = pl.N, d = g.d;
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
+  C2<R>* buf = tws + N;
+  const int q0 = blockIdx.x * tx;
+  const int cols = min(tx, g.P1 - q0);
+  const long long off = blockIdx.y * ostride + q0;
+  const int tile = N * tx;
+  const bool first = ctl ? ctl->iter == 0 : true;
+  const R beta = ctl ? (R)ctl->beta : R(0);
+  for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
+  for (int e = threadIdx.x; e < tile; e += kThreads) {
+    const int n = e / tx, col = e - n * tx;
+    if (col >= cols) continue;
+    int m0, m1, m2;
+    last_modes(g, q0, col, n, m0, m1, m2);
+    R a[3];
+    C2<R> ph;
+    symbol(g, t, m0, m1, m2, a, ph);
+    const R Mk = R(1) / (R(1) + ell2m * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+    const long long idx = off + n * astride + col;
+    C2<R> pn;
+    if (raw) {
+      pn = r[idx];
+    } else {
+      pn = cscale(r[idx], Mk);
+      if (!first) pn = pn + cscale(p[idx], beta);
+      p[idx] = pn;
+    }
+    const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
+    for (int j = 0; j < d; j++) buf[j * tile + e] = cscale(ipp, a[j]);
+  }
+  __syncthreads();
+  for (int j = 0; j < d; j++) fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  for (int e = threadIdx.x; e < d * tile; e += kThreads) {
+    const int j = e / tile, rem = e - j * tile;
+    const int n = rem / tx, col = rem - n * tx;
+    if (col < cols) W[j * g.sstride + off + n * astride + col] = buf[e];
+  }
+}
+
+// Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
+// partial Hermitian-weighted (p, y).
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C2<R>* __restrict__ W,
+           const C2<R>* __restrict__ p, C2<R>* __restrict__ y, int tx, long long astride,
+           long long ostride, double* __restrict__ part, int pstride,
+           const KrylovCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  constexpr int E = StridedE<R>::E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = pl.N, d = g.d;
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
+  C2<R>* buf = tws + N;
+  const int q0 = blockIdx.x * tx;
+  const int cols = min(tx, g.P1 - q0);
+  const long long off = blockIdx.y * ostride + q0;
+  const int tile = N * tx;
+  for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
+  for (int e = threadIdx.x; e < d * tile; e += kThreads) {
+    const int j = e / tile, rem = e - j * tile;
+    const int n = rem / tx, col = rem - n * tx;
+    if (col < cols) buf[e] = W[j * g.sstride + off + n * astride + col];
+  }
+  __syncthreads();
+  for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  double acc[1] = {0.0};
+  for (int e = threadIdx.x; e < tile; e += kThreads) {
+    const int n = e / tx, col = e - n * tx;
+    if (col >= cols) continue;
+    int m0, m1, m2;
+    last_modes(g, q0, col, n, m0, m1, m2);
+    R a[3];
+    C2<R> ph;
+    symbol(g, t, m0, m1, m2, a, ph);
+    C2<R> s = mk<R>(0, 0);
+    for (int j = 0; j < d; j++) s = s + cscale(buf[j * tile + e], a[j]);
+    // conj(k_j) = -i e^{-i phi} a_j
+    const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
+    const long long idx = off + n * astride + col;
+    const C2<R> pv = p[idx];
+    const C2<R> yv = pv + ks;
+    y[idx] = yv;
+    acc[0] += (double)q1_weight<R>(g, m0) * ((double)pv.x * (double)yv.x + (double)pv.y * (double)yv.y);
+  }
+  block_sum_store<1>(acc, part, pstride);
+}
+
+// ============================================================ Krylov vectors
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_cg_init(long long n, R* __restrict__ x, const R* __restrict__ r, double* __restrict__ part, int pstride) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    x[i] = R(0);
+    const double rv = r[i];
+    acc[0] += rv * rv;
+  }
+  block_sum_store<1>(acc, part, pstride);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_cg_update(long long n, R* __restrict__ x, R* __restrict__ r, const R* __restrict__ p,
+            const R* __restrict__ Ap, double* __restrict__ part, int pstride,
+            const KrylovCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  const R alpha = (R)ctl->alpha;
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    x[i] += alpha * p[i];
+    const R rn = r[i] - alpha * Ap[i];
+    r[i] = rn;
+    acc[0] += (double)rn * (double)rn;
+  }
+  block_sum_store<1>(acc, part, pstride);
+}
+
+template <typename R>
+__device__ __forceinline__ R precond_at(const Geo& g, const Tables<R>& t, long long e, R ell2m,
+                                        int& q1) {
+  const long long line = e / g.P1;
+  q1 = (int)(e - line * g.P1);
+  const int m1 = (int)(line % g.n2), m2 = (int)(line / g.n2);
+  R a[3];
+  C2<R> ph;
+  symbol(g, t, q1, m1, m2, a, ph);
+  return R(1) / (R(1) + ell2m * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pcg_init(Geo g, Tables<R> t, C2<R>* __restrict__ x, const C2<R>* __restrict__ r, R ell2m,
+           double* __restrict__ part, int pstride) {
+  double acc[2] = {0.0, 0.0};
+  const long long n = (long long)g.P1 * g.nlines;
+  for (long long e = blockIdx.x * (long long)kThreads + threadIdx.x; e < n; e += (long long)gridDim.x * kThreads) {
+    int q1;
+    const R Mk = precond_at(g, t, e, ell2m, q1);
+    const long long idx = (e / g.P1) * g.ps + q1;
+    x[idx] = mk<R>(0, 0);
+    const C2<R> rv = r[idx];
+    const double w = q1_weight<R>(g, q1);
+    const double rr = (double)rv.x * rv.x + (double)rv.y * rv.y;
+    acc[0] += w * rr;
+    acc[1] += w * (double)Mk * rr;
+  }
+  block_sum_store<2>(acc, part, pstride);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pcg_update(Geo g, Tables<R> t, C2<R>* __restrict__ x, C2<R>* __restrict__ r,
+             const C2<R>* __restrict__ p, const C2<R>* __restrict__ y, R ell2m,
+             double* __restrict__ part, int pstride, const KrylovCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  const R alpha = (R)ctl->alpha;
+  double acc[2] = {0.0, 0.0};
+  const long long n = (long long)g.P1 * g.nlines;
+  for (long long e = blockIdx.x * (long long)kThreads + threadIdx.x; e < n; e += (long long)gridDim.x * kThreads) {
+    int q1;
+    const R Mk = precond_at(g, t, e, ell2m, q1);
+    const long long idx = (e / g.P1) * g.ps + q1;
+    x[idx] = x[idx] + cscale(p[idx], alpha);
+    const C2<R> rn = r[idx] - cscale(y[idx], alpha);
+    r[idx] = rn;
+    const double w = q1_weight<R>(g, q1);
+    const double rr = (double)rn.x * rn.x + (double)rn.y * rn.y;
+    acc[0] += w * rr;
+    acc[1] += w * (double)Mk * rr;
+  }
+  block_sum_store<2>(acc, part, pstride);
+}
+
+// ============================================================ return map
+// Backward-Euler Lemaitre update (Appendix A.2; readings R8-R11) at every
+// voxel: radial return on the effective stress, D from the frozen non-local
+// variable, sigma = (1 - D) sigma_eff, consistent tangent descriptor.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __restrict__ phase,
+             const double* __restrict__ eps, const double* __restrict__ epsp_n,
+             const double* __restrict__ ep_n, const double* __restrict__ abar,
+             double* __restrict__ sigma, double* __restrict__ epsp, double* __restrict__ ep,
+             double* __restrict__ Dout, double* __restrict__ alpha, R* __restrict__ desc,
+             double* __restrict__ part, int pstride) {
+  const long long V = g.V;
+  const int nc = g.nc;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double dmx[1] = {0.0};
+  const double s23 = 0.81649658092772603273;   // sqrt(2/3)
+  for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
+    const PhaseDev P = pt->p[phase[v]];
+    double e[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < nc; c++) e[g.cmap[c]] = eps[c * V + v];
+    double pn[6];
+    for (int c = 0; c < 6; c++) { pn[c] = epsp_n[c * V + v]; e[c] -= pn[c]; }
+    const double tr = e[0] + e[1] + e[2];
+    double dev[6];
+    for (int c = 0; c < 6; c++) dev[c] = e[c] - (c < 3 ? tr / 3.0 : 0.0);
+    const double K = P.K, mu = P.mu;
+    double q = 0.0;
+    for (int c = 0; c < 6; c++) q += dev[c] * dev[c];
+    q = 2.0 * mu * sqrt(q);
+    const double epn = ep_n[v];
+    double dl = 0.0, theta = 1.0, thetab = 0.0, D = 0.0;
+    double nh[6] = {0, 0, 0, 0, 0, 0};
+    if (P.law == 1) {
+      const double f = q - s23 * (P.sigma_y + P.H * epn);
+      if (f > 0.0) {
+        dl = f / (2.0 * mu + 2.0 * P.H / 3.0);
+        for (int c = 0; c < 6; c++) nh[c] = 2.0 * mu * dev[c] / q;
+        theta = 1.0 - 2.0 * mu * dl / q;
+        thetab = 1.0 / (1.0 + P.H / (3.0 * mu)) - (1.0 - theta);
+      }
+      if (P.var >= 0) {
+        const double ab = abar[P.var * V + v];
+        D = (ab - P.eps_C) / (P.eps_R - P.eps_C);
+        D = D < 0.0 ? 0.0 : (D > P.D_max ? P.D_max : D);
+      }
+    }
+    const double om = 1.0 - D;
+    double sg[6];
+    for (int c = 0; c < 6; c++) {
+      const double seff = (c < 3 ? K * tr : 0.0) + 2.0 * mu * dev[c] - 2.0 * mu * dl * nh[c];
+      sg[c] = om * seff;
+      sigma[c * V + v] = sg[c];
+      epsp[c * V + v] = pn[c] + dl * nh[c];
+      acc[c] += sg[c];
+    }
+    const double epv = epn + s23 * dl;
+    ep[v] = epv;
+    Dout[v] = D;
+    for (int j = 0; j < J; j++) alpha[j * V + v] = (P.var == j) ? epv : 0.0;
+    acc[6] += D;
+    dmx[0] = fmax(dmx[0], D);
+    desc[v] = (R)(om * K);
+    desc[V + v] = (R)(om * 2.0 * mu * theta);
+    const double ms = sqrt(om * 2.0 * mu * thetab);
+    for (int c = 0; c < nc; c++) desc[(2 + c) * V + v] = (R)(ms * nh[g.cmap[c]]);
+  }
+  block_sum_store<7>(acc, part, pstride);
+  __syncthreads();
+  block_max_store<1>(dmx, part + 7 * (long long)pstride, pstride);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_tangent64(Geo g, const R* __restrict__ desc, const double* __restrict__ p, double* __restrict__ tau) {
+  const long long V = g.V;
+  const int nc = g.nc, nn = g.d == 3 ? 3 : 2;
+  for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
+    double pv[6], tr = 0.0, mp = 0.0;
+    for (int c = 0; c < nc; c++) pv[c] = p[c * V + v];
+    for (int c = 0; c < nn; c++) tr += pv[c];
+    for (int c = 0; c < nc; c++) mp += (double)desc[(2 + c) * V + v] * pv[c];
+    const double c1 = desc[v], c2 = desc[V + v];
+    for (int c = 0; c < nc; c++) {
+      double o = c2 * pv[c] - (double)desc[(2 + c) * V + v] * mp;
+      if (c < nn) o += c1 * tr - c2 * tr / 3.0;
+      tau[c * V + v] = o;
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_eps_update(Geo g, double* __restrict__ eps, const R* __restrict__ x, double* __restrict__ part,
+             int pstride) {
+  const long long V = g.V;
+  const int nc = g.nc;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  double mx[1] = {0.0};
+  for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
+    for (int c = 0; c < nc; c++) {
+      const double xv = x[c * V + v];
+      const double en = eps[c * V + v] + xv;
+      eps[c * V + v] = en;
+      acc[c] += en;
+      mx[0] = fmax(mx[0], fabs(xv));
+    }
+  }
+  block_sum_store<6>(acc, part, pstride);
+  __syncthreads();
+  block_max_store<1>(mx, part + 6 * (long long)pstride, pstride);
+}
+
+template <typename R>
+__global__ void k_to_r(long long n, const double* __restrict__ a, R* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) b[i] = (R)a[i];
+}
+template <typename R>
+__global__ void k_from_r(long long n, const R* __restrict__ a, double* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) b[i] = (double)a[i];
+}
+
+// ============================================================ launchers
+template <typename R>
+static size_t xsmem(const Geo& g, int nrows, int nc) {
+  return (size_t)g.n1 * sizeof(C2<R>) + (size_t)nrows * nc * g.n1 * sizeof(R);
+}
+static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrows - 1) / nrows); }
+
+template <typename R>
+void Ops<R>::xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
+                          const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl) {
+  ProTangent<R> pro;
+  pro.p = p; pro.r = r; pro.desc = desc; pro.V = g.V; pro.nc = g.nc;
+  pro.nnormal = g.d == 3 ? 3 : 2; pro.update = ctl != nullptr; pro.beta = R(0); pro.first = true;
+  const int nr = lc.nrows_c[g.nc];
+  const size_t sm = xsmem<R>(g, nr, g.nc);
+  auto k = k_xfwd<R, ProTangent<R>>;
+  set_smem(k, sm);
+  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, g.nc, nr, pro, ctl);
+}
+
+template <typename R>
+void Ops<R>::xfwd_field64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                          const double* f, int ncomp, const int* fmap, const double* mean_dev, C2<R>* S) {
+  ProField64<R> pro;
+  pro.f = f; pro.mean = mean_dev; pro.V = g.V; pro.nc = ncomp;
+  for (int c = 0; c < 6; c++) pro.map[c] = c < ncomp ? fmap[c] : 0;
+  const int nr = lc.nrows_c[ncomp];
+  const size_t sm = xsmem<R>(g, nr, ncomp);
+  auto k = k_xfwd<R, ProField64<R>>;
+  set_smem(k, sm);
+  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, ncomp, nr, pro, nullptr);
+}
+
+template <typename R>
+void Ops<R>::xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                         const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl) {
+  EpiMatvec<R> epi;
+  epi.Ap = Ap; epi.p = p; epi.V = g.V; epi.nc = g.nc;
+  const int nr = lc.nrows_c[g.nc];
+  const size_t sm = xsmem<R>(g, nr, g.nc);
+  auto k = k_xinv<R, EpiMatvec<R>, 1>;
+  set_smem(k, sm);
+  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, g.nc, nr, R(2.0 / (double)g.V), epi,
+                                        part, lc.max_blocks, ctl);
+}
+
+template <typename R>
+void Ops<R>::xinv_residual(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                           const C2<R>* S, R* b, const double* mean_sig_dev, const double* mask,
+                           const double* sbar, double* part) {
+  EpiResidual<R> epi;
+  epi.b = b; epi.mean_sig = mean_sig_dev; epi.V = g.V; epi.nc = g.nc;
+  for (int c = 0; c < 6; c++) {
+    epi.mask[c] = c < g.nc ? mask[c] : 0.0;
+    epi.sbar[c] = c < g.nc ? sbar[c] : 0.0;
+    epi.map[c] = g.cmap[c];
+  }
+  const int nr = lc.nrows_c[g.nc];
+  const size_t sm = xsmem<R>(g, nr, g.nc);
+  auto k = k_xinv<R, EpiResidual<R>, 1>;
+  set_smem(k, sm);
+  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, g.nc, nr, R(2.0 / (double)g.V), epi,
+                                        part, lc.max_blocks, nullptr);
+}
+
+template <typename R>
+void Ops<R>::xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                          const C2<R>* S, int ncomp, double* out) {
+  EpiStore64<R> epi;
+  epi.out = out; epi.V = g.V; epi.nc = ncomp;
+  const int nr = lc.nrows_c[ncomp];
+  const size_t sm = xsmem<R>(g, nr, ncomp);
+  auto k = k_xinv<R, EpiStore64<R>, 0>;
+  set_smem(k, sm);
+  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, ncomp, nr, R(2.0 / (double)g.V), epi,
+                                        nullptr, 0, nullptr);
+}
+
+template <typename R>
+void Ops<R>::xmid_ell(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* W,
+                      const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl) {
+  const int nr = lc.nrows_c[g.d];
+  const size_t sm = xsmem<R>(g, nr, g.d);
+  auto k = k_xmid<R>;
+  set_smem(k, sm);
+  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], W, g.d, nr, R(2.0 / (double)g.V), phase,
+                                        ell2_tab, ctl);
+}
+
+template <typename R>
+void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                           C2<R>* S, int ncomp, int axis, int sign, const KrylovCtl* ctl) {
+  const StrideInfo<R> si = stride_of<R>(g, axis);
+  const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
+  const int tx = lc.tx;
+  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + tx);
+  dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? g.n3 : g.n2, ncomp);
+  if (sign < 0) {
+    auto k = k_strided_plain<R, -1>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+  } else {
+    auto k = k_strided_plain<R, 1>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+  }
+}
+
+template <typename R>
+void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* S,
+                   const float* stress_mask, int dc_mode, const KrylovCtl* ctl) {
+  const int axis = g.d - 1;
+  const StrideInfo<R> si = stride_of<R>(g, axis);
+  const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
+  const int tx = lc.tx;
+  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.nc * tx);
+  dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
+  Mask6 m;
+  for (int c = 0; c < 6; c++) m.m[c] = c < g.nc ? stress_mask[c] : 0.f;
+  auto k = k_gamma<R>;
+  set_smem(k, sm);
+  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
+}
+
+template <typename R>
+void Ops<R>::helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* W,
+                         C2<R>* p, const C2<R>* r, double ell2_mean, const KrylovCtl* ctl, int raw) {
+  const int axis = g.d - 1;
+  const StrideInfo<R> si = stride_of<R>(g, axis);
+  const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
+  const int tx = lc.tx;
+  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.d * tx);
+  dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
+  auto k = k_expand<R>;
+  set_smem(k, sm);
+  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
+                                raw);
+}
+
+template <typename R>
+void Ops<R>::helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                           const C2<R>* W, const C2<R>* p, C2<R>* y, double* part, const KrylovCtl* ctl) {
+  const int axis = g.d - 1;
+  const StrideInfo<R> si = stride_of<R>(g, axis);
+  const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
+  const int tx = lc.tx;
+  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.d * tx);
+  dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
+  auto k = k_contract<R>;
+  set_smem(k, sm);
+  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
+                                lc.max_blocks, ctl);
+}
+
+template <typename R>
+void Ops<R>::cg_init(const Geo& g, const LaunchCfg& lc, cudaStream_t st, R* x, const R* r, double* part) {
+  k_cg_init<R><<<lc.n_ew_blocks, kThreads, 0, st>>>((long long)g.nc * g.V, x, r, part, lc.max_blocks);
+}
+
+template <typename R>
+void Ops<R>::cg_update(const Geo& g, const LaunchCfg& lc, cudaStream_t st, R* x, R* r, const R* p,
+                       const R* Ap, double* part, const KrylovCtl* ctl) {
+  k_cg_update<R><<<lc.n_ew_blocks, kThreads, 0, st>>>((long long)g.nc * g.V, x, r, p, Ap, part,
+                                                      lc.max_blocks, ctl);
+}
+
+template <typename R>
+void Ops<R>::pcg_init(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* x,
+                      const C2<R>* r, double ell2_mean, double* part) {
+  k_pcg_init<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, t, x, r, (R)ell2_mean, part, lc.max_blocks);
+}
+
+template <typename R>
+void Ops<R>::pcg_update(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* x,
+                        C2<R>* r, const C2<R>* p, const C2<R>* y, double ell2_mean, double* part,
+                        const KrylovCtl* ctl) {
+  k_pcg_update<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, t, x, r, p, y, (R)ell2_mean, part,
+                                                       lc.max_blocks, ctl);
+}
+
+template <typename R>
+void Ops<R>::return_map(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const PhaseTable* pt, int J,
+                        const uint8_t* phase, const double* eps, const double* epsp_n, const double* ep_n,
+                        const double* abar, double* sigma, double* epsp, double* ep, double* D,
+                        double* alpha, R* desc, double* part) {
+  k_return_map<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, pt, J, phase, eps, epsp_n, ep_n, abar, sigma,
+                                                       epsp, ep, D, alpha, desc, part, lc.max_blocks);
+}
+
+template <typename R>
+void Ops<R>::tangent_apply64(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const R* desc,
+                             const double* p, double* tau) {
+  k_tangent64<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, desc, p, tau);
+}
+
+template <typename R>
+void Ops<R>::eps_update(const Geo& g, const LaunchCfg& lc, cudaStream_t st, double* eps, const R* x,
+                        double* part) {
+  k_eps_update<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, eps, x, part, lc.max_blocks);
+}
+
+template <typename R>
+void Ops<R>::to_r(cudaStream_t st, long long n, const double* a, R* b) {
+  k_to_r<R><<<(int)((n + kThreads - 1) / kThreads < 4096 ? (n + kThreads - 1) / kThreads : 4096), kThreads, 0, st>>>(n, a, b);
+}
+template <typename R>
+void Ops<R>::from_r(cudaStream_t st, long long n, const R* a, double* b) {
+  k_from_r<R><<<(int)((n + kThreads - 1) / kThreads < 4096 ? (n + kThreads - 1) / kThreads : 4096), kThreads, 0, st>>>(n, a, b);
+}
+
+}  // namespace rvk

@@ -1,0 +1,160 @@
+// Precision-independent reductions: deterministic finalisation of per-CTA
+// partial sums (FP64) into Krylov scalars, and the staggered-error sweeps
+// of Algorithm 1 (iii).
+#include "ops.h"
+
+namespace rvk {
+
+// One CTA: slot s is reduced in a fixed order (thread t sums blocks
+// t, t + 256, ...; then a fixed tree), so results are reproducible.
+__global__ void __launch_bounds__(kThreads)
+k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int nslots, int mode,
+                KrylovCtl* ctl, double* out, double scale, int imax) {
+  __shared__ double red[kThreads];
+  __shared__ double vals[16];
+  const bool is_max = mode == FIN_MAXS;
+  for (int s = 0; s < nslots; s++) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads) {
+      const double x = part[(long long)s * stride + b];
+      acc = is_max ? fmax(acc, x) : acc + x;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        red[threadIdx.x] = is_max ? fmax(red[threadIdx.x], red[threadIdx.x + o])
+                                  : red[threadIdx.x] + red[threadIdx.x + o];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) vals[s] = red[0];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  switch (mode) {
+    case FIN_SUMS:
+    case FIN_MAXS:
+      for (int s = 0; s < nslots; s++) out[s] = vals[s] * scale;
+      break;
+    case FIN_CG_INIT:
+      ctl->rtol2 = scale;
+      ctl->maxit = imax;
+      ctl->b2 = vals[0];
+      ctl->rr = vals[0];
+      ctl->rnorm2 = vals[0];
+      ctl->iter = 0;
+      ctl->beta = 0.0;
+      ctl->alpha = 0.0;
+      ctl->status = 0;
+      ctl->done = vals[0] == 0.0 ? 1 : 0;
+      if (!(vals[0] == vals[0])) { ctl->done = 1; ctl->status = 3; }
+      if (ctl->done && ctl->status == 0) ctl->status = 1;
+      if (!ctl->done && imax <= 0) { ctl->done = 1; ctl->status = 2; }
+      break;
+    case FIN_PCG_INIT:
+      ctl->rtol2 = scale;
+      ctl->maxit = imax;
+      ctl->b2 = vals[0];
+      ctl->rnorm2 = vals[0];
+      ctl->rr = vals[1];
+      ctl->iter = 0;
+      ctl->beta = 0.0;
+      ctl->alpha = 0.0;
+      ctl->status = 0;
+      ctl->done = vals[0] == 0.0 ? 1 : 0;
+      if (!(vals[0] == vals[0])) { ctl->done = 1; ctl->status = 3; }
+      if (ctl->done && ctl->status == 0) ctl->status = 1;
+      if (!ctl->done && imax <= 0) { ctl->done = 1; ctl->status = 2; }
+      break;
+    case FIN_ALPHA:
+      if (ctl->done) break;
+      ctl->pAp = vals[0];
+      // NaN: numeric failure; (p, Ap) <= 0: the SPD operator is at its
+      // round-off floor, stop and keep the current iterate
+      if (!(vals[0] == vals[0])) { ctl->done = 1; ctl->status = 3; break; }
+      if (!(vals[0] > 0.0)) { ctl->done = 1; ctl->status = 4; break; }
+      ctl->alpha = ctl->rr / vals[0];
+      break;
+    case FIN_CG_BETA:
+    case FIN_PCG_BETA: {
+      if (ctl->done) break;
+      const double rn2 = vals[0];
+      const double rrn = mode == FIN_CG_BETA ? vals[0] : vals[1];
+      ctl->iter += 1;
+      ctl->rnorm2 = rn2;
+      if (!(rn2 == rn2)) { ctl->done = 1; ctl->status = 3; break; }
+      if (rn2 <= ctl->rtol2 * ctl->b2) { ctl->done = 1; ctl->status = 1; break; }
+      if (ctl->iter >= ctl->maxit) { ctl->done = 1; ctl->status = 2; break; }
+      ctl->beta = rrn / ctl->rr;
+      ctl->rr = rrn;
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+void k_finalize(cudaStream_t st, const double* part, int nblocks, int nblk_stride, int nslots, int mode,
+                KrylovCtl* ctl, double* out, double scale, int imax) {
+  k_finalize_impl<<<1, kThreads, 0, st>>>(part, nblocks, nblk_stride, nslots, mode, ctl, out, scale, imax);
+}
+
+struct Add6 { double a[6]; };
+
+__global__ void __launch_bounds__(kThreads)
+k_copy_add_impl(long long V, int nc, const double* __restrict__ src, double* __restrict__ dst, Add6 add) {
+  const long long n = (long long)nc * V;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    dst[i] = src[i] + add.a[i / V];
+}
+
+void k_copy_add(cudaStream_t st, long long V, int nc, const double* src, double* dst, const double* add_host6) {
+  Add6 a;
+  for (int c = 0; c < 6; c++) a.a[c] = add_host6[c];
+  const long long n = (long long)nc * V;
+  const long long nb = (n + kThreads - 1) / kThreads;
+  k_copy_add_impl<<<(int)(nb < 4096 ? nb : 4096), kThreads, 0, st>>>(V, nc, src, dst, a);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_err_eps_impl(Geo g, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ part,
+               int pstride) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  double mx[1] = {0.0};
+  const long long V = g.V;
+  for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
+    for (int c = 0; c < g.nc; c++) {
+      const double x = a[c * V + v];
+      acc[c] += x;
+      mx[0] = fmax(mx[0], fabs(x - b[c * V + v]));
+    }
+  }
+  block_sum_store<6>(acc, part, pstride);
+  __syncthreads();
+  block_max_store<1>(mx, part + 6 * (long long)pstride, pstride);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_err_abar_impl(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                double* __restrict__ part, int pstride) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    const double d = a[i] - b[i];
+    acc[0] += d * d;
+    acc[1] += a[i] * a[i];
+  }
+  block_sum_store<2>(acc, part, pstride);
+}
+
+void k_err_eps(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const double* eps_new,
+               const double* eps_old, double* part) {
+  k_err_eps_impl<<<lc.n_ew_blocks, kThreads, 0, st>>>(g, eps_new, eps_old, part, lc.max_blocks);
+}
+
+void k_err_abar(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const double* a_new, const double* a_old,
+                double* part) {
+  k_err_abar_impl<<<lc.n_ew_blocks, kThreads, 0, st>>>(g.V, a_new, a_old, part, lc.max_blocks);
+}
+
+}  // namespace rvk

@@ -1,0 +1,356 @@
+"""GPU parity: every step of the hot path, called through the C ABI, against
+the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances: FP64 form <= 1e-10 relative (the bar for the path), element-wise
+<= 1e-12 for single operators; mixed form <= 1e-5 for FP32 operators and
+<= 1e-4 on the homogenised stress of full increments.
+"""
+import numpy as np
+import pytest
+
+import rve_inputs as I
+from oracle import rve_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+pkg = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global pkg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2103_04770_gb300 as p
+    p.lib()
+    pkg = p
+    yield
+
+
+PARAMS = [I.MATRIX, I.PARTICLE]
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda", dtype=dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def cm(a, nc):
+    """oracle layout (..., nc) -> component-major (nc, V)"""
+    return np.ascontiguousarray(a.reshape(-1, nc).T)
+
+
+def om(a, shape):
+    """component-major (nc, V) -> oracle layout shape + (nc,)"""
+    return np.ascontiguousarray(a.T).reshape(tuple(shape) + (a.shape[0],))
+
+
+def handle(n, phase, prec, ell=None, ctrl=None, params=PARAMS):
+    ell = np.array([[2.0, 0.04]]) if ell is None else ell
+    h = pkg.rve_create(len(n), n, [float(x) for x in n], prec, ell.shape[0])
+    pkg.rve_set_phases(h, phase, params, ell)
+    if ctrl is not None:
+        pkg.rve_set_load_path(h, ctrl, np.zeros((1, 6)))
+    return h
+
+
+def mixed_ctrl(d):
+    c = np.array([1, 0, 0, 0, 0, 0], dtype=np.uint8)
+    return I.plane_strain_mask(c) if d == 2 else c
+
+
+def stress_mask_c(ctrl, d):
+    return 1.0 - ctrl[O.carried(d)].astype(float)
+
+
+def rand_state(g, seed):
+    rng = np.random.default_rng(seed)
+    d = g.d
+    nc = 6 if d == 3 else 3
+    phase = (rng.random(g.shape) < 0.3).astype(np.uint8)
+    amp = rng.uniform(0.2, 1.5, (g.V, 1)) * 2e-3
+    eps = amp * rng.standard_normal((g.V, nc))
+    eps[:, 0] += 2e-3
+    epsp_n = 2e-4 * rng.standard_normal((g.V, 6))
+    epsp_n[:, :3] -= epsp_n[:, :3].mean(axis=1, keepdims=True)
+    ep_n = np.abs(3e-2 * rng.standard_normal(g.V))
+    abar = rng.uniform(0.0, 0.12, (1, g.V))
+    return phase, eps, epsp_n, ep_n, abar
+
+
+GRIDS = [(24, 20), (40, 15), (8, 6, 10), (12, 15, 8), (16, 10, 6)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", GRIDS)
+def test_return_map_and_tangent(n, prec):
+    g = O.Grid(n)
+    d = g.d
+    nc = 6 if d == 3 else 3
+    phase, eps, epsp_n, ep_n, abar = rand_state(g, 1)
+    h = handle(n, phase, prec)
+    try:
+        rm = O.return_map(O.embed(eps, d), epsp_n, ep_n, abar, phase.ravel().astype(int),
+                          O.phases_from_dicts(PARAMS))
+        V = g.V
+        outs = dict(sigma=torch.empty(6, V, device="cuda", dtype=torch.float64),
+                    epsp=torch.empty(6, V, device="cuda", dtype=torch.float64),
+                    ep=torch.empty(V, device="cuda", dtype=torch.float64),
+                    D=torch.empty(V, device="cuda", dtype=torch.float64),
+                    alpha=torch.empty(1, V, device="cuda", dtype=torch.float64))
+        pkg.rve_op_return_map(h, dev(eps.T), dev(epsp_n.T), dev(ep_n), dev(abar), outs["sigma"],
+                              outs["epsp"], outs["ep"], outs["D"], outs["alpha"])
+        s_ref = rm["sigma"].T
+        assert np.abs(host(outs["sigma"]) - s_ref).max() <= 1e-12 * np.abs(s_ref).max()
+        assert np.abs(host(outs["epsp"]) - rm["epsp"].T).max() <= 1e-15
+        assert np.abs(host(outs["ep"]) - rm["ep"]).max() <= 1e-15
+        assert np.abs(host(outs["D"]) - rm["D"]).max() <= 1e-14
+        assert np.abs(host(outs["alpha"]) - rm["alpha"]).max() <= 1e-15
+        assert (rm["ep"] > ep_n).sum() > 0.1 * V          # plastic points present
+        assert ((rm["D"] > 0) & (rm["D"] < 0.99)).sum() > 0.05 * V
+        # tangent
+        rng = np.random.default_rng(5)
+        p = rng.standard_normal((V, nc))
+        comps = O.carried(d)
+        tau_ref = np.einsum("vij,vj->vi", rm["C"][:, comps][:, :, comps], p)
+        tau = torch.empty(nc, V, device="cuda", dtype=torch.float64)
+        pkg.rve_op_tangent_apply(h, dev(p.T), tau)
+        tol = 1e-12 if prec == 0 else 2e-6
+        assert np.abs(host(tau) - tau_ref.T).max() <= tol * np.abs(tau_ref).max()
+    finally:
+        pkg.rve_free(h)
+
+
+GAMMA_GRIDS = [(32, 30), (40, 16), (2, 2), (6, 5), (16, 12, 10), (12, 15, 8), (8, 8, 8), (4, 3, 5)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", GAMMA_GRIDS)
+def test_apply_gamma(n, prec):
+    g = O.Grid(n)
+    d = g.d
+    nc = 6 if d == 3 else 3
+    rng = np.random.default_rng(2)
+    phase = (rng.random(g.shape) < 0.3).astype(np.uint8)
+    ctrl = mixed_ctrl(d)
+    h = handle(n, phase, prec, ctrl=ctrl)
+    try:
+        tau = rng.standard_normal(g.shape + (nc,)) + np.array([3.0, -1.0, 0.5, 0.2, 0.1, -0.3])[:nc]
+        ref = O.G_apply(tau, g, stress_mask_c(ctrl, d))
+        out = torch.empty(nc, g.V, device="cuda", dtype=torch.float64)
+        pkg.rve_op_apply_gamma(h, dev(cm(tau, nc)), out)
+        tol = 1e-12 if prec == 0 else 5e-6
+        assert np.abs(host(out) - cm(ref, nc)).max() <= tol * np.abs(tau).max()
+    finally:
+        pkg.rve_free(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [(24, 20), (40, 15), (8, 6, 10), (12, 15, 8)])
+def test_matvec_and_cg(n, prec):
+    g = O.Grid(n)
+    d = g.d
+    nc = 6 if d == 3 else 3
+    phase, eps, epsp_n, ep_n, abar = rand_state(g, 3)
+    ctrl = mixed_ctrl(d)
+    mask = stress_mask_c(ctrl, d)
+    h = handle(n, phase, prec, ctrl=ctrl)
+    try:
+        V = g.V
+        rm = O.return_map(O.embed(eps, d), epsp_n, ep_n, abar, phase.ravel().astype(int),
+                          O.phases_from_dicts(PARAMS))
+        z = [torch.empty(6, V, device="cuda", dtype=torch.float64) for _ in range(2)]
+        s = [torch.empty(V, device="cuda", dtype=torch.float64) for _ in range(2)]
+        al = torch.empty(1, V, device="cuda", dtype=torch.float64)
+        pkg.rve_op_return_map(h, dev(eps.T), dev(epsp_n.T), dev(ep_n), dev(abar), z[0], z[1], s[0], s[1], al)
+        comps = O.carried(d)
+        Cc = rm["C"][:, comps][:, :, comps].reshape(g.shape + (nc, nc))
+
+        def A(x):
+            return O.G_apply(np.einsum("...ij,...j->...i", Cc, x), g, mask)
+
+        rng = np.random.default_rng(4)
+        p = O.G_apply(rng.standard_normal(g.shape + (nc,)), g, mask)
+        out = torch.empty(nc, V, device="cuda", dtype=torch.float64)
+        pkg.rve_op_matvec(h, dev(cm(p, nc)), out)
+        ref = A(p)
+        tol = 1e-12 if prec == 0 else 1e-5
+        assert np.abs(host(out) - cm(ref, nc)).max() <= tol * np.abs(ref).max()
+        # CG on a right-hand side in the range of G*
+        b = O.G_apply(rng.standard_normal(g.shape + (nc,)), g, mask)
+        rtol = 1e-12 if prec == 0 else 1e-5
+        xr, itr = O.cg(A, b, rtol, 2000)
+        x = torch.empty(nc, V, device="cuda", dtype=torch.float64)
+        it = pkg.rve_op_cg(h, dev(cm(b, nc)), x, rtol, 2000)
+        xs = host(x)
+        if prec == 0:
+            assert abs(it - itr) <= 1
+            assert np.abs(xs - cm(xr, nc)).max() <= 1e-9 * np.abs(xr).max()
+        else:
+            # the mixed solve meets the same residual bound (checked in FP64)
+            res = b - A(om(xs, g.shape))
+            assert np.linalg.norm(res) <= 5 * rtol * np.linalg.norm(b)
+            assert it <= 2 * itr + 10
+    finally:
+        pkg.rve_free(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [(32, 30), (40, 16), (16, 12, 10), (12, 15, 8), (6, 5)])
+def test_helmholtz(n, prec):
+    g = O.Grid(n)
+    rng = np.random.default_rng(6)
+    phase = (rng.random(g.shape) < 0.35).astype(np.uint8)
+    ell = np.array([[2.5, 0.05]])
+    h = handle(n, phase, prec, ell=ell)
+    try:
+        ell2 = (ell[0][phase] ** 2)
+        a = rng.standard_normal(g.shape)
+        ref = O.ifft_fields(O.helmholtz_apply_hat(O.fft_fields(a, g), ell2, g), g).real
+        out = torch.empty(g.V, device="cuda", dtype=torch.float64)
+        pkg.rve_op_helmholtz_apply(h, 0, dev(a.ravel()), out)
+        tol = 1e-12 if prec == 0 else 5e-6
+        assert np.abs(host(out) - ref.ravel()).max() <= tol * np.abs(ref).max()
+        alpha = rng.random(g.shape) * (phase == 0)
+        rtol = 1e-12 if prec == 0 else 1e-6
+        abar_ref, itr = O.helmholtz_solve(alpha, ell2, g, rtol, 3000)
+        abar = torch.empty(g.V, device="cuda", dtype=torch.float64)
+        it = pkg.rve_op_helmholtz_solve(h, 0, dev(alpha.ravel()), abar, rtol, 3000)
+        if prec == 0:
+            assert abs(it - itr) <= 1
+            assert np.abs(host(abar) - abar_ref.ravel()).max() <= 1e-10 * np.abs(abar_ref).max()
+        else:
+            assert np.abs(host(abar) - abar_ref.ravel()).max() <= 2e-5 * np.abs(abar_ref).max()
+    finally:
+        pkg.rve_free(h)
+
+
+# Test materials that reach damage within a few small increments (the damage
+# thresholds are inputs, not readings of the paper; full Newton needs
+# increments of ~1e-3 strain to converge from the elastic predictor).
+EARLY_DAMAGE_2D = dict(I.MATRIX, eps_C=0.003, eps_R=0.2)
+EARLY_DAMAGE_3D = dict(I.MATRIX, eps_C=0.004, eps_R=0.04)
+
+
+def _disc_cfg(N, ell, n_incr, dE):
+    cfg = I.config_2d_disc(N, ell_vox=ell, n_incr=n_incr, dE=dE)
+    cfg.params = [EARLY_DAMAGE_2D, I.PARTICLE]
+    return cfg
+
+
+def _sphere_cfg(N, r, n_incr, dE):
+    n = (N, N, N)
+    ph = I.voxelize_spheres(n, np.array([[N / 2, N / 2, N / 2]]), r)
+    ctrl, tgt = I.uniaxial_path(n_incr, dE)
+    return I.RVEConfig("sphere", n, (float(N),) * 3, ph, [EARLY_DAMAGE_3D, I.PARTICLE],
+                       np.array([[2.0, 0.04]]), ctrl, tgt, 0)
+
+
+CASES = {
+    "2d_disc_16": lambda: _disc_cfg(16, 3.0, 6, 1e-3),
+    "3d_sphere_8": lambda: _sphere_cfg(8, 2.6, 5, 1.5e-3),
+}
+
+
+def _run_pair(cfg, prec):
+    g = O.Grid(cfg.n, cfg.L)
+    st = O.make_state(g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
+    oopt = O.PARITY_OPTIONS
+    opt = pkg.rve_default_options(prec)
+    if prec == 0:
+        opt.tol_stag, opt.tol_newton, opt.cg_rtol, opt.pcg_rtol = (oopt.tol_stag, oopt.tol_newton,
+                                                                   oopt.cg_rtol, oopt.pcg_rtol)
+    recs, infos = [], []
+    prev = np.zeros(6)
+    with pkg.RVE(cfg, precision=prec, options=opt) as r:
+        for i in range(cfg.target.shape[0]):
+            infos.append(r.step())
+            recs.append(O.step_increment(st, cfg.strain_ctrl, prev, cfg.target[i], oopt))
+            prev = cfg.target[i]
+    return recs, infos
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", list(CASES))
+def test_increments_match_oracle(case, prec):
+    cfg = CASES[case]()
+    recs, infos = _run_pair(cfg, prec)
+    smax = max(abs(r["S"][0]) for r in recs)
+    tol = 1e-10 if prec == 0 else 1e-4
+    for rec, info in zip(recs, infos):
+        assert np.abs(info["sigma"] - rec["S"]).max() <= tol * smax
+        assert np.abs(info["eps"] - rec["E"]).max() <= tol * abs(rec["E"][0])
+        assert abs(info["D_max"] - rec["D_max"]) <= (1e-9 if prec == 0 else 1e-3)
+        if prec == 0:
+            assert info["staggered_iters"] == rec["stag"]
+    assert recs[-1]["D_max"] > 0.0        # the path reached damage
+
+
+def test_budget_exhaustion_keeps_state():
+    cfg = I.config_2d_disc(16, ell_vox=2.0, n_incr=3, dE=1e-3)
+    opt = pkg.rve_default_options(0)
+    with pkg.RVE(cfg, precision=0, options=opt) as r:
+        r.step()
+        s1 = r.stress().copy()
+        bad = pkg.rve_default_options(0)
+        bad.max_cg = 1
+        pkg.rve_set_options(r.h, bad)
+        info = r.step(raise_on_error=False)
+        assert info["status"] == pkg.RVE_ERR_NOT_CONVERGED
+        np.testing.assert_array_equal(r.stress(), s1)
+        pkg.rve_set_options(r.h, opt)
+        info = r.step()
+        assert info["increment"] == 2
+
+
+def test_call_order_and_argument_errors():
+    n = (16, 16)
+    h = pkg.rve_create(2, n, (16.0, 16.0), 0, 1)
+    try:
+        with pytest.raises(pkg.RVEError) as e:
+            pkg.rve_step_increment(h)
+        assert e.value.status == pkg.RVE_ERR_STATE
+        bad = np.full((16, 16), 3, dtype=np.uint8)
+        with pytest.raises(pkg.RVEError) as e:
+            pkg.rve_set_phases(h, bad, PARAMS, np.array([[1.0, 0.1]]))
+        assert e.value.status == pkg.RVE_ERR_ARG
+        ph = np.zeros((16, 16), dtype=np.uint8)
+        pkg.rve_set_phases(h, ph, PARAMS, np.array([[1.0, 0.1]]))
+        with pytest.raises(pkg.RVEError) as e:      # plane strain needs 33/23/13 strain-controlled
+            pkg.rve_set_load_path(h, [1, 0, 0, 0, 0, 0], np.zeros((1, 6)))
+        assert e.value.status == pkg.RVE_ERR_ARG
+        pkg.rve_set_load_path(h, [1, 0, 1, 1, 1, 0], np.array([[1e-4, 0, 0, 0, 0, 0]]))
+        pkg.rve_step_increment(h)
+        with pytest.raises(pkg.RVEError) as e:
+            pkg.rve_step_increment(h)
+        assert e.value.status == pkg.RVE_ERR_LOAD_PATH_END
+    finally:
+        pkg.rve_free(h)
+
+
+def test_homogeneous_and_no_nonlocal_variable():
+    """Uniform strain in a homogeneous elastic cell needs no CG; a handle
+    without non-local variables (J = 0) steps through elastic increments."""
+    n = (8, 6, 4)
+    ph = np.ones((4, 6, 8), dtype=np.uint8)
+    params = [dict(I.MATRIX, law=0, var=-1), I.PARTICLE]
+    h = pkg.rve_create(3, n, (8.0, 6.0, 4.0), 0, 0)
+    try:
+        pkg.rve_set_phases(h, ph, params, np.zeros((0, 2)))
+        tgt = np.array([[1e-3, -2e-4, 3e-4, 1e-4, -5e-5, 2e-4]])
+        pkg.rve_set_load_path(h, [1] * 6, tgt)
+        info = pkg.rve_step_increment(h)
+        assert info["cg_iters"] == 0 and info["pcg_iters"] == 0
+        np.testing.assert_allclose(info["eps"], tgt[0], atol=1e-16)
+        E, nu = I.PARTICLE["E"], I.PARTICLE["nu"]
+        lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+        mu = E / (2 * (1 + nu))
+        tr = tgt[0][:3].sum()
+        ref = np.concatenate([lam * tr + 2 * mu * tgt[0][:3], 2 * mu * tgt[0][3:]])
+        np.testing.assert_allclose(info["sigma"], ref, rtol=1e-12)
+    finally:
+        pkg.rve_free(h)
