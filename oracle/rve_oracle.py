@@ -16,7 +16,7 @@ components 11, 22, 12 only; the local state is kept in full 3D with
 eps33 = eps13 = eps23 = 0.
 
 Readings where the paper is silent or ambiguous (each is a numbered reading
-R1..R25 of the design notes):
+R1..R26 of the design notes):
   R1  Algorithm 1 loops while ERR > TOL.
   R2  ERR uses Mandel components and the Frobenius norm of <eps>; the
       non-local term counts 0 when ||abar|| < 1e-30; at least 2 staggered
@@ -41,6 +41,10 @@ R1..R25 of the design notes):
   R25 CG and PCG stop when (p, A p) <= 0: the operators are symmetric
       positive definite in exact arithmetic, so this only happens once the
       residual has reached the round-off floor; the current iterate is kept.
+  R26 The mechanical CG of a Newton step also stops once ||r|| <=
+      0.01 TOL_N sqrt(V) ||<sigma>||: the linear solve is not pushed below the
+      accuracy the Newton test (R4) can use, where the right-hand side is
+      dominated by the round-off of -G*(sigma - Sigma_bar).
 
 Parity: every function below is pinned by the CPU tests (closed forms,
 invariants, dense brute-force solves built from real-space stencils, finite
@@ -342,16 +346,17 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
 
 
 # ============================================================ Krylov solvers
-def cg(A, b, rtol, maxit, dot=None):
+def cg(A, b, rtol, maxit, dot=None, floor=0.0):
     """Textbook conjugate gradients from x0 = 0; stops when ||r|| <=
-    rtol ||b|| (the criterion of Algorithm 2) or when (p, A p) <= 0 (R25).
-    Returns (x, iterations)."""
+    max(rtol ||b||, floor) (the criterion of Algorithm 2, with the absolute
+    floor of R26) or when (p, A p) <= 0 (R25).  Returns (x, iterations)."""
     if dot is None:
         def dot(u, v):
             return float(np.sum(u * v))
     x = np.zeros_like(b)
     bn = math.sqrt(dot(b, b))
-    if bn == 0.0:
+    tol = max(rtol * bn, floor)
+    if bn == 0.0 or bn <= tol:
         return x, 0
     r = b.copy()
     p = r.copy()
@@ -367,7 +372,7 @@ def cg(A, b, rtol, maxit, dot=None):
         r = r - alpha * Ap
         it += 1
         rr_new = dot(r, r)
-        if math.sqrt(rr_new) <= rtol * bn:
+        if math.sqrt(rr_new) <= tol:
             break
         p = r + (rr_new / rr) * p
         rr = rr_new
@@ -486,7 +491,8 @@ def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_
         if newton >= opt.max_newton:
             raise RuntimeError("Newton did not converge")
         dx, it = cg(lambda x: G_apply(np.einsum("...ij,...j->...i", Cc, x), grid, stress_mask),
-                    res, opt.cg_rtol, opt.max_cg)
+                    res, opt.cg_rtol, opt.max_cg,
+                    floor=0.01 * opt.tol_newton * math.sqrt(Vn) * smean)
         eps_c = eps_c + dx
         cg_total += it
         newton += 1
