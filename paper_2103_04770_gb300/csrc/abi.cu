@@ -104,6 +104,13 @@ struct rve {
   void* tw[3] = {nullptr, nullptr, nullptr};
   void* ts[3] = {nullptr, nullptr, nullptr};
   void* tc[3] = {nullptr, nullptr, nullptr};
+  // FP64 tables, spectrum and launch shape of the Newton residual sweep
+  // (aliases of the above in the FP64 form)
+  void* tw64[3] = {nullptr, nullptr, nullptr};
+  void* ts64[3] = {nullptr, nullptr, nullptr};
+  void* tc64[3] = {nullptr, nullptr, nullptr};
+  void* S64 = nullptr;
+  LaunchCfg lc64{};
   FftPlan plan[3]{};
   // reductions and control
   double* part = nullptr;
@@ -248,6 +255,20 @@ inline void prof_end(rve* h, int cls) {
     prof_end((h), (cls));                \
   } while (0)
 
+Tables<double> tables64(const rve* h) {
+  Tables<double> t;
+  for (int j = 0; j < 3; j++) {
+    t.tw[j] = (C2<double>*)h->tw64[j];
+    t.s[j] = (double*)h->ts64[j];
+    t.c[j] = (double*)h->tc64[j];
+    t.two_over_h[j] = 2.0 / h->g.h[j];
+  }
+  t.plan_x = h->plan[0];
+  t.plan_y = h->plan[1];
+  t.plan_z = h->plan[2];
+  return t;
+}
+
 int sync_read(rve* h) {
   CK(cudaMemcpyAsync(h->hscal, h->dscal, kScal * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, h->st));
@@ -291,16 +312,34 @@ struct Alg {
                FIN_MAXS, nullptr, h->dscal + OFF_DMAX, 1.0));
   }
 
-  // b = -G*(sigma - Sigma_bar) into r, ctl initialised for CG.
-  static void residual(rve* h, const Tables<R>& t, const double* sbar_c, double rtol, int maxit) {
-    LAUNCHB(h, KC_X_FWD_FIELD, (double)h->g.nc * (8.0 * VV(h) + VS(h) * CS), Op::xfwd_field64(h->g, t, h->lc, h->st, h->sigma, h->g.nc, h->g.cmap, h->dscal + OFF_SIGMEAN,
-                     (C2<R>*)h->S));
-    gamma_sweep(h, t, 1, nullptr);
-    LAUNCHB(h, KC_X_INV_RESIDUAL, (double)h->g.nc * (VS(h) * CS + VV(h) * RS), Op::xinv_residual(h->g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->r, h->dscal + OFF_SIGMEAN,
-                      h->smask_d, sbar_c, h->part));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, h->g.nc), h->lc.max_blocks, 1, FIN_CG_INIT, h->ctl, nullptr,
-               rtol * rtol, maxit));
+  // b = -G*(sigma - Sigma_bar), swept in FP64 in both forms and stored in
+  // the working precision into r; ctl initialised for CG.
+  static void residual(rve* h, const double* sbar_c, double rtol, int maxit) {
+    const Tables<double> t64 = tables64(h);
+    C2<double>* S64 = (C2<double>*)h->S64;
+    const Geo& g = h->g;
+    const double cs64 = 16.0, nc = g.nc;
+    LAUNCHB(h, KC_X_FWD_FIELD, nc * (8.0 * VV(h) + VS(h) * cs64),
+            Ops<double>::xfwd_field64(g, t64, h->lc64, h->st, h->sigma, g.nc, g.cmap, h->dscal + OFF_SIGMEAN,
+                                      S64));
+    if (g.d == 3)
+      LAUNCHB(h, KC_Y_PASS, 2.0 * nc * VS(h) * cs64,
+              Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, -1, nullptr));
+    LAUNCHB(h, KC_GAMMA, 2.0 * nc * VS(h) * cs64,
+            Ops<double>::gamma(g, t64, h->lc64, h->st, S64, h->smask_f, 1, nullptr));
+    if (g.d == 3)
+      LAUNCHB(h, KC_Y_PASS, 2.0 * nc * VS(h) * cs64,
+              Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, +1, nullptr));
+    LAUNCHB(h, KC_X_INV_RESIDUAL, nc * (VS(h) * cs64 + VV(h) * RS),
+            Ops<double>::template xinv_residual<R>(g, t64, h->lc64, h->st, S64, (R*)h->r,
+                                                   h->dscal + OFF_SIGMEAN, h->smask_d, sbar_c, h->part));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
+                                            h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
   }
+
+  // FP32 Krylov solves stop when (r, r) has not fallen below a quarter of its
+  // best value for this many iterations (attainable accuracy reached).
+  static int stall_window() { return sizeof(R) == sizeof(float) ? 150 : 0; }
 
   // CG on G*(C_T : x) = b (r holds b, ctl initialised, x zeroed by caller).
   static int cg_loop(rve* h, const Tables<R>& t, int* iters) {
@@ -335,7 +374,7 @@ struct Alg {
     int newton = 0;
     for (;;) {
       return_map(h, abar_use);
-      residual(h, t, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
+      residual(h, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
       int s = sync_read(h);
       if (s) return s;
       double sm = 0.0;
@@ -350,8 +389,18 @@ struct Alg {
       if (res_rel < h->opt.tol_newton && (de_rel < 0.0 || de_rel < h->opt.tol_newton)) break;
       if (newton >= h->opt.max_newton) { h->fail_stage = 1; *newton_out += newton; return RVE_ERR_NOT_CONVERGED; }
       CK(cudaMemsetAsync(h->x, 0, (size_t)g.nc * g.V * rsize(h), h->st));
+      // absolute floor of the linear solve: 0.01 TOL_N sqrt(V) |<sigma>|
+      const double floor_ = 0.01 * h->opt.tol_newton * std::sqrt((double)g.V) * sm;
       int it = 0;
-      s = cg_loop(h, t, &it);
+      if (b2 <= floor_ * floor_) {
+        h->hctl->done = 1;
+        h->hctl->status = 1;
+        h->hctl->iter = 0;
+      } else {
+        h->hctl->tol2 = std::max(h->hctl->tol2, floor_ * floor_);
+        CK(cudaMemcpyAsync(h->ctl, h->hctl, sizeof(KrylovCtl), cudaMemcpyHostToDevice, h->st));
+        s = cg_loop(h, t, &it);
+      }
       *cg_out += it;
       if (h->verbose)
         std::fprintf(stderr, "[rve]   cg iters %d status %d pAp %.3e rnorm2 %.3e b2 %.3e -> %d\n", it,
@@ -410,7 +459,7 @@ struct Alg {
     forward1(h, t, alpha_j, hr);
     LAUNCHB(h, KC_PCG_UPDATE, 2.0 * VS(h) * CS, Op::pcg_init(g, t, h->lc, h->st, hx, hr, h->ell2_mean[j], h->part));
     LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_INIT, h->ctl, nullptr,
-               rtol * rtol, maxit));
+               rtol * rtol, maxit, stall_window()));
     const int chunk = std::max(1, h->opt.check_every);
     const int nbl = last_blocks(h);
     for (;;) {
@@ -606,28 +655,30 @@ struct Alg {
   }
 };
 
+// Twiddles exp(-2 pi i m / N) and half-angle tables sin/cos(pi q / N) (cos
+// exactly 0 at the Nyquist index) of the three axes, from double precision.
 template <typename R>
-int build_tables(rve* h) {
+int build_tables(rve* h, void* tw[3], void* ts[3], void* tc[3]) {
   const int Ns[3] = {h->g.n1, h->g.n2, h->g.n3};
   for (int j = 0; j < 3; j++) {
     const int N = Ns[j];
-    std::vector<C2<R>> tw(N);
-    std::vector<R> s(N), c(N);
+    std::vector<C2<R>> twv(N);
+    std::vector<R> sv(N), cv(N);
     for (int m = 0; m < N; m++) {
       const double ang = -2.0 * kPi * (double)m / (double)N;
-      tw[m] = mk<R>((R)std::cos(ang), (R)std::sin(ang));
+      twv[m] = mk<R>((R)std::cos(ang), (R)std::sin(ang));
       const int q = m < (N + 1) / 2 ? m : m - N;
       const double half = kPi * (double)q / (double)N;
-      s[m] = (R)std::sin(half);
-      c[m] = (2 * std::abs(q) == N) ? R(0) : (R)std::cos(half);
+      sv[m] = (R)std::sin(half);
+      cv[m] = (2 * std::abs(q) == N) ? R(0) : (R)std::cos(half);
     }
     int st;
-    if ((st = dalloc(h, &h->tw[j], N * sizeof(C2<R>)))) return st;
-    if ((st = dalloc(h, &h->ts[j], N * sizeof(R)))) return st;
-    if ((st = dalloc(h, &h->tc[j], N * sizeof(R)))) return st;
-    CK(cudaMemcpy(h->tw[j], tw.data(), N * sizeof(C2<R>), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->ts[j], s.data(), N * sizeof(R), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->tc[j], c.data(), N * sizeof(R), cudaMemcpyHostToDevice));
+    if ((st = dalloc(h, &tw[j], N * sizeof(C2<R>)))) return st;
+    if ((st = dalloc(h, &ts[j], N * sizeof(R)))) return st;
+    if ((st = dalloc(h, &tc[j], N * sizeof(R)))) return st;
+    CK(cudaMemcpy(tw[j], twv.data(), N * sizeof(C2<R>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ts[j], sv.data(), N * sizeof(R), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(tc[j], cv.data(), N * sizeof(R), cudaMemcpyHostToDevice));
   }
   return RVE_OK;
 }
@@ -691,7 +742,8 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
     if (nn[j] < 1 || !(LL[j] > 0.0)) return RVE_ERR_ARG;
   if (nn[0] < 2 || nn[0] % 2) return RVE_ERR_ARG;
   const int ET = (precision == RVE_MIXED ? 8 : 4) * kThreads;
-  if (std::max(nn[1], nn[2]) > ET) return RVE_ERR_ARG;
+  // the FP64 Newton residual sweep runs in both forms
+  if (std::max(nn[1], nn[2]) > 4 * kThreads) return RVE_ERR_ARG;
   const int nc = dim == 3 ? 6 : 3;
   if ((nn[0] / 2) * nc > 16 * kThreads) return RVE_ERR_ARG;
   FftPlan pl[3];
@@ -716,8 +768,8 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   g.n1 = nn[0]; g.n2 = nn[1]; g.n3 = nn[2];
   g.M = nn[0] / 2;
   g.P1 = g.M + 1;
-  const int align = precision == RVE_MIXED ? 16 : 8;
-  g.ps = ((g.P1 + align - 1) / align) * align;
+  // rows padded to 16 complex entries in both precisions (128 B / 256 B)
+  g.ps = ((g.P1 + 15) / 16) * 16;
   g.nc = nc;
   const int cm3[6] = {0, 1, 2, 3, 4, 5}, cm2[6] = {0, 1, 5, 0, 0, 0};
   for (int c = 0; c < 6; c++) g.cmap[c] = dim == 3 ? cm3[c] : cm2[c];
@@ -729,16 +781,23 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   LaunchCfg& lc = h->lc;
   for (int c = 1; c <= 6; c++) lc.nrows_c[c] = std::max(1, std::min(32, (16 * kThreads) / (c * g.M)));
   lc.nrows_c[0] = 1;
-  int tx = 1;
   const int nmax = std::max(nn[1], nn[2]);
-  while (tx * 2 * nmax <= ET && tx * 2 <= 32) tx *= 2;
-  lc.tx = tx;
+  auto tx_for = [&](int et) {
+    int tx = 1;
+    while (tx * 2 * nmax <= et && tx * 2 <= 32) tx *= 2;
+    return tx;
+  };
+  const int ET64 = 4 * kThreads;
+  lc.tx = tx_for(ET);
   long long ew = (g.V + kThreads - 1) / kThreads;
   lc.n_ew_blocks = (int)std::min<long long>(ew, 152LL * 16);
   long long mb = lc.n_ew_blocks;
   for (int c = 1; c <= 6; c++) mb = std::max<long long>(mb, (g.nlines + lc.nrows_c[c] - 1) / lc.nrows_c[c]);
-  mb = std::max<long long>(mb, (long long)((g.P1 + tx - 1) / tx) * std::max(nn[1], 1));
+  const int tx64 = tx_for(ET64);
+  mb = std::max<long long>(mb, (long long)((g.P1 + tx64 - 1) / tx64) * std::max(nn[1], 1));
   lc.max_blocks = (int)mb;
+  h->lc64 = lc;
+  h->lc64.tx = tx64;
 
   int s = RVE_OK;
   const size_t V = (size_t)g.V;
@@ -780,7 +839,14 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   AL(dalloc_t(h, &h->part, (size_t)kSlots * lc.max_blocks));
   AL(dalloc_t(h, &h->ctl, 1));
   AL(dalloc_t(h, &h->dscal, kScal));
-  AL(precision == RVE_MIXED ? build_tables<float>(h) : build_tables<double>(h));
+  AL(build_tables<double>(h, h->tw64, h->ts64, h->tc64));
+  if (precision == RVE_MIXED) {
+    AL(build_tables<float>(h, h->tw, h->ts, h->tc));
+    AL(dalloc(h, &h->S64, (size_t)nc * g.sstride * 16));
+  } else {
+    for (int j = 0; j < 3; j++) { h->tw[j] = h->tw64[j]; h->ts[j] = h->ts64[j]; h->tc[j] = h->tc64[j]; }
+    h->S64 = h->S;
+  }
 #undef AL
   if (cudaMallocHost((void**)&h->hctl, sizeof(KrylovCtl)) != cudaSuccess ||
       cudaMallocHost((void**)&h->hscal, kScal * sizeof(double)) != cudaSuccess) {
@@ -791,6 +857,7 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   }
   // a (spectral) buffer that is never written in the padding stays defined
   cudaMemset(h->S, 0, (size_t)nc * g.sstride * cs);
+  if (h->S64 != h->S) cudaMemset(h->S64, 0, (size_t)nc * g.sstride * 16);
   cudaMemset(h->hx, 0, (size_t)g.sstride * cs);
   cudaMemset(h->hr, 0, (size_t)g.sstride * cs);
   cudaMemset(h->hp, 0, (size_t)g.sstride * cs);

@@ -55,6 +55,11 @@ struct KrylovCtl {
   double pAp;
   double alpha, beta;
   double rtol2;
+  double tol2;     // stop when (r, r) <= tol2 = max(rtol^2 (b, b), floor^2)
+  double best;     // smallest (r, r) seen (stall detection)
+  int best_it;
+  int stall;       // > 0: stop after this many iterations without (r, r)
+                   // falling below best / 4 (FP32 Krylov solves)
   // status: 0 running, 1 converged, 2 budget, 3 non-finite, 4 stopped at
   // the round-off floor ((p, Ap) <= 0)
   int iter, maxit, done, status;

@@ -281,9 +281,9 @@ struct EpiMatvec {       // Ap = val; acc0 += p . Ap
   }
 };
 
-template <typename R>
+template <typename R, typename RO>
 struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
-  R* b;
+  RO* b;
   const double* mean_sig;   // full Mandel (6)
   double mask[6];
   double sbar[6];
@@ -297,7 +297,7 @@ struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
   __device__ __forceinline__ void operator()(long long v, const R* val, double* acc) const {
     for (int c = 0; c < nc; c++) {
       const double bv = -((double)val[c] + dc[c]);
-      const R br = (R)bv;
+      const RO br = (RO)bv;
       b[c * V + v] = br;
       acc[0] += (double)br * (double)br;
     }
@@ -772,10 +772,11 @@ void Ops<R>::xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
 }
 
 template <typename R>
+template <typename RO>
 void Ops<R>::xinv_residual(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
-                           const C2<R>* S, R* b, const double* mean_sig_dev, const double* mask,
+                           const C2<R>* S, RO* b, const double* mean_sig_dev, const double* mask,
                            const double* sbar, double* part) {
-  EpiResidual<R> epi;
+  EpiResidual<R, RO> epi;
   epi.b = b; epi.mean_sig = mean_sig_dev; epi.V = g.V; epi.nc = g.nc;
   for (int c = 0; c < 6; c++) {
     epi.mask[c] = c < g.nc ? mask[c] : 0.0;
@@ -784,7 +785,7 @@ void Ops<R>::xinv_residual(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   }
   const int nr = lc.nrows_c[g.nc];
   const size_t sm = xsmem<R>(g, nr, g.nc);
-  auto k = k_xinv<R, EpiResidual<R>, 1>;
+  auto k = k_xinv<R, EpiResidual<R, RO>, 1>;
   set_smem(k, sm);
   k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, g.nc, nr, R(2.0 / (double)g.V), epi,
                                         part, lc.max_blocks, nullptr);

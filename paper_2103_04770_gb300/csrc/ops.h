@@ -58,9 +58,11 @@ struct Ops {
   // inverse: Ap = scale * C2R(S); partial (p, Ap)
   static void xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                           const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl);
-  // inverse: b = -(C2R + mask (mean_sigma - sbar)); partial (b, b)
+  // inverse: b = -(C2R + mask (mean_sigma - sbar)) stored in precision RO;
+  // partial (b, b) of the stored values
+  template <typename RO>
   static void xinv_residual(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
-                            const C2<R>* S, R* b, const double* mean_sig_dev, const double* dcterm_mask,
+                            const C2<R>* S, RO* b, const double* mean_sig_dev, const double* dcterm_mask,
                             const double* sbar, double* part);
   // inverse: out64[c][v] = scale * C2R(S)
   static void xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
@@ -121,7 +123,7 @@ void k_err_abar(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const double
 // finalize: reduce nslots slots of per-CTA partials; INIT modes also store
 // rtol2 = scale and maxit = imax into ctl.
 void k_finalize(cudaStream_t st, const double* part, int nblocks, int nblk_stride, int nslots,
-                int mode, KrylovCtl* ctl, double* out, double scale, int imax = 0);
+                int mode, KrylovCtl* ctl, double* out, double scale, int imax = 0, int stall = 0);
 // dst[c][v] = src[c][v] + add[c]  (c < nc, FP64)
 void k_copy_add(cudaStream_t st, long long V, int nc, const double* src, double* dst, const double* add_host6);
 

@@ -9,7 +9,7 @@ namespace rvk {
 // t, t + 256, ...; then a fixed tree), so results are reproducible.
 __global__ void __launch_bounds__(kThreads)
 k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int nslots, int mode,
-                KrylovCtl* ctl, double* out, double scale, int imax) {
+                KrylovCtl* ctl, double* out, double scale, int imax, int stall) {
   __shared__ double red[kThreads];
   __shared__ double vals[16];
   const bool is_max = mode == FIN_MAXS;
@@ -40,7 +40,11 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
     case FIN_CG_INIT:
       ctl->rtol2 = scale;
       ctl->maxit = imax;
+      ctl->stall = stall;
       ctl->b2 = vals[0];
+      ctl->tol2 = scale * vals[0];
+      ctl->best = vals[0];
+      ctl->best_it = 0;
       ctl->rr = vals[0];
       ctl->rnorm2 = vals[0];
       ctl->iter = 0;
@@ -55,6 +59,10 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
     case FIN_PCG_INIT:
       ctl->rtol2 = scale;
       ctl->maxit = imax;
+      ctl->stall = stall;
+      ctl->tol2 = scale * vals[0];
+      ctl->best = vals[0];
+      ctl->best_it = 0;
       ctl->b2 = vals[0];
       ctl->rnorm2 = vals[0];
       ctl->rr = vals[1];
@@ -84,8 +92,10 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
       ctl->iter += 1;
       ctl->rnorm2 = rn2;
       if (!(rn2 == rn2)) { ctl->done = 1; ctl->status = 3; break; }
-      if (rn2 <= ctl->rtol2 * ctl->b2) { ctl->done = 1; ctl->status = 1; break; }
+      if (rn2 <= ctl->tol2) { ctl->done = 1; ctl->status = 1; break; }
       if (ctl->iter >= ctl->maxit) { ctl->done = 1; ctl->status = 2; break; }
+      if (rn2 < 0.25 * ctl->best) { ctl->best = rn2; ctl->best_it = ctl->iter; }
+      else if (ctl->stall > 0 && ctl->iter - ctl->best_it >= ctl->stall) { ctl->done = 1; ctl->status = 4; break; }
       ctl->beta = rrn / ctl->rr;
       ctl->rr = rrn;
       break;
@@ -96,8 +106,9 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
 }
 
 void k_finalize(cudaStream_t st, const double* part, int nblocks, int nblk_stride, int nslots, int mode,
-                KrylovCtl* ctl, double* out, double scale, int imax) {
-  k_finalize_impl<<<1, kThreads, 0, st>>>(part, nblocks, nblk_stride, nslots, mode, ctl, out, scale, imax);
+                KrylovCtl* ctl, double* out, double scale, int imax, int stall) {
+  k_finalize_impl<<<1, kThreads, 0, st>>>(part, nblocks, nblk_stride, nslots, mode, ctl, out, scale, imax,
+                                          stall);
 }
 
 struct Add6 { double a[6]; };
