@@ -95,7 +95,12 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
       if (rn2 <= ctl->tol2) { ctl->done = 1; ctl->status = 1; break; }
       if (ctl->iter >= ctl->maxit) { ctl->done = 1; ctl->status = 2; break; }
       if (rn2 < 0.25 * ctl->best) { ctl->best = rn2; ctl->best_it = ctl->iter; }
-      else if (ctl->stall > 0 && ctl->iter - ctl->best_it >= ctl->stall) { ctl->done = 1; ctl->status = 4; break; }
+      else if (ctl->stall > 0 && (ctl->iter - ctl->best_it >= ctl->stall || rn2 > 1e2 * ctl->best)) {
+        // FP32 solve at its attainable accuracy (stalled) or losing stability
+        ctl->done = 1;
+        ctl->status = 4;
+        break;
+      }
       ctl->beta = rrn / ctl->rr;
       ctl->rr = rrn;
       break;

@@ -60,7 +60,7 @@ def test_struct_layout_matches_header(pkg, tmp_path):
 def test_host_only_calls(pkg):
     assert pkg.rve_status_string(pkg.RVE_ERR_NOT_CONVERGED) == "iteration budget exhausted"
     o = pkg.rve_default_options(pkg.RVE_MIXED)
-    assert o.cg_rtol == 1e-6 and o.min_stag == 2
+    assert o.cg_rtol == 1e-3 and o.min_stag == 2
     o64 = pkg.rve_default_options(pkg.RVE_FP64)
     assert o64.cg_rtol == 1e-8
 
