@@ -229,6 +229,37 @@ int rve_op_helmholtz_apply(rve_t* h, int j, const double* a, double* out);
 int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, double rtol,
                            int maxit, int* iters);
 
+/* ------------------------------------------------ allocation-free variant
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory, such as an application that hands
+ * all device memory out of its own pool at start-up and forbids later
+ * cudaMalloc calls, or a plug-in running inside a host framework that owns
+ * the device's memory.  Such a caller cannot create a handle (rve_create
+ * allocates), so this call computes the same out = G*(tau) as
+ * rve_op_apply_gamma (Eq. eqdiscrete2, FP64) without one, and allocates
+ * nothing: its half-spectrum scratch (32 MiB) and its FFT tables sit in
+ * static device arrays that every GPU which loads the library holds until
+ * the process exits.
+ *  - dim, n, L: grid as in rve_create (N1 even, axes products of 2, 3, 5,
+ *    every axis <= 1024); strain_ctrl[6]: 1 where the mean strain is
+ *    prescribed (the zero frequency keeps the other, stress-controlled,
+ *    components), as in rve_set_load_path.
+ *  - tau, out: caller-owned DEVICE buffers [nc][V] (Mandel, FP64).
+ *  - cuda_stream: the stream the work is enqueued on; the call returns after
+ *    synchronising it.
+ *  - Grids whose FP64 half spectrum (nc * N3 * N2 * ps * 16 bytes, ps = N1/2+1
+ *    rounded up to 16) exceeds 32 MiB, e.g. beyond 64^3 in 3D, are rejected
+ *    with RVE_ERR_ARG before any device work.
+ *  - The first call on a device (with that device current) looks up the
+ *    static arrays' device addresses; make that first call before any stream
+ *    capture.
+ *  - Every call shares the same static scratch and tables, which keep the
+ *    last call's contents: calls that overlap on the GPU (other streams,
+ *    other host threads) race and must be serialised by the caller.
+ * Errors: RVE_ERR_ARG, RVE_ERR_CUDA. */
+int rve_op_apply_gamma_noalloc(int dim, const int n[3], const double L[3], const uint8_t strain_ctrl[6],
+                               const double* tau, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,8 @@ _SIGNATURES = {
     "rve_op_cg": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I)]),
     "rve_op_helmholtz_apply": (_I, [_P, _I, _P, _P]),
     "rve_op_helmholtz_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(_I)]),
+    "rve_op_apply_gamma_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D),
+                                        ctypes.POINTER(ctypes.c_uint8), _P, _P, _P]),
     "rve_profile": (_I, [_P, _I]),
     "rve_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                               ctypes.POINTER(_D)]),
@@ -272,6 +274,17 @@ def rve_op_helmholtz_solve(h, j, alpha, abar, rtol, maxit):
     _check(lib().rve_op_helmholtz_solve(h, int(j), _ptr(alpha), _ptr(abar), float(rtol), int(maxit),
                                         ctypes.byref(it)), "rve_op_helmholtz_solve")
     return it.value
+
+
+def rve_op_apply_gamma_noalloc(dim, n, L, strain_ctrl, tau, out, stream=None):
+    """G*(tau) without a handle and without any device allocation (static
+    device scratch inside the library); tau/out are CUDA float64 tensors
+    [nc][V]."""
+    n3 = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    L3 = (ctypes.c_double * 3)(*(list(map(float, L)) + [1.0] * (3 - len(L))))
+    c = (ctypes.c_uint8 * 6)(*[int(x) for x in strain_ctrl])
+    _check(lib().rve_op_apply_gamma_noalloc(int(dim), n3, L3, c, _ptr(tau), _ptr(out),
+                                            _stream_handle(stream)), "rve_op_apply_gamma_noalloc")
 
 
 # -------------------------------------------------------------- profiling
