@@ -779,8 +779,15 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   for (int j = 0; j < 3; j++) g.h[j] = LL[j] / nn[j];
 
   LaunchCfg& lc = h->lc;
-  for (int c = 1; c <= 6; c++) lc.nrows_c[c] = std::max(1, std::min(32, (16 * kThreads) / (c * g.M)));
+  // x1 passes: 4 staged FFT elements per thread when a row of c components
+  // fits (several CTAs per SM), 16 otherwise
+  for (int c = 1; c <= 6; c++) {
+    const int e = (c * g.M <= 4 * kThreads) ? 4 : 16;
+    lc.xe_c[c] = e;
+    lc.nrows_c[c] = std::max(1, std::min(32, (e * kThreads) / (c * g.M)));
+  }
   lc.nrows_c[0] = 1;
+  lc.xe_c[0] = 16;
   const int nmax = std::max(nn[1], nn[2]);
   auto tx_for = [&](int et) {
     int tx = 1;

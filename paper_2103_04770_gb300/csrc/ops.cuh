@@ -21,7 +21,6 @@ namespace rvk {
 template <typename R> struct StridedE;
 template <> struct StridedE<float> { static constexpr int E = 8; };
 template <> struct StridedE<double> { static constexpr int E = 4; };
-constexpr int kXE = 16;
 
 struct Mask6 { float m[6]; };
 
@@ -83,10 +82,17 @@ __device__ __forceinline__ void gamma_mode(int d, const R n[3], C2<R>* t) {
 }
 
 // ================================================================ x1 passes
-template <typename R, class PRO>
-__global__ void __launch_bounds__(kThreads)
-k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, int nc, int nrows,
-       PRO pro, const KrylovCtl* __restrict__ ctl) {
+// Kernels are specialised on the component count NC (so per-voxel vectors
+// live in registers) and on E, the FFT elements staged per thread (4: one or
+// a few rows per CTA and four CTAs per SM; 16: long rows).
+template <typename R, int E> struct XMinBlocks {
+  static constexpr int v = E <= 4 ? (sizeof(R) == 4 ? 3 : 2) : 1;
+};
+
+template <typename R, int NC, int E, class PRO>
+__global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
+k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, int nrows, PRO pro,
+       const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
@@ -100,16 +106,17 @@ k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, 
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
     const int r = e / g.n1, x = e - r * g.n1;
     const long long v = (row0 + r) * g.n1 + x;
-    R val[6];
+    R val[NC];
     pro(v, val);
-    for (int c = 0; c < nc; c++) rbuf[(r * nc + c) * g.n1 + x] = val[c];
+#pragma unroll
+    for (int c = 0; c < NC; c++) rbuf[(r * NC + c) * g.n1 + x] = val[c];
   }
   __syncthreads();
-  fft_lines<R, kXE, -1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
-  const int nout = rows * nc * g.P1;
+  fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
+  const int nout = rows * NC * g.P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
     const int l = e / g.P1, k = e - l * g.P1;
-    const int r = l / nc, c = l - r * nc;
+    const int r = l / NC, c = l - r * NC;
     const C2<R> zk = cbuf[l * g.M + (k == g.M ? 0 : k)];
     const C2<R> zm = cbuf[l * g.M + (k == 0 ? 0 : g.M - k)];
     const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
@@ -135,11 +142,10 @@ __device__ __forceinline__ void xinv_pre(const Geo& g, const C2<R>* __restrict__
   }
 }
 
-template <typename R, class EPI, int NS>
-__global__ void __launch_bounds__(kThreads)
-k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict__ S, int nc,
-       int nrows, R scale, EPI epi, double* __restrict__ part, int pstride,
-       const KrylovCtl* __restrict__ ctl) {
+template <typename R, int NC, int E, class EPI, int NS>
+__global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
+k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict__ S, int nrows, R scale,
+       EPI epi, double* __restrict__ part, int pstride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
@@ -149,30 +155,31 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
   __syncthreads();
-  xinv_pre(g, S, row0, rows, nc, tws, cbuf);
+  xinv_pre(g, S, row0, rows, NC, tws, cbuf);
   __syncthreads();
-  fft_lines<R, kXE, +1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
-  double acc[NS > 0 ? NS : 1];
+  fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
+  constexpr int NSA = NS > 0 ? NS : 1;
+  double acc[NSA];
 #pragma unroll
-  for (int s = 0; s < (NS > 0 ? NS : 1); s++) acc[s] = 0.0;
+  for (int s = 0; s < NSA; s++) acc[s] = 0.0;
   epi.begin(ctl);
   const int nvox = rows * g.n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
     const int r = e / g.n1, x = e - r * g.n1;
     const long long v = (row0 + r) * g.n1 + x;
-    R val[6];
-    for (int c = 0; c < nc; c++) val[c] = rbuf[(r * nc + c) * g.n1 + x] * scale;
+    R val[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) val[c] = rbuf[(r * NC + c) * g.n1 + x] * scale;
     epi(v, val, acc);
   }
-  if (NS > 0) block_sum_store<(NS > 0 ? NS : 1)>(acc, part, pstride);
+  if (NS > 0) block_sum_store<NSA>(acc, part, pstride);
 }
 
-// C2R -> l^2(x) * scale -> R2C of the d gradient components (Algorithm 2, GC).
-template <typename R>
-__global__ void __launch_bounds__(kThreads)
-k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, int nc, int nrows,
-       R scale, const uint8_t* __restrict__ phase, const R* __restrict__ ell2,
-       const KrylovCtl* __restrict__ ctl) {
+// C2R -> l^2(x) * scale -> R2C of the NC = d gradient components (Algorithm 2, GC).
+template <typename R, int NC, int E>
+__global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
+k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, int nrows, R scale,
+       const uint8_t* __restrict__ phase, const R* __restrict__ ell2, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
@@ -182,22 +189,23 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
   __syncthreads();
-  xinv_pre(g, W, row0, rows, nc, tws, cbuf);
+  xinv_pre(g, W, row0, rows, NC, tws, cbuf);
   __syncthreads();
-  fft_lines<R, kXE, +1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
+  fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   const int nvox = rows * g.n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
     const int r = e / g.n1, x = e - r * g.n1;
     const long long v = (row0 + r) * g.n1 + x;
     const R w = ell2[phase[v]] * scale;
-    for (int c = 0; c < nc; c++) rbuf[(r * nc + c) * g.n1 + x] *= w;
+#pragma unroll
+    for (int c = 0; c < NC; c++) rbuf[(r * NC + c) * g.n1 + x] *= w;
   }
   __syncthreads();
-  fft_lines<R, kXE, -1>(cbuf, pl, rows * nc, 1, g.M, true, tws, 2);
-  const int nout = rows * nc * g.P1;
+  fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
+  const int nout = rows * NC * g.P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
     const int l = e / g.P1, k = e - l * g.P1;
-    const int r = l / nc, c = l - r * nc;
+    const int r = l / NC, c = l - r * NC;
     const C2<R> zk = cbuf[l * g.M + (k == g.M ? 0 : k)];
     const C2<R> zm = cbuf[l * g.M + (k == 0 ? 0 : g.M - k)];
     const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
@@ -208,57 +216,66 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
 
 // ------------------------------------------------------ x1 prologues / epilogues
 // tau = C_T : p with the compact tangent descriptor
-//   desc = [c1, c2, m_0 .. m_{nc-1}],  tau = c1 tr(p) 1 + c2 dev(p) - m (m . p)
+//   desc = [c1, c2, m_0 .. m_{NC-1}],  tau = c1 tr(p) 1 + c2 dev(p) - m (m . p)
 // (c1 = (1-D) K, c2 = (1-D) 2 mu theta, m = sqrt((1-D) 2 mu thetabar) nhat).
 // Inside CG the direction is refreshed first: p <- r (iter 0) or r + beta p.
-template <typename R>
+template <typename R, int NC>
 struct ProTangent {
   R* p;
   const R* r;
   const R* desc;
   long long V;
-  int nc, nnormal;
   int update;
   R beta;
   bool first;
   __device__ void begin(const KrylovCtl* ctl) {
     if (ctl) { first = ctl->iter == 0; beta = (R)ctl->beta; }
   }
-  __device__ __forceinline__ void operator()(long long v, R* out) const {
-    R pv[6];
+  __device__ __forceinline__ void operator()(long long v, R (&out)[NC]) const {
+    constexpr int NN = NC == 6 ? 3 : 2;
+    R pv[NC];
     if (update) {
-      for (int c = 0; c < nc; c++) {
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
         const R rv = r[c * V + v];
         pv[c] = first ? rv : rv + beta * p[c * V + v];
         p[c * V + v] = pv[c];
       }
     } else {
-      for (int c = 0; c < nc; c++) pv[c] = p[c * V + v];
+#pragma unroll
+      for (int c = 0; c < NC; c++) pv[c] = p[c * V + v];
     }
     const R c1 = desc[v], c2 = desc[V + v];
+    R m[NC];
     R tr = R(0), mp = R(0);
-    for (int c = 0; c < nnormal; c++) tr += pv[c];
-    for (int c = 0; c < nc; c++) mp += desc[(2 + c) * V + v] * pv[c];
+#pragma unroll
+    for (int c = 0; c < NN; c++) tr += pv[c];
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      m[c] = desc[(2 + c) * V + v];
+      mp += m[c] * pv[c];
+    }
     const R third = tr * R(1.0 / 3.0);
-    for (int c = 0; c < nc; c++) {
-      R o = c2 * pv[c] - desc[(2 + c) * V + v] * mp;
-      if (c < nnormal) o += c1 * tr - c2 * third;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      R o = c2 * pv[c] - m[c] * mp;
+      if (c < NN) o += c1 * tr - c2 * third;
       out[c] = o;
     }
   }
 };
 
-// tau_c = f[map[c]][v] - mean[c]  (FP64 source fields)
-template <typename R>
+// tau_c = f[map[c]][v] - mean[map[c]]  (FP64 source fields)
+template <typename R, int NC>
 struct ProField64 {
   const double* f;
   const double* mean;   // device, may be null
   long long V;
-  int nc;
-  int map[6];
+  int map[NC];
   __device__ void begin(const KrylovCtl*) {}
-  __device__ __forceinline__ void operator()(long long v, R* out) const {
-    for (int c = 0; c < nc; c++) {
+  __device__ __forceinline__ void operator()(long long v, R (&out)[NC]) const {
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
       double x = f[map[c] * V + v];
       if (mean) x -= mean[map[c]];
       out[c] = (R)x;
@@ -266,36 +283,37 @@ struct ProField64 {
   }
 };
 
-template <typename R>
+template <typename R, int NC>
 struct EpiMatvec {       // Ap = val; acc0 += p . Ap
   R* Ap;
   const R* p;
   long long V;
-  int nc;
   __device__ void begin(const KrylovCtl*) {}
-  __device__ __forceinline__ void operator()(long long v, const R* val, double* acc) const {
-    for (int c = 0; c < nc; c++) {
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc) const {
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
       Ap[c * V + v] = val[c];
       acc[0] += (double)p[c * V + v] * (double)val[c];
     }
   }
 };
 
-template <typename R, typename RO>
+template <typename R, typename RO, int NC>
 struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
   RO* b;
   const double* mean_sig;   // full Mandel (6)
-  double mask[6];
-  double sbar[6];
-  int map[6];
+  double mask[NC];
+  double sbar[NC];
+  int map[NC];
   long long V;
-  int nc;
-  double dc[6];
+  double dc[NC];
   __device__ void begin(const KrylovCtl*) {
-    for (int c = 0; c < nc; c++) dc[c] = mask[c] * (mean_sig[map[c]] - sbar[c]);
+#pragma unroll
+    for (int c = 0; c < NC; c++) dc[c] = mask[c] * (mean_sig[map[c]] - sbar[c]);
   }
-  __device__ __forceinline__ void operator()(long long v, const R* val, double* acc) const {
-    for (int c = 0; c < nc; c++) {
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc) const {
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
       const double bv = -((double)val[c] + dc[c]);
       const RO br = (RO)bv;
       b[c * V + v] = br;
@@ -304,14 +322,14 @@ struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
   }
 };
 
-template <typename R>
+template <typename R, int NC>
 struct EpiStore64 {
   double* out;
   long long V;
-  int nc;
   __device__ void begin(const KrylovCtl*) {}
-  __device__ __forceinline__ void operator()(long long v, const R* val, double*) const {
-    for (int c = 0; c < nc; c++) out[c * V + v] = (double)val[c];
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double*) const {
+#pragma unroll
+    for (int c = 0; c < NC; c++) out[c * V + v] = (double)val[c];
   }
 };
 
@@ -328,7 +346,7 @@ static StrideInfo<R> stride_of(const Geo& g, int axis) {
 }
 
 template <typename R, int SIGN>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
                 long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
@@ -361,15 +379,16 @@ __device__ __forceinline__ void last_modes(const Geo& g, int q0, int col, int n,
   else { m1 = n; m2 = 0; }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads)
+template <typename R, int NC>
+__global__ void __launch_bounds__(kThreads, 2)
 k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
         long long astride, long long ostride, Mask6 mask, int dc_mode,
         const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
+  constexpr int nc = NC;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = pl.N, nc = g.nc;
+  const int N = pl.N;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = tws + N;
   const int q0 = blockIdx.x * tx;
@@ -393,16 +412,19 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
     C2<R> ph;
     symbol(g, t, m0, m1, m2, a, ph);
     const R a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
-    C2<R> tv[6];
+    C2<R> tv[NC];
+#pragma unroll
     for (int c = 0; c < nc; c++) tv[c] = buf[c * tile + e];
     if (a2 > R(0)) {
       const R inv = R(1) / sqrt(a2);
       R nv[3] = {a[0] * inv, a[1] * inv, a[2] * inv};
-      gamma_mode<R>(g.d, nv, tv);
+      gamma_mode<R>(NC == 6 ? 3 : 2, nv, tv);
     } else {
       const bool dc = (m0 == 0) && (m1 == 0) && (m2 == 0);
+#pragma unroll
       for (int c = 0; c < nc; c++) tv[c] = (dc && !dc_mode) ? cscale(tv[c], (R)mask.m[c]) : mk<R>(0, 0);
     }
+#pragma unroll
     for (int c = 0; c < nc; c++) buf[c * tile + e] = tv[c];
   }
   __syncthreads();
@@ -421,15 +443,16 @@ __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
 
 // Helmholtz: p <- M r + beta p (M = 1/(1 + <l^2>|k|^2)); W_j = k_j p; inverse
 // transform along the last axis.
-template <typename R>
-__global__ void __launch_bounds__(kThreads)
+template <typename R, int D>
+__global__ void __launch_bounds__(kThreads, 2)
 k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
          C2<R>* __restrict__ p, const C2<R>* __restrict__ r, int tx, long long astride,
          long long ostride, R ell2m, const KrylovCtl* __restrict__ ctl, int raw) {
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = pl.N, d = g.d;
+  const int N = pl.N;
+  constexpr int d = D;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = tws + N;
   const int q0 = blockIdx.x * tx;
@@ -471,8 +494,8 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
 
 // Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
 // partial Hermitian-weighted (p, y).
-template <typename R>
-__global__ void __launch_bounds__(kThreads)
+template <typename R, int D>
+__global__ void __launch_bounds__(kThreads, 2)
 k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C2<R>* __restrict__ W,
            const C2<R>* __restrict__ p, C2<R>* __restrict__ y, int tx, long long astride,
            long long ostride, double* __restrict__ part, int pstride,
@@ -480,7 +503,8 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = pl.N, d = g.d;
+  const int N = pl.N;
+  constexpr int d = D;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = tws + N;
   const int q0 = blockIdx.x * tx;
@@ -732,43 +756,87 @@ static size_t xsmem(const Geo& g, int nrows, int nc) {
 }
 static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrows - 1) / nrows); }
 
+// launch an x1 kernel K<E> with E = 4 or 16 as chosen in the launch config
+#define XLAUNCH(KT4, KT16, NCC, ...)                                          \
+  do {                                                                        \
+    const int nr = lc.nrows_c[NCC];                                           \
+    const size_t sm = xsmem<R>(g, nr, NCC);                                   \
+    if (lc.xe_c[NCC] == 4) {                                                  \
+      auto k = KT4;                                                           \
+      set_smem(k, sm);                                                        \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                     \
+    } else {                                                                  \
+      auto k = KT16;                                                          \
+      set_smem(k, sm);                                                        \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                     \
+    }                                                                         \
+  } while (0)
+
+template <typename R, int NC>
+static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
+                            const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl) {
+  ProTangent<R, NC> pro;
+  pro.p = p; pro.r = r; pro.desc = desc; pro.V = g.V;
+  pro.update = ctl != nullptr; pro.beta = R(0); pro.first = true;
+  XLAUNCH((k_xfwd<R, NC, 4, ProTangent<R, NC>>), (k_xfwd<R, NC, 16, ProTangent<R, NC>>), NC,
+          g, t.plan_x, t.tw[0], S, nr, pro, ctl);
+}
+
 template <typename R>
 void Ops<R>::xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
                           const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl) {
-  ProTangent<R> pro;
-  pro.p = p; pro.r = r; pro.desc = desc; pro.V = g.V; pro.nc = g.nc;
-  pro.nnormal = g.d == 3 ? 3 : 2; pro.update = ctl != nullptr; pro.beta = R(0); pro.first = true;
-  const int nr = lc.nrows_c[g.nc];
-  const size_t sm = xsmem<R>(g, nr, g.nc);
-  auto k = k_xfwd<R, ProTangent<R>>;
-  set_smem(k, sm);
-  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, g.nc, nr, pro, ctl);
+  if (g.nc == 6) xfwd_tangent_nc<R, 6>(g, t, lc, st, p, r, desc, S, ctl);
+  else xfwd_tangent_nc<R, 3>(g, t, lc, st, p, r, desc, S, ctl);
+}
+
+template <typename R, int NC>
+static void xfwd_field64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                            const double* f, const int* fmap, const double* mean_dev, C2<R>* S) {
+  ProField64<R, NC> pro;
+  pro.f = f; pro.mean = mean_dev; pro.V = g.V;
+  for (int c = 0; c < NC; c++) pro.map[c] = fmap[c];
+  XLAUNCH((k_xfwd<R, NC, 4, ProField64<R, NC>>), (k_xfwd<R, NC, 16, ProField64<R, NC>>), NC,
+          g, t.plan_x, t.tw[0], S, nr, pro, nullptr);
 }
 
 template <typename R>
 void Ops<R>::xfwd_field64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                           const double* f, int ncomp, const int* fmap, const double* mean_dev, C2<R>* S) {
-  ProField64<R> pro;
-  pro.f = f; pro.mean = mean_dev; pro.V = g.V; pro.nc = ncomp;
-  for (int c = 0; c < 6; c++) pro.map[c] = c < ncomp ? fmap[c] : 0;
-  const int nr = lc.nrows_c[ncomp];
-  const size_t sm = xsmem<R>(g, nr, ncomp);
-  auto k = k_xfwd<R, ProField64<R>>;
-  set_smem(k, sm);
-  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, ncomp, nr, pro, nullptr);
+  if (ncomp == 6) xfwd_field64_nc<R, 6>(g, t, lc, st, f, fmap, mean_dev, S);
+  else if (ncomp == 3) xfwd_field64_nc<R, 3>(g, t, lc, st, f, fmap, mean_dev, S);
+  else xfwd_field64_nc<R, 1>(g, t, lc, st, f, fmap, mean_dev, S);
+}
+
+template <typename R, int NC>
+static void xinv_matvec_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                           const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl) {
+  EpiMatvec<R, NC> epi;
+  epi.Ap = Ap; epi.p = p; epi.V = g.V;
+  XLAUNCH((k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1>), (k_xinv<R, NC, 16, EpiMatvec<R, NC>, 1>), NC,
+          g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, ctl);
 }
 
 template <typename R>
 void Ops<R>::xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                          const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl) {
-  EpiMatvec<R> epi;
-  epi.Ap = Ap; epi.p = p; epi.V = g.V; epi.nc = g.nc;
-  const int nr = lc.nrows_c[g.nc];
-  const size_t sm = xsmem<R>(g, nr, g.nc);
-  auto k = k_xinv<R, EpiMatvec<R>, 1>;
-  set_smem(k, sm);
-  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, g.nc, nr, R(2.0 / (double)g.V), epi,
-                                        part, lc.max_blocks, ctl);
+  if (g.nc == 6) xinv_matvec_nc<R, 6>(g, t, lc, st, S, Ap, p, part, ctl);
+  else xinv_matvec_nc<R, 3>(g, t, lc, st, S, Ap, p, part, ctl);
+}
+
+template <typename R, typename RO, int NC>
+static void xinv_residual_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                             const C2<R>* S, RO* b, const double* mean_sig_dev, const double* mask,
+                             const double* sbar, double* part) {
+  EpiResidual<R, RO, NC> epi;
+  epi.b = b; epi.mean_sig = mean_sig_dev; epi.V = g.V;
+  for (int c = 0; c < NC; c++) {
+    epi.mask[c] = mask[c];
+    epi.sbar[c] = sbar[c];
+    epi.map[c] = g.cmap[c];
+    epi.dc[c] = 0.0;
+  }
+  XLAUNCH((k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1>), (k_xinv<R, NC, 16, EpiResidual<R, RO, NC>, 1>), NC,
+          g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, nullptr);
 }
 
 template <typename R>
@@ -776,43 +844,36 @@ template <typename RO>
 void Ops<R>::xinv_residual(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                            const C2<R>* S, RO* b, const double* mean_sig_dev, const double* mask,
                            const double* sbar, double* part) {
-  EpiResidual<R, RO> epi;
-  epi.b = b; epi.mean_sig = mean_sig_dev; epi.V = g.V; epi.nc = g.nc;
-  for (int c = 0; c < 6; c++) {
-    epi.mask[c] = c < g.nc ? mask[c] : 0.0;
-    epi.sbar[c] = c < g.nc ? sbar[c] : 0.0;
-    epi.map[c] = g.cmap[c];
-  }
-  const int nr = lc.nrows_c[g.nc];
-  const size_t sm = xsmem<R>(g, nr, g.nc);
-  auto k = k_xinv<R, EpiResidual<R, RO>, 1>;
-  set_smem(k, sm);
-  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, g.nc, nr, R(2.0 / (double)g.V), epi,
-                                        part, lc.max_blocks, nullptr);
+  if (g.nc == 6) xinv_residual_nc<R, RO, 6>(g, t, lc, st, S, b, mean_sig_dev, mask, sbar, part);
+  else xinv_residual_nc<R, RO, 3>(g, t, lc, st, S, b, mean_sig_dev, mask, sbar, part);
+}
+
+template <typename R, int NC>
+static void xinv_store64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                            const C2<R>* S, double* out) {
+  EpiStore64<R, NC> epi;
+  epi.out = out; epi.V = g.V;
+  XLAUNCH((k_xinv<R, NC, 4, EpiStore64<R, NC>, 0>), (k_xinv<R, NC, 16, EpiStore64<R, NC>, 0>), NC,
+          g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, nullptr, 0, nullptr);
 }
 
 template <typename R>
 void Ops<R>::xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                           const C2<R>* S, int ncomp, double* out) {
-  EpiStore64<R> epi;
-  epi.out = out; epi.V = g.V; epi.nc = ncomp;
-  const int nr = lc.nrows_c[ncomp];
-  const size_t sm = xsmem<R>(g, nr, ncomp);
-  auto k = k_xinv<R, EpiStore64<R>, 0>;
-  set_smem(k, sm);
-  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], S, ncomp, nr, R(2.0 / (double)g.V), epi,
-                                        nullptr, 0, nullptr);
+  if (ncomp == 6) xinv_store64_nc<R, 6>(g, t, lc, st, S, out);
+  else if (ncomp == 3) xinv_store64_nc<R, 3>(g, t, lc, st, S, out);
+  else xinv_store64_nc<R, 1>(g, t, lc, st, S, out);
 }
 
 template <typename R>
 void Ops<R>::xmid_ell(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* W,
                       const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl) {
-  const int nr = lc.nrows_c[g.d];
-  const size_t sm = xsmem<R>(g, nr, g.d);
-  auto k = k_xmid<R>;
-  set_smem(k, sm);
-  k<<<xgrid(g, nr), kThreads, sm, st>>>(g, t.plan_x, t.tw[0], W, g.d, nr, R(2.0 / (double)g.V), phase,
-                                        ell2_tab, ctl);
+  if (g.d == 3)
+    XLAUNCH((k_xmid<R, 3, 4>), (k_xmid<R, 3, 16>), 3, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
+            ell2_tab, ctl);
+  else
+    XLAUNCH((k_xmid<R, 2, 4>), (k_xmid<R, 2, 16>), 2, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
+            ell2_tab, ctl);
 }
 
 template <typename R>
@@ -845,9 +906,15 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   Mask6 m;
   for (int c = 0; c < 6; c++) m.m[c] = c < g.nc ? stress_mask[c] : 0.f;
-  auto k = k_gamma<R>;
-  set_smem(k, sm);
-  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
+  if (g.nc == 6) {
+    auto k = k_gamma<R, 6>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
+  } else {
+    auto k = k_gamma<R, 3>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
+  }
 }
 
 template <typename R>
@@ -859,10 +926,17 @@ void Ops<R>::helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
   const int tx = lc.tx;
   const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.d * tx);
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  auto k = k_expand<R>;
-  set_smem(k, sm);
-  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
-                                raw);
+  if (g.d == 3) {
+    auto k = k_expand<R, 3>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
+                                  raw);
+  } else {
+    auto k = k_expand<R, 2>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
+                                  raw);
+  }
 }
 
 template <typename R>
@@ -874,10 +948,17 @@ void Ops<R>::helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const int tx = lc.tx;
   const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.d * tx);
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  auto k = k_contract<R>;
-  set_smem(k, sm);
-  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
-                                lc.max_blocks, ctl);
+  if (g.d == 3) {
+    auto k = k_contract<R, 3>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
+                                  lc.max_blocks, ctl);
+  } else {
+    auto k = k_contract<R, 2>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
+                                  lc.max_blocks, ctl);
+  }
 }
 
 template <typename R>

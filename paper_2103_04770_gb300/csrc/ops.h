@@ -40,6 +40,7 @@ struct Tables {
 // Launch configuration chosen once per grid.
 struct LaunchCfg {
   int nrows_c[7];        // rows per CTA of the x1 pass for 1..6 components
+  int xe_c[7];           // FFT elements staged per thread in that x1 pass (4 or 16)
   int tx;                // q1 columns per CTA of the strided passes
   int n_ew_blocks;       // CTAs of element-wise kernels
   int max_blocks;        // upper bound of CTAs of any reducing kernel
