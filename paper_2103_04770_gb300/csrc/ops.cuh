@@ -333,6 +333,71 @@ struct EpiStore64 {
   }
 };
 
+// twiddle table bytes at the head of a strided kernel's shared memory,
+// rounded up so that the tile behind it starts on a 16-byte boundary
+template <typename R>
+__host__ __device__ __forceinline__ size_t tw_bytes(int N) {
+  return ((size_t)N * sizeof(C2<R>) + 15) & ~(size_t)15;
+}
+
+// ------------------------------------------------ tile staging (cp.async)
+// Tiles of the strided passes are rows of `cols` complex entries (row n of
+// component c at src + c*cstride + n*astride) held in shared memory as
+// buf[c][n][tx].  Loads go through cp.async in 16-byte chunks (8 bytes for
+// an odd FP32 tail) so that each thread keeps many copies in flight; rows
+// start on 16-byte boundaries (padded rows, even tile starts).
+__device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sm, const void* gm) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename R>
+__device__ __forceinline__ void tile_load_async(C2<R>* buf, const C2<R>* src, int ncomp, long long cstride,
+                                                int N, long long astride, int tx, int cols) {
+  constexpr int PER = 16 / (int)sizeof(C2<R>);
+  const int cpr = (cols + PER - 1) / PER;
+  const int total = ncomp * N * cpr;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int row = e / cpr, ch = e - row * cpr;
+    const int c = row / N, n = row - c * N;
+    const int col = ch * PER;
+    C2<R>* d = buf + (c * N + n) * tx + col;
+    const C2<R>* sp = src + c * cstride + n * astride + col;
+    if (PER == 2 && col + 1 >= cols) cp_async8(d, sp);
+    else cp_async16(d, sp);
+  }
+  cp_async_wait_all();
+}
+
+template <typename R>
+__device__ __forceinline__ void tile_store(const C2<R>* buf, C2<R>* dst, int ncomp, long long cstride, int N,
+                                           long long astride, int tx, int cols) {
+  constexpr int PER = 16 / (int)sizeof(C2<R>);
+  const int cpr = (cols + PER - 1) / PER;
+  const int total = ncomp * N * cpr;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int row = e / cpr, ch = e - row * cpr;
+    const int c = row / N, n = row - c * N;
+    const int col = ch * PER;
+    const C2<R>* sp = buf + (c * N + n) * tx + col;
+    C2<R>* d = dst + c * cstride + n * astride + col;
+    if (PER == 2 && col + 1 >= cols) {
+      d[0] = sp[0];
+    } else if (PER == 2) {
+      *reinterpret_cast<float4*>(d) = *reinterpret_cast<const float4*>(sp);
+    } else {
+      *reinterpret_cast<double2*>(d) = *reinterpret_cast<const double2*>(sp);
+    }
+  }
+}
+
 // ============================================================ strided passes
 template <typename R>
 struct StrideInfo { long long astride, ostride; int N; };
@@ -354,21 +419,15 @@ k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restri
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = pl.N;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
-  C2<R>* buf = tws + N;
+  C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   C2<R>* base = S + blockIdx.z * g.sstride + blockIdx.y * ostride + q0;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  for (int e = threadIdx.x; e < N * tx; e += kThreads) {
-    const int n = e / tx, col = e - n * tx;
-    if (col < cols) buf[e] = base[n * astride + col];
-  }
+  tile_load_async(buf, base, 1, 0, N, astride, tx, cols);
   __syncthreads();
   fft_lines<R, E, SIGN>(buf, pl, cols, tx, 1, false, tws, 1);
-  for (int e = threadIdx.x; e < N * tx; e += kThreads) {
-    const int n = e / tx, col = e - n * tx;
-    if (col < cols) base[n * astride + col] = buf[e];
-  }
+  tile_store(buf, base, 1, 0, N, astride, tx, cols);
 }
 
 // mode indices of element (n, col) of a last-axis tile
@@ -390,17 +449,13 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = pl.N;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
-  C2<R>* buf = tws + N;
+  C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   C2<R>* base = S + blockIdx.y * ostride + q0;
   const int tile = N * tx;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  for (int e = threadIdx.x; e < nc * tile; e += kThreads) {
-    const int c = e / tile, rem = e - c * tile;
-    const int n = rem / tx, col = rem - n * tx;
-    if (col < cols) buf[e] = base[c * g.sstride + n * astride + col];
-  }
+  tile_load_async(buf, base, nc, g.sstride, N, astride, tx, cols);
   __syncthreads();
   for (int c = 0; c < nc; c++) fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
   for (int e = threadIdx.x; e < tile; e += kThreads) {
@@ -429,11 +484,7 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   }
   __syncthreads();
   for (int c = 0; c < nc; c++) fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
-  for (int e = threadIdx.x; e < nc * tile; e += kThreads) {
-    const int c = e / tile, rem = e - c * tile;
-    const int n = rem / tx, col = rem - n * tx;
-    if (col < cols) base[c * g.sstride + n * astride + col] = buf[e];
-  }
+  tile_store(buf, base, nc, g.sstride, N, astride, tx, cols);
 }
 
 template <typename R>
@@ -454,7 +505,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   const int N = pl.N;
   constexpr int d = D;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
-  C2<R>* buf = tws + N;
+  C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   const long long off = blockIdx.y * ostride + q0;
@@ -485,11 +536,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   }
   __syncthreads();
   for (int j = 0; j < d; j++) fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
-  for (int e = threadIdx.x; e < d * tile; e += kThreads) {
-    const int j = e / tile, rem = e - j * tile;
-    const int n = rem / tx, col = rem - n * tx;
-    if (col < cols) W[j * g.sstride + off + n * astride + col] = buf[e];
-  }
+  tile_store(buf, W + off, d, g.sstride, N, astride, tx, cols);
 }
 
 // Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
@@ -506,17 +553,13 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   const int N = pl.N;
   constexpr int d = D;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
-  C2<R>* buf = tws + N;
+  C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   const long long off = blockIdx.y * ostride + q0;
   const int tile = N * tx;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  for (int e = threadIdx.x; e < d * tile; e += kThreads) {
-    const int j = e / tile, rem = e - j * tile;
-    const int n = rem / tx, col = rem - n * tx;
-    if (col < cols) buf[e] = W[j * g.sstride + off + n * astride + col];
-  }
+  tile_load_async(buf, W + off, d, g.sstride, N, astride, tx, cols);
   __syncthreads();
   for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   double acc[1] = {0.0};
@@ -882,7 +925,7 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
   const int tx = lc.tx;
-  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + tx);
+  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? g.n3 : g.n2, ncomp);
   if (sign < 0) {
     auto k = k_strided_plain<R, -1>;
@@ -902,7 +945,7 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
   const int tx = lc.tx;
-  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.nc * tx);
+  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.nc * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   Mask6 m;
   for (int c = 0; c < 6; c++) m.m[c] = c < g.nc ? stress_mask[c] : 0.f;
@@ -924,7 +967,7 @@ void Ops<R>::helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
   const int tx = lc.tx;
-  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.d * tx);
+  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   if (g.d == 3) {
     auto k = k_expand<R, 3>;
@@ -946,7 +989,7 @@ void Ops<R>::helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
   const int tx = lc.tx;
-  const size_t sm = (size_t)si.N * sizeof(C2<R>) * (1 + (size_t)g.d * tx);
+  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   if (g.d == 3) {
     auto k = k_contract<R, 3>;
