@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "fft.cuh"
+#include "fft_ct.cuh"
 #include "ops.h"
 
 namespace rvk {
@@ -89,7 +90,8 @@ template <typename R, int E> struct XMinBlocks {
   static constexpr int v = E <= 4 ? (sizeof(R) == 4 ? 3 : 2) : 1;
 };
 
-template <typename R, int NC, int E, class PRO>
+// MCT > 0: compile-time row of MCT = N1/2 complex points, one row per CTA.
+template <typename R, int NC, int E, class PRO, int MCT = 0>
 __global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
 k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, int nrows, PRO pro,
        const KrylovCtl* __restrict__ ctl) {
@@ -112,7 +114,8 @@ k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, 
     for (int c = 0; c < NC; c++) rbuf[(r * NC + c) * g.n1 + x] = val[c];
   }
   __syncthreads();
-  fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, -1, true, 2>(cbuf, tws);
+  else fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   const int nout = rows * NC * g.P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
     const int l = e / g.P1, k = e - l * g.P1;
@@ -142,7 +145,33 @@ __device__ __forceinline__ void xinv_pre(const Geo& g, const C2<R>* __restrict__
   }
 }
 
-template <typename R, int NC, int E, class EPI, int NS>
+// Offset of the spectrum staging area behind the x1 pass buffers.
+template <typename R>
+__host__ __device__ __forceinline__ size_t xstage_off(int n1, int rows, int nc) {
+  return (((size_t)n1 * sizeof(C2<R>) + (size_t)rows * nc * n1 * sizeof(R)) + 15) & ~(size_t)15;
+}
+
+// Stage the spectrum rows of the CTA with cp.async (xs[c][r][ps]), then
+// split them into the half-length complex sequences (cbuf line r*NC + c).
+template <typename R, int NC>
+__device__ __forceinline__ void xinv_pre_staged(const Geo& g, const C2<R>* __restrict__ S, long long row0,
+                                                int rows, const C2<R>* tws, C2<R>* cbuf, C2<R>* xs) {
+  tile_load_async(xs, S + row0 * g.ps, NC, g.sstride, rows, (long long)g.ps, g.ps, g.P1);
+  __syncthreads();
+  const int nin = rows * NC * g.M;
+  for (int e = threadIdx.x; e < nin; e += kThreads) {
+    const int l = e / g.M, k = e - l * g.M;
+    const int r = l / NC, c = l - r * NC;
+    const C2<R>* row = xs + (c * rows + r) * g.ps;
+    const C2<R> xk = row[k], xm = row[g.M - k];
+    const C2<R> E = mk<R>(R(0.5) * (xk.x + xm.x), R(0.5) * (xk.y - xm.y));
+    const C2<R> Dd = mk<R>(R(0.5) * (xk.x - xm.x), R(0.5) * (xk.y + xm.y));
+    const C2<R> O = cmul(Dd, conj_(tws[k]));
+    cbuf[l * g.M + k] = mk<R>(E.x - O.y, E.y + O.x);
+  }
+}
+
+template <typename R, int NC, int E, class EPI, int NS, int MCT = 0>
 __global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
 k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict__ S, int nrows, R scale,
        EPI epi, double* __restrict__ part, int pstride, const KrylovCtl* __restrict__ ctl) {
@@ -151,13 +180,14 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
   C2<R>* cbuf = reinterpret_cast<C2<R>*>(rbuf);
+  C2<R>* xs = reinterpret_cast<C2<R>*>(smraw + xstage_off<R>(g.n1, nrows, NC));
   const long long row0 = (long long)blockIdx.x * nrows;
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
+  xinv_pre_staged<R, NC>(g, S, row0, rows, tws, cbuf, xs);
   __syncthreads();
-  xinv_pre(g, S, row0, rows, NC, tws, cbuf);
-  __syncthreads();
-  fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, +1, true, 2>(cbuf, tws);
+  else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   constexpr int NSA = NS > 0 ? NS : 1;
   double acc[NSA];
 #pragma unroll
@@ -176,7 +206,7 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
 }
 
 // C2R -> l^2(x) * scale -> R2C of the NC = d gradient components (Algorithm 2, GC).
-template <typename R, int NC, int E>
+template <typename R, int NC, int E, int MCT = 0>
 __global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
 k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, int nrows, R scale,
        const uint8_t* __restrict__ phase, const R* __restrict__ ell2, const KrylovCtl* __restrict__ ctl) {
@@ -185,13 +215,14 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
   C2<R>* cbuf = reinterpret_cast<C2<R>*>(rbuf);
+  C2<R>* xs = reinterpret_cast<C2<R>*>(smraw + xstage_off<R>(g.n1, nrows, NC));
   const long long row0 = (long long)blockIdx.x * nrows;
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
+  xinv_pre_staged<R, NC>(g, W, row0, rows, tws, cbuf, xs);
   __syncthreads();
-  xinv_pre(g, W, row0, rows, NC, tws, cbuf);
-  __syncthreads();
-  fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, +1, true, 2>(cbuf, tws);
+  else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   const int nvox = rows * g.n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
     const int r = e / g.n1, x = e - r * g.n1;
@@ -201,7 +232,8 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
     for (int c = 0; c < NC; c++) rbuf[(r * NC + c) * g.n1 + x] *= w;
   }
   __syncthreads();
-  fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, -1, true, 2>(cbuf, tws);
+  else fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   const int nout = rows * NC * g.P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
     const int l = e / g.P1, k = e - l * g.P1;
@@ -410,7 +442,8 @@ static StrideInfo<R> stride_of(const Geo& g, int axis) {
   return s;
 }
 
-template <typename R, int SIGN>
+// NCT > 0: compile-time axis length NCT and tile width TXC.
+template <typename R, int SIGN, int NCT = 0, int TXC = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
                 long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
@@ -426,7 +459,8 @@ k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restri
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
   tile_load_async(buf, base, 1, 0, N, astride, tx, cols);
   __syncthreads();
-  fft_lines<R, E, SIGN>(buf, pl, cols, tx, 1, false, tws, 1);
+  if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, SIGN, false, 1>(buf, tws);
+  else fft_lines<R, E, SIGN>(buf, pl, cols, tx, 1, false, tws, 1);
   tile_store(buf, base, 1, 0, N, astride, tx, cols);
 }
 
@@ -438,7 +472,7 @@ __device__ __forceinline__ void last_modes(const Geo& g, int q0, int col, int n,
   else { m1 = n; m2 = 0; }
 }
 
-template <typename R, int NC>
+template <typename R, int NC, int NCT = 0, int TXC = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
         long long astride, long long ostride, Mask6 mask, int dc_mode,
@@ -457,7 +491,10 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
   tile_load_async(buf, base, nc, g.sstride, N, astride, tx, cols);
   __syncthreads();
-  for (int c = 0; c < nc; c++) fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  for (int c = 0; c < nc; c++) {
+    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, -1, false, 1>(buf + c * tile, tws);
+    else fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  }
   for (int e = threadIdx.x; e < tile; e += kThreads) {
     const int n = e / tx, col = e - n * tx;
     if (col >= cols) continue;
@@ -483,7 +520,10 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
     for (int c = 0; c < nc; c++) buf[c * tile + e] = tv[c];
   }
   __syncthreads();
-  for (int c = 0; c < nc; c++) fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  for (int c = 0; c < nc; c++) {
+    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, +1, false, 1>(buf + c * tile, tws);
+    else fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  }
   tile_store(buf, base, nc, g.sstride, N, astride, tx, cols);
 }
 
@@ -800,20 +840,30 @@ static size_t xsmem(const Geo& g, int nrows, int nc) {
 static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrows - 1) / nrows); }
 
 // launch an x1 kernel K<E> with E = 4 or 16 as chosen in the launch config
-#define XLAUNCH(KT4, KT16, NCC, ...)                                          \
-  do {                                                                        \
-    const int nr = lc.nrows_c[NCC];                                           \
-    const size_t sm = xsmem<R>(g, nr, NCC);                                   \
-    if (lc.xe_c[NCC] == 4) {                                                  \
-      auto k = KT4;                                                           \
-      set_smem(k, sm);                                                        \
-      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                     \
-    } else {                                                                  \
-      auto k = KT16;                                                          \
-      set_smem(k, sm);                                                        \
-      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                     \
-    }                                                                         \
+// x1 launch: compile-time variant KCT for rows of 128 complex points (N1 =
+// 256) at one row per CTA, else KT4 / KT16 by the staged-element count
+#define XLAUNCH(KCT, KT4, KT16, NCC, STAGE, ...)                                                        \
+  do {                                                                                                  \
+    const int nr = lc.nrows_c[NCC];                                                                     \
+    const size_t sm = STAGE ? xstage_off<R>(g.n1, nr, NCC) + (size_t)nr * NCC * g.ps * sizeof(C2<R>)   \
+                            : xsmem<R>(g, nr, NCC);                                                     \
+    if (lc.xe_c[NCC] == 4 && g.M == 128 && nr == 1) {                                                   \
+      auto k = KCT;                                                                                     \
+      set_smem(k, sm);                                                                                  \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
+    } else if (lc.xe_c[NCC] == 4) {                                                                     \
+      auto k = KT4;                                                                                     \
+      set_smem(k, sm);                                                                                  \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
+    } else {                                                                                            \
+      auto k = KT16;                                                                                    \
+      set_smem(k, sm);                                                                                  \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
+    }                                                                                                   \
   } while (0)
+
+// tile width of the compile-time strided passes on a 256-point axis
+template <typename R> struct Tx256 { static constexpr int v = StridedE<R>::E * kThreads / 256; };
 
 template <typename R, int NC>
 static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
@@ -821,7 +871,8 @@ static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
   ProTangent<R, NC> pro;
   pro.p = p; pro.r = r; pro.desc = desc; pro.V = g.V;
   pro.update = ctl != nullptr; pro.beta = R(0); pro.first = true;
-  XLAUNCH((k_xfwd<R, NC, 4, ProTangent<R, NC>>), (k_xfwd<R, NC, 16, ProTangent<R, NC>>), NC,
+  XLAUNCH((k_xfwd<R, NC, 4, ProTangent<R, NC>, 128>), (k_xfwd<R, NC, 4, ProTangent<R, NC>>),
+          (k_xfwd<R, NC, 16, ProTangent<R, NC>>), NC, false,
           g, t.plan_x, t.tw[0], S, nr, pro, ctl);
 }
 
@@ -838,7 +889,8 @@ static void xfwd_field64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
   ProField64<R, NC> pro;
   pro.f = f; pro.mean = mean_dev; pro.V = g.V;
   for (int c = 0; c < NC; c++) pro.map[c] = fmap[c];
-  XLAUNCH((k_xfwd<R, NC, 4, ProField64<R, NC>>), (k_xfwd<R, NC, 16, ProField64<R, NC>>), NC,
+  XLAUNCH((k_xfwd<R, NC, 4, ProField64<R, NC>, 128>), (k_xfwd<R, NC, 4, ProField64<R, NC>>),
+          (k_xfwd<R, NC, 16, ProField64<R, NC>>), NC, false,
           g, t.plan_x, t.tw[0], S, nr, pro, nullptr);
 }
 
@@ -855,7 +907,8 @@ static void xinv_matvec_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
                            const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl) {
   EpiMatvec<R, NC> epi;
   epi.Ap = Ap; epi.p = p; epi.V = g.V;
-  XLAUNCH((k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1>), (k_xinv<R, NC, 16, EpiMatvec<R, NC>, 1>), NC,
+  XLAUNCH((k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1, 128>), (k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1>),
+          (k_xinv<R, NC, 16, EpiMatvec<R, NC>, 1>), NC, true,
           g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, ctl);
 }
 
@@ -878,8 +931,8 @@ static void xinv_residual_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& 
     epi.map[c] = g.cmap[c];
     epi.dc[c] = 0.0;
   }
-  XLAUNCH((k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1>), (k_xinv<R, NC, 16, EpiResidual<R, RO, NC>, 1>), NC,
-          g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, nullptr);
+  XLAUNCH((k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1, 128>), (k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1>),
+          (k_xinv<R, NC, 16, EpiResidual<R, RO, NC>, 1>), NC, true, g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, nullptr);
 }
 
 template <typename R>
@@ -896,7 +949,8 @@ static void xinv_store64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
                             const C2<R>* S, double* out) {
   EpiStore64<R, NC> epi;
   epi.out = out; epi.V = g.V;
-  XLAUNCH((k_xinv<R, NC, 4, EpiStore64<R, NC>, 0>), (k_xinv<R, NC, 16, EpiStore64<R, NC>, 0>), NC,
+  XLAUNCH((k_xinv<R, NC, 4, EpiStore64<R, NC>, 0, 128>), (k_xinv<R, NC, 4, EpiStore64<R, NC>, 0>),
+          (k_xinv<R, NC, 16, EpiStore64<R, NC>, 0>), NC, true,
           g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, nullptr, 0, nullptr);
 }
 
@@ -912,10 +966,10 @@ template <typename R>
 void Ops<R>::xmid_ell(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* W,
                       const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl) {
   if (g.d == 3)
-    XLAUNCH((k_xmid<R, 3, 4>), (k_xmid<R, 3, 16>), 3, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
+    XLAUNCH((k_xmid<R, 3, 4, 128>), (k_xmid<R, 3, 4>), (k_xmid<R, 3, 16>), 3, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
             ell2_tab, ctl);
   else
-    XLAUNCH((k_xmid<R, 2, 4>), (k_xmid<R, 2, 16>), 2, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
+    XLAUNCH((k_xmid<R, 2, 4, 128>), (k_xmid<R, 2, 4>), (k_xmid<R, 2, 16>), 2, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
             ell2_tab, ctl);
 }
 
@@ -927,14 +981,28 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const int tx = lc.tx;
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? g.n3 : g.n2, ncomp);
+  constexpr int TXC = Tx256<R>::v;
+  const bool ct = si.N == 256 && tx == TXC;
   if (sign < 0) {
-    auto k = k_strided_plain<R, -1>;
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    if (ct) {
+      auto k = k_strided_plain<R, -1, 256, TXC>;
+      set_smem(k, sm);
+      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    } else {
+      auto k = k_strided_plain<R, -1>;
+      set_smem(k, sm);
+      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    }
   } else {
-    auto k = k_strided_plain<R, 1>;
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    if (ct) {
+      auto k = k_strided_plain<R, 1, 256, TXC>;
+      set_smem(k, sm);
+      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    } else {
+      auto k = k_strided_plain<R, 1>;
+      set_smem(k, sm);
+      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    }
   }
 }
 
@@ -949,7 +1017,12 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   Mask6 m;
   for (int c = 0; c < 6; c++) m.m[c] = c < g.nc ? stress_mask[c] : 0.f;
-  if (g.nc == 6) {
+  constexpr int TXC = Tx256<R>::v;
+  if (g.nc == 6 && si.N == 256 && tx == TXC) {
+    auto k = k_gamma<R, 6, 256, TXC>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
+  } else if (g.nc == 6) {
     auto k = k_gamma<R, 6>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);

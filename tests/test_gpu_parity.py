@@ -127,7 +127,9 @@ def test_return_map_and_tangent(n, prec):
 
 GAMMA_GRIDS = [(32, 30), (40, 16), (2, 2), (6, 5), (16, 12, 10), (12, 15, 8), (8, 8, 8), (4, 3, 5),
                # several q1 tiles per line and two-stage radix-8 axes
-               (96, 20), (128, 64), (80, 12, 10), (64, 64, 16), (64, 24, 64)]
+               (96, 20), (128, 64), (80, 12, 10), (64, 64, 16), (64, 24, 64),
+               # compile-time FFT paths: N1 = 256 rows, 256-point y and last axes
+               (256, 256), (256, 8, 8), (16, 256, 8), (16, 8, 256)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -152,7 +154,8 @@ def test_apply_gamma(n, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n", [(24, 20), (40, 15), (8, 6, 10), (12, 15, 8), (96, 20), (64, 16, 24)])
+@pytest.mark.parametrize("n", [(24, 20), (40, 15), (8, 6, 10), (12, 15, 8), (96, 20), (64, 16, 24),
+                               (256, 8, 8), (16, 8, 256)])
 def test_matvec_and_cg(n, prec):
     g = O.Grid(n)
     d = g.d
