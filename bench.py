@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--grid", default=None, help="N1,N2,N3 instead of the n^3 cube (profiling shapes)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
@@ -51,14 +52,15 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n):
+def workload(n, grid=None):
     import rve_inputs as I
-    cfg = I.config_3d_spheres(N=n, radius=10.0, vf=0.25, seed=0, ell_vox=4.0, n_incr=40, dE=1e-3)
+    g = tuple(int(x) for x in grid.split(",")) if grid else None
+    cfg = I.config_3d_spheres(N=n, radius=10.0, vf=0.25, seed=0, ell_vox=4.0, n_incr=40, dE=1e-3, grid=g)
     return cfg
 
 
 def workload_config(cfg, precision):
-    return {"workload": "3d_spheres_%d" % cfg.n[0], "grid": list(cfg.n), "voxels": int(np.prod(cfg.n)),
+    return {"workload": cfg.name, "grid": list(cfg.n), "voxels": int(np.prod(cfg.n)),
             "spheres": cfg.meta["count"], "radius_vox": cfg.meta["radius"],
             "vf": round(cfg.meta["vf_voxel"], 4), "seed": cfg.meta["seed"], "ell_matrix_vox": 4.0,
             "load": "uniaxial E11, 40 x 1e-3, Sigma_other = 0", "precision": precision,
@@ -154,7 +156,7 @@ def run_ours(args, rank, ws, dist):
     torch.cuda.init()
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
-    cfg = workload(args.n)
+    cfg = workload(args.n, args.grid)
     V = int(np.prod(cfg.n))
     prec = pkg.RVE_MIXED if args.precision == "mixed" else pkg.RVE_FP64
 
@@ -302,7 +304,7 @@ def cpu_threads():
 def run_reference(args, rank, ws, dist):
     """The oracle, as it stands, on the host cores: each step is one
     mechanical CG iteration of the oracle on the full workload."""
-    cfg = workload(args.n)
+    cfg = workload(args.n, args.grid)
     if rank != 0:
         return None, cfg
     from oracle import rve_oracle as O

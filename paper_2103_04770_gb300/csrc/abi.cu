@@ -466,7 +466,7 @@ struct Alg {
       for (int i = 0; i < chunk; i++) {
         helm_matvec(h, t, j, hp, hr, hy, h->ctl, 0);
         LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbl, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
-        LAUNCHB(h, KC_CG_UPDATE, 6.0 * g.nc * VV(h) * RS, Op::pcg_update(g, t, h->lc, h->st, hx, hr, hp, hy, h->ell2_mean[j], h->part, h->ctl));
+        LAUNCHB(h, KC_PCG_UPDATE, 6.0 * VS(h) * CS, Op::pcg_update(g, t, h->lc, h->st, hx, hr, hp, hy, h->ell2_mean[j], h->part, h->ctl));
         LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_BETA, h->ctl, nullptr, 1.0));
       }
       int s = sync_read(h);

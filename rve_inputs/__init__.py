@@ -236,16 +236,18 @@ def config_mesh_objectivity(N, n_incr=50, dE=1e-3):
 
 
 def config_3d_spheres(N=256, radius=10.0, vf=0.25, seed=0, ell_vox=4.0,
-                      n_incr=40, dE=1e-3, precision=1, count=None):
+                      n_incr=40, dE=1e-3, precision=1, count=None, grid=None):
     """3D RVE of random non-overlapping elastic spheres (random sequential
-    addition) in the damaging matrix; uniaxial tension under mixed control."""
-    n = (N, N, N)
+    addition) in the damaging matrix; uniaxial tension under mixed control.
+    ``grid`` = (N1, N2, N3) replaces the N^3 cube (profiling shapes)."""
+    n = tuple(grid) if grid is not None else (N, N, N)
     if count is None:
         count = sphere_count_for_fraction(n, radius, vf)
     cen = rsa_sphere_centres(n, radius, count, seed)
     ph = voxelize_spheres(n, cen, radius)
     ctrl, tgt = uniaxial_path(n_incr, dE)
-    return RVEConfig("3d_spheres_%d" % N, n, (float(N),) * 3, ph, phase_params(),
+    name = "3d_spheres_%d" % N if grid is None else "3d_spheres_%dx%dx%d" % n
+    return RVEConfig(name, n, tuple(float(x) for x in n), ph, phase_params(),
                      _ell_table(ell_vox), ctrl, tgt, precision,
                      dict(radius=radius, count=count, seed=seed,
                           vf_voxel=float(ph.mean()), sha256=phase_sha256(ph)))
