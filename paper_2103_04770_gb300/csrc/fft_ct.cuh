@@ -16,7 +16,15 @@ template <int REM> struct PickRadix {
   static constexpr int v = (REM % 8 == 0) ? 8 : (REM % 4 == 0) ? 4 : (REM % 2 == 0) ? 2 : (REM % 5 == 0) ? 5 : 3;
 };
 
-template <typename R, int N, int NL, int ES, int LS, int SIGN, bool JFAST, int TWMUL, int Ns, int RAD>
+// shared-memory index with one padding entry every 2^PADSH entries (PADSH =
+// 0: none); breaks the power-of-two strides of the Stockham writes
+template <int PADSH>
+__device__ __forceinline__ int cpad(int i) {
+  return PADSH ? i + (i >> PADSH) : i;
+}
+
+template <typename R, int N, int NL, int ES, int LS, int SIGN, bool JFAST, int TWMUL, int Ns, int RAD,
+          int PADSH = 0>
 __device__ __forceinline__ void ct_stage(C2<R>* buf, const C2<R>* tw) {
   constexpr int NR = N / RAD;
   constexpr int NBF = NL * NR;
@@ -30,9 +38,8 @@ __device__ __forceinline__ void ct_stage(C2<R>* buf, const C2<R>* tw) {
       int line, j;
       if (JFAST) { line = b / NR; j = b - line * NR; }
       else { j = b / NL; line = b - j * NL; }
-      const C2<R>* base = buf + line * LS;
 #pragma unroll
-      for (int r = 0; r < RAD; r++) v[i][r] = base[(j + r * NR) * ES];
+      for (int r = 0; r < RAD; r++) v[i][r] = buf[cpad<PADSH>(line * LS + (j + r * NR) * ES)];
     }
   }
   __syncthreads();
@@ -53,30 +60,29 @@ __device__ __forceinline__ void ct_stage(C2<R>* buf, const C2<R>* tw) {
         }
       }
       Dft<R, RAD, SIGN>::run(v[i]);
-      C2<R>* base = buf + line * LS;
       const int o0 = (j / Ns) * Ns * RAD + k;
 #pragma unroll
-      for (int r = 0; r < RAD; r++) base[(o0 + r * Ns) * ES] = v[i][r];
+      for (int r = 0; r < RAD; r++) buf[cpad<PADSH>(line * LS + (o0 + r * Ns) * ES)] = v[i][r];
     }
   }
   __syncthreads();
 }
 
-template <typename R, int N, int NL, int ES, int LS, int SIGN, bool JFAST, int TWMUL, int Ns>
+template <typename R, int N, int NL, int ES, int LS, int SIGN, bool JFAST, int TWMUL, int Ns, int PADSH>
 struct CtStages {
   static __device__ __forceinline__ void run(C2<R>* buf, const C2<R>* tw) {
     if constexpr (Ns < N) {
       constexpr int RAD = PickRadix<N / Ns>::v;
-      ct_stage<R, N, NL, ES, LS, SIGN, JFAST, TWMUL, Ns, RAD>(buf, tw);
-      CtStages<R, N, NL, ES, LS, SIGN, JFAST, TWMUL, Ns * RAD>::run(buf, tw);
+      ct_stage<R, N, NL, ES, LS, SIGN, JFAST, TWMUL, Ns, RAD, PADSH>(buf, tw);
+      CtStages<R, N, NL, ES, LS, SIGN, JFAST, TWMUL, Ns * RAD, PADSH>::run(buf, tw);
     }
   }
 };
 
-// NL lines of length N: element n of line l at buf[l * LS + n * ES].
-template <typename R, int N, int NL, int ES, int LS, int SIGN, bool JFAST, int TWMUL>
+// NL lines of length N: element n of line l at buf[cpad(l * LS + n * ES)].
+template <typename R, int N, int NL, int ES, int LS, int SIGN, bool JFAST, int TWMUL, int PADSH = 0>
 __device__ __forceinline__ void fft_lines_ct(C2<R>* buf, const C2<R>* tw) {
-  CtStages<R, N, NL, ES, LS, SIGN, JFAST, TWMUL, 1>::run(buf, tw);
+  CtStages<R, N, NL, ES, LS, SIGN, JFAST, TWMUL, 1, PADSH>::run(buf, tw);
 }
 
 }  // namespace rvk

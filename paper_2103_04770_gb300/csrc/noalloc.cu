@@ -123,8 +123,13 @@ extern "C" int rve_op_apply_gamma_noalloc(int dim, const int n[3], const double 
   if ((size_t)nc * (size_t)g.sstride * sizeof(C2<double>) > kScratchBytes) return RVE_ERR_ARG;
 
   LaunchCfg lc{};
-  for (int c = 1; c <= 6; c++) lc.nrows_c[c] = std::max(1, std::min(32, (16 * kThreads) / (c * g.M)));
+  for (int c = 1; c <= 6; c++) {
+    const int e = (c * g.M <= 4 * kThreads) ? 4 : 16;
+    lc.xe_c[c] = e;
+    lc.nrows_c[c] = std::max(1, std::min(32, (e * kThreads) / (c * g.M)));
+  }
   lc.nrows_c[0] = 1;
+  lc.xe_c[0] = 16;
   int tx = 1;
   while (tx * 2 * nmax <= 4 * kThreads && tx * 2 <= 32) tx *= 2;
   lc.tx = tx;

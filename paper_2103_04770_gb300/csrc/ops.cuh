@@ -82,7 +82,47 @@ __device__ __forceinline__ void gamma_mode(int d, const R n[3], C2<R>* t) {
   }
 }
 
+// ------------------------------------------------ tile staging (cp.async)
+// Tiles of the strided passes are rows of `cols` complex entries (row n of
+// component c at src + c*cstride + n*astride) held in shared memory as
+// buf[c][n][tx].  Loads go through cp.async in 16-byte chunks (8 bytes for
+// an odd FP32 tail) so that each thread keeps many copies in flight; rows
+// start on 16-byte boundaries (padded rows, even tile starts).
+__device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sm, const void* gm) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ================================================================ x1 passes
+// Padding shift of the compile-time x1 kernels' shared buffers (one complex
+// entry per 16 in FP32, per 8 in FP64; 0 for the runtime-sized kernels).
+template <typename R, int MCT> struct XPad {
+  static constexpr int v = MCT > 0 ? (sizeof(R) == 4 ? 4 : 3) : 0;
+};
+// complex entries reserved for rows * nc lines of M points, padding included
+__host__ __device__ __forceinline__ size_t xbuf_c(int rows, int nc, int M) {
+  const size_t n = (size_t)rows * nc * M;
+  return n + (n >> 3) + 16;
+}
+// rows per CTA of the compile-time x1 kernels: the E = 4 row rule
+// min(32, 4 kThreads / (NC M)) for M = MCT
+template <int MCT, int NC> struct XRows {
+  static constexpr int v = MCT > 0 ? ((4 * kThreads) / (MCT * NC) < 32 ? (4 * kThreads) / (MCT * NC) : 32) : 0;
+};
+
+// real element ri of a padded complex buffer
+template <typename R, int PADSH>
+__device__ __forceinline__ R& rpad(R* rbuf, int ri) {
+  return rbuf[2 * cpad<PADSH>(ri >> 1) + (ri & 1)];
+}
+
 // Kernels are specialised on the component count NC (so per-voxel vectors
 // live in registers) and on E, the FFT elements staged per thread (4: one or
 // a few rows per CTA and four CTAs per SM; 16: long rows).
@@ -96,6 +136,7 @@ __global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
 k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, int nrows, PRO pro,
        const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
+  constexpr int PS = XPad<R, MCT>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
@@ -111,49 +152,32 @@ k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, 
     R val[NC];
     pro(v, val);
 #pragma unroll
-    for (int c = 0; c < NC; c++) rbuf[(r * NC + c) * g.n1 + x] = val[c];
+    for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * g.n1 + x) = val[c];
   }
   __syncthreads();
-  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, -1, true, 2>(cbuf, tws);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, -1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   const int nout = rows * NC * g.P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
     const int l = e / g.P1, k = e - l * g.P1;
     const int r = l / NC, c = l - r * NC;
-    const C2<R> zk = cbuf[l * g.M + (k == g.M ? 0 : k)];
-    const C2<R> zm = cbuf[l * g.M + (k == 0 ? 0 : g.M - k)];
+    const C2<R> zk = cbuf[cpad<PS>(l * g.M + (k == g.M ? 0 : k))];
+    const C2<R> zm = cbuf[cpad<PS>(l * g.M + (k == 0 ? 0 : g.M - k))];
     const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
     const C2<R> Ok = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
     S[c * g.sstride + (row0 + r) * g.ps + k] = Ek + cmul(tws[k], Ok);
   }
 }
 
-// Split of the half spectrum back to the half-length complex sequence.
-template <typename R>
-__device__ __forceinline__ void xinv_pre(const Geo& g, const C2<R>* __restrict__ S, long long row0,
-                                         int rows, int nc, const C2<R>* tws, C2<R>* cbuf) {
-  const int nin = rows * nc * g.M;
-  for (int e = threadIdx.x; e < nin; e += kThreads) {
-    const int l = e / g.M, k = e - l * g.M;
-    const int r = l / nc, c = l - r * nc;
-    const C2<R>* row = S + c * g.sstride + (row0 + r) * g.ps;
-    const C2<R> xk = row[k], xm = row[g.M - k];
-    const C2<R> E = mk<R>(R(0.5) * (xk.x + xm.x), R(0.5) * (xk.y - xm.y));
-    const C2<R> Dd = mk<R>(R(0.5) * (xk.x - xm.x), R(0.5) * (xk.y + xm.y));
-    const C2<R> O = cmul(Dd, conj_(tws[k]));
-    cbuf[l * g.M + k] = mk<R>(E.x - O.y, E.y + O.x);
-  }
-}
-
 // Offset of the spectrum staging area behind the x1 pass buffers.
 template <typename R>
 __host__ __device__ __forceinline__ size_t xstage_off(int n1, int rows, int nc) {
-  return (((size_t)n1 * sizeof(C2<R>) + (size_t)rows * nc * n1 * sizeof(R)) + 15) & ~(size_t)15;
+  return (((size_t)n1 * sizeof(C2<R>) + xbuf_c(rows, nc, n1 / 2) * sizeof(C2<R>)) + 15) & ~(size_t)15;
 }
 
 // Stage the spectrum rows of the CTA with cp.async (xs[c][r][ps]), then
 // split them into the half-length complex sequences (cbuf line r*NC + c).
-template <typename R, int NC>
+template <typename R, int NC, int PS>
 __device__ __forceinline__ void xinv_pre_staged(const Geo& g, const C2<R>* __restrict__ S, long long row0,
                                                 int rows, const C2<R>* tws, C2<R>* cbuf, C2<R>* xs) {
   tile_load_async(xs, S + row0 * g.ps, NC, g.sstride, rows, (long long)g.ps, g.ps, g.P1);
@@ -167,15 +191,22 @@ __device__ __forceinline__ void xinv_pre_staged(const Geo& g, const C2<R>* __res
     const C2<R> E = mk<R>(R(0.5) * (xk.x + xm.x), R(0.5) * (xk.y - xm.y));
     const C2<R> Dd = mk<R>(R(0.5) * (xk.x - xm.x), R(0.5) * (xk.y + xm.y));
     const C2<R> O = cmul(Dd, conj_(tws[k]));
-    cbuf[l * g.M + k] = mk<R>(E.x - O.y, E.y + O.x);
+    cbuf[cpad<PS>(l * g.M + k)] = mk<R>(E.x - O.y, E.y + O.x);
   }
 }
 
+// minimum resident CTAs of the x1 inverse kernels (the compile-time FP32
+// variant fits 64 registers)
+template <typename R, int E, int MCT> struct XInvMinBlocks {
+  static constexpr int v = (MCT > 0 && sizeof(R) == 4) ? 4 : XMinBlocks<R, E>::v;
+};
+
 template <typename R, int NC, int E, class EPI, int NS, int MCT = 0>
-__global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
+__global__ void __launch_bounds__(kThreads, XInvMinBlocks<R, E, MCT>::v)
 k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict__ S, int nrows, R scale,
        EPI epi, double* __restrict__ part, int pstride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
+  constexpr int PS = XPad<R, MCT>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
@@ -184,9 +215,12 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
   const long long row0 = (long long)blockIdx.x * nrows;
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
-  xinv_pre_staged<R, NC>(g, S, row0, rows, tws, cbuf, xs);
+  // rows of the epilogue's input field, fetched together with the spectrum
+  R* pre = reinterpret_cast<R*>(xs + (size_t)nrows * NC * g.ps);
+  if constexpr (EPI::kPrefetch) epi.prefetch(pre, row0, rows, g.n1);
+  xinv_pre_staged<R, NC, PS>(g, S, row0, rows, tws, cbuf, xs);
   __syncthreads();
-  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, +1, true, 2>(cbuf, tws);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, +1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   constexpr int NSA = NS > 0 ? NS : 1;
   double acc[NSA];
@@ -199,8 +233,9 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
     const long long v = (row0 + r) * g.n1 + x;
     R val[NC];
 #pragma unroll
-    for (int c = 0; c < NC; c++) val[c] = rbuf[(r * NC + c) * g.n1 + x] * scale;
-    epi(v, val, acc);
+    for (int c = 0; c < NC; c++) val[c] = rpad<R, PS>(rbuf, (r * NC + c) * g.n1 + x) * scale;
+    if constexpr (EPI::kPrefetch) epi(v, val, acc, pre + (r * NC) * g.n1 + x, g.n1);
+    else epi(v, val, acc);
   }
   if (NS > 0) block_sum_store<NSA>(acc, part, pstride);
 }
@@ -211,6 +246,7 @@ __global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
 k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, int nrows, R scale,
        const uint8_t* __restrict__ phase, const R* __restrict__ ell2, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
+  constexpr int PS = XPad<R, MCT>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
@@ -219,9 +255,9 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
   const long long row0 = (long long)blockIdx.x * nrows;
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
-  xinv_pre_staged<R, NC>(g, W, row0, rows, tws, cbuf, xs);
+  xinv_pre_staged<R, NC, PS>(g, W, row0, rows, tws, cbuf, xs);
   __syncthreads();
-  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, +1, true, 2>(cbuf, tws);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, +1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   const int nvox = rows * g.n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
@@ -229,17 +265,17 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
     const long long v = (row0 + r) * g.n1 + x;
     const R w = ell2[phase[v]] * scale;
 #pragma unroll
-    for (int c = 0; c < NC; c++) rbuf[(r * NC + c) * g.n1 + x] *= w;
+    for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * g.n1 + x) *= w;
   }
   __syncthreads();
-  if constexpr (MCT > 0) fft_lines_ct<R, MCT, NC, 1, MCT, -1, true, 2>(cbuf, tws);
+  if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, -1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   const int nout = rows * NC * g.P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
     const int l = e / g.P1, k = e - l * g.P1;
     const int r = l / NC, c = l - r * NC;
-    const C2<R> zk = cbuf[l * g.M + (k == g.M ? 0 : k)];
-    const C2<R> zm = cbuf[l * g.M + (k == 0 ? 0 : g.M - k)];
+    const C2<R> zk = cbuf[cpad<PS>(l * g.M + (k == g.M ? 0 : k))];
+    const C2<R> zm = cbuf[cpad<PS>(l * g.M + (k == 0 ? 0 : g.M - k))];
     const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
     const C2<R> Ok = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
     W[c * g.sstride + (row0 + r) * g.ps + k] = Ek + cmul(tws[k], Ok);
@@ -265,28 +301,33 @@ struct ProTangent {
   }
   __device__ __forceinline__ void operator()(long long v, R (&out)[NC]) const {
     constexpr int NN = NC == 6 ? 3 : 2;
-    R pv[NC];
+    // every load first (r, p, descriptor), then the store of the new p:
+    // the store could alias the loads, so it would otherwise serialise them
+    R pv[NC], m[NC];
+    const R c1 = desc[v], c2 = desc[V + v];
+#pragma unroll
+    for (int c = 0; c < NC; c++) m[c] = desc[(2 + c) * V + v];
     if (update) {
+      R rv[NC], po[NC];
 #pragma unroll
       for (int c = 0; c < NC; c++) {
-        const R rv = r[c * V + v];
-        pv[c] = first ? rv : rv + beta * p[c * V + v];
+        rv[c] = r[c * V + v];
+        po[c] = first ? R(0) : p[c * V + v];
+      }
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        pv[c] = first ? rv[c] : rv[c] + beta * po[c];
         p[c * V + v] = pv[c];
       }
     } else {
 #pragma unroll
       for (int c = 0; c < NC; c++) pv[c] = p[c * V + v];
     }
-    const R c1 = desc[v], c2 = desc[V + v];
-    R m[NC];
     R tr = R(0), mp = R(0);
 #pragma unroll
     for (int c = 0; c < NN; c++) tr += pv[c];
 #pragma unroll
-    for (int c = 0; c < NC; c++) {
-      m[c] = desc[(2 + c) * V + v];
-      mp += m[c] * pv[c];
-    }
+    for (int c = 0; c < NC; c++) mp += m[c] * pv[c];
     const R third = tr * R(1.0 / 3.0);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
@@ -316,22 +357,49 @@ struct ProField64 {
 };
 
 template <typename R, int NC>
-struct EpiMatvec {       // Ap = val; acc0 += p . Ap
+struct EpiMatvec {       // Ap = val; acc0 += p . Ap   (p rows prefetched)
+  static constexpr bool kPrefetch = true;
   R* Ap;
   const R* p;
   long long V;
   __device__ void begin(const KrylovCtl*) {}
-  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc) const {
+  // cp.async of the CTA's rows of p: pre[(r * NC + c) * n1 + x]
+  __device__ __forceinline__ void prefetch(R* pre, long long row0, int rows, int n1) const {
+    constexpr int PER = 16 / (int)sizeof(R);
+    const int cpr = n1 / PER;
+    const int total = rows * NC * cpr;
+    if (n1 % PER == 0) {
+      for (int e = threadIdx.x; e < total; e += kThreads) {
+        const int l = e / cpr, ch = e - l * cpr;
+        const int r = l / NC, c = l - r * NC;
+        cp_async16(pre + (size_t)l * n1 + ch * PER, p + c * V + (row0 + r) * n1 + ch * PER);
+      }
+    } else {
+      for (int e = threadIdx.x; e < rows * NC * n1; e += kThreads) {
+        const int l = e / n1, x = e - l * n1;
+        const int r = l / NC, c = l - r * NC;
+        pre[e] = p[c * V + (row0 + r) * n1 + x];
+      }
+    }
+  }
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc, const R* pv,
+                                             int n1) const {
+    // the voxel's NC products are summed in the working precision, the sum
+    // over voxels in FP64
+    R part = R(0);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       Ap[c * V + v] = val[c];
-      acc[0] += (double)p[c * V + v] * (double)val[c];
+      part += pv[c * n1] * val[c];
     }
+    acc[0] += (double)part;
   }
 };
 
 template <typename R, typename RO, int NC>
 struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
+  static constexpr bool kPrefetch = false;
+  __device__ void prefetch(R*, long long, int, int) const {}
   RO* b;
   const double* mean_sig;   // full Mandel (6)
   double mask[NC];
@@ -344,18 +412,22 @@ struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
     for (int c = 0; c < NC; c++) dc[c] = mask[c] * (mean_sig[map[c]] - sbar[c]);
   }
   __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc) const {
+    RO part = RO(0);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       const double bv = -((double)val[c] + dc[c]);
       const RO br = (RO)bv;
       b[c * V + v] = br;
-      acc[0] += (double)br * (double)br;
+      part += br * br;
     }
+    acc[0] += (double)part;
   }
 };
 
 template <typename R, int NC>
 struct EpiStore64 {
+  static constexpr bool kPrefetch = false;
+  __device__ void prefetch(R*, long long, int, int) const {}
   double* out;
   long long V;
   __device__ void begin(const KrylovCtl*) {}
@@ -370,24 +442,6 @@ struct EpiStore64 {
 template <typename R>
 __host__ __device__ __forceinline__ size_t tw_bytes(int N) {
   return ((size_t)N * sizeof(C2<R>) + 15) & ~(size_t)15;
-}
-
-// ------------------------------------------------ tile staging (cp.async)
-// Tiles of the strided passes are rows of `cols` complex entries (row n of
-// component c at src + c*cstride + n*astride) held in shared memory as
-// buf[c][n][tx].  Loads go through cp.async in 16-byte chunks (8 bytes for
-// an odd FP32 tail) so that each thread keeps many copies in flight; rows
-// start on 16-byte boundaries (padded rows, even tile starts).
-__device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gm) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* sm, const void* gm) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gm) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename R>
@@ -534,7 +588,7 @@ __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
 
 // Helmholtz: p <- M r + beta p (M = 1/(1 + <l^2>|k|^2)); W_j = k_j p; inverse
 // transform along the last axis.
-template <typename R, int D>
+template <typename R, int D, int NCT = 0, int TXC = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
          C2<R>* __restrict__ p, const C2<R>* __restrict__ r, int tx, long long astride,
@@ -575,13 +629,16 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
     for (int j = 0; j < d; j++) buf[j * tile + e] = cscale(ipp, a[j]);
   }
   __syncthreads();
-  for (int j = 0; j < d; j++) fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  for (int j = 0; j < d; j++) {
+    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, +1, false, 1>(buf + j * tile, tws);
+    else fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  }
   tile_store(buf, W + off, d, g.sstride, N, astride, tx, cols);
 }
 
 // Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
 // partial Hermitian-weighted (p, y).
-template <typename R, int D>
+template <typename R, int D, int NCT = 0, int TXC = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C2<R>* __restrict__ W,
            const C2<R>* __restrict__ p, C2<R>* __restrict__ y, int tx, long long astride,
@@ -601,7 +658,10 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
   tile_load_async(buf, W + off, d, g.sstride, N, astride, tx, cols);
   __syncthreads();
-  for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  for (int j = 0; j < d; j++) {
+    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, -1, false, 1>(buf + j * tile, tws);
+    else fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  }
   double acc[1] = {0.0};
   for (int e = threadIdx.x; e < tile; e += kThreads) {
     const int n = e / tx, col = e - n * tx;
@@ -637,15 +697,56 @@ k_cg_init(long long n, R* __restrict__ x, const R* __restrict__ r, double* __res
   block_sum_store<1>(acc, part, pstride);
 }
 
+// 16-byte vector of the working precision
+template <typename R> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using T = double2; static constexpr int n = 2; };
+
+template <typename R>
+__device__ __forceinline__ R vdot_self(const typename Vec16<R>::T& a);
+template <> __device__ __forceinline__ float vdot_self<float>(const float4& a) {
+  return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+}
+template <> __device__ __forceinline__ double vdot_self<double>(const double2& a) {
+  return a.x * a.x + a.y * a.y;
+}
+template <typename R>
+__device__ __forceinline__ void vaxpy(typename Vec16<R>::T& y, R a, const typename Vec16<R>::T& x);
+template <> __device__ __forceinline__ void vaxpy<float>(float4& y, float a, const float4& x) {
+  y.x += a * x.x; y.y += a * x.y; y.z += a * x.z; y.w += a * x.w;
+}
+template <> __device__ __forceinline__ void vaxpy<double>(double2& y, double a, const double2& x) {
+  y.x += a * x.x; y.y += a * x.y;
+}
+
+// x += alpha p, r -= alpha Ap, partial (r, r): 16-byte vectors, the vector's
+// terms summed in the working precision and accumulated in FP64
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_cg_update(long long n, R* __restrict__ x, R* __restrict__ r, const R* __restrict__ p,
             const R* __restrict__ Ap, double* __restrict__ part, int pstride,
             const KrylovCtl* __restrict__ ctl) {
   if (ctl->done) return;
+  using VT = typename Vec16<R>::T;
+  constexpr int VN = Vec16<R>::n;
   const R alpha = (R)ctl->alpha;
   double acc[1] = {0.0};
-  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+  const long long nv = n / VN;
+  VT* xv = reinterpret_cast<VT*>(x);
+  VT* rv = reinterpret_cast<VT*>(r);
+  const VT* pv = reinterpret_cast<const VT*>(p);
+  const VT* av = reinterpret_cast<const VT*>(Ap);
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < nv; i += (long long)gridDim.x * kThreads) {
+    VT xi = xv[i], ri = rv[i];
+    const VT pi = pv[i], ai = av[i];
+    vaxpy<R>(xi, alpha, pi);
+    vaxpy<R>(ri, -alpha, ai);
+    xv[i] = xi;
+    rv[i] = ri;
+    acc[0] += (double)vdot_self<R>(ri);
+  }
+  for (long long i = nv * VN + blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads) {
     x[i] += alpha * p[i];
     const R rn = r[i] - alpha * Ap[i];
     r[i] = rn;
@@ -835,19 +936,21 @@ __global__ void k_from_r(long long n, const R* __restrict__ a, double* __restric
 // ============================================================ launchers
 template <typename R>
 static size_t xsmem(const Geo& g, int nrows, int nc) {
-  return (size_t)g.n1 * sizeof(C2<R>) + (size_t)nrows * nc * g.n1 * sizeof(R);
+  return (size_t)g.n1 * sizeof(C2<R>) + xbuf_c(nrows, nc, g.M) * sizeof(C2<R>);
 }
 static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrows - 1) / nrows); }
 
 // launch an x1 kernel K<E> with E = 4 or 16 as chosen in the launch config
+// (STAGE: 0 plain, 1 staged spectrum rows, 2 staged rows plus prefetched p)
 // x1 launch: compile-time variant KCT for rows of 128 complex points (N1 =
 // 256) at one row per CTA, else KT4 / KT16 by the staged-element count
 #define XLAUNCH(KCT, KT4, KT16, NCC, STAGE, ...)                                                        \
   do {                                                                                                  \
     const int nr = lc.nrows_c[NCC];                                                                     \
     const size_t sm = STAGE ? xstage_off<R>(g.n1, nr, NCC) + (size_t)nr * NCC * g.ps * sizeof(C2<R>)   \
+                                  + (STAGE == 2 ? (size_t)nr * NCC * g.n1 * sizeof(R) : 0)              \
                             : xsmem<R>(g, nr, NCC);                                                     \
-    if (lc.xe_c[NCC] == 4 && g.M == 128 && nr == 1) {                                                   \
+    if (lc.xe_c[NCC] == 4 && g.M == 128 && nr == XRows<128, NCC>::v) {                                  \
       auto k = KCT;                                                                                     \
       set_smem(k, sm);                                                                                  \
       k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
@@ -908,7 +1011,7 @@ static void xinv_matvec_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   EpiMatvec<R, NC> epi;
   epi.Ap = Ap; epi.p = p; epi.V = g.V;
   XLAUNCH((k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1, 128>), (k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1>),
-          (k_xinv<R, NC, 16, EpiMatvec<R, NC>, 1>), NC, true,
+          (k_xinv<R, NC, 16, EpiMatvec<R, NC>, 1>), NC, 2,
           g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, ctl);
 }
 
@@ -1042,7 +1145,13 @@ void Ops<R>::helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
   const int tx = lc.tx;
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  if (g.d == 3) {
+  constexpr int TXC = Tx256<R>::v;
+  if (g.d == 3 && si.N == 256 && tx == TXC) {
+    auto k = k_expand<R, 3, 256, TXC>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
+                                  raw);
+  } else if (g.d == 3) {
     auto k = k_expand<R, 3>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
@@ -1064,7 +1173,13 @@ void Ops<R>::helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const int tx = lc.tx;
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  if (g.d == 3) {
+  constexpr int TXC = Tx256<R>::v;
+  if (g.d == 3 && si.N == 256 && tx == TXC) {
+    auto k = k_contract<R, 3, 256, TXC>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
+                                  lc.max_blocks, ctl);
+  } else if (g.d == 3) {
     auto k = k_contract<R, 3>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,

@@ -205,7 +205,9 @@ def test_matvec_and_cg(n, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n", [(32, 30), (40, 16), (16, 12, 10), (12, 15, 8), (6, 5)])
+@pytest.mark.parametrize("n", [(32, 30), (40, 16), (16, 12, 10), (12, 15, 8), (6, 5),
+                               # compile-time paths: 256-point rows and last axis
+                               (256, 24), (256, 8, 16), (16, 8, 256)])
 def test_helmholtz(n, prec):
     g = O.Grid(n)
     rng = np.random.default_rng(6)
