@@ -282,11 +282,6 @@ int xblocks(const rve* h, int nc) {
   return (int)((h->g.nlines + h->lc.nrows_c[nc] - 1) / h->lc.nrows_c[nc]);
 }
 
-int last_blocks(const rve* h) {
-  const int nt = (h->g.P1 + h->lc.tx - 1) / h->lc.tx;
-  return nt * (h->g.d == 3 ? h->g.n2 : 1);
-}
-
 template <typename R>
 struct Alg {
   using Op = Ops<R>;
@@ -461,7 +456,7 @@ struct Alg {
     LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_INIT, h->ctl, nullptr,
                rtol * rtol, maxit, stall_window()));
     const int chunk = std::max(1, h->opt.check_every);
-    const int nbl = last_blocks(h);
+    const int nbl = Op::contract_blocks(g, h->lc);
     for (;;) {
       for (int i = 0; i < chunk; i++) {
         helm_matvec(h, t, j, hp, hr, hy, h->ctl, 0);

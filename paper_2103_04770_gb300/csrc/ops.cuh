@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "fft.cuh"
+#include "fft256.cuh"
 #include "fft_ct.cuh"
 #include "ops.h"
 
@@ -444,36 +445,55 @@ __host__ __device__ __forceinline__ size_t tw_bytes(int N) {
   return ((size_t)N * sizeof(C2<R>) + 15) & ~(size_t)15;
 }
 
-template <typename R>
+// Tile of ncomp components x N points x tx columns in shared memory:
+// element (c, n, col) at (c N + n) tx + col, or with IL (components
+// interleaved) at n rs + c tx + col (rs >= ncomp tx: the stride of one
+// point's group of lines), where one batched transform of ncomp tx lines
+// covers every component.  With SW (256-point axes) global row n maps to
+// tile row swap16(n), the order of the register-pass spectrum.  Interleaved
+// tiles are walked component-fastest so that a warp's shared-memory rows are
+// adjacent.
+template <bool IL, bool SW>
+__device__ __forceinline__ int tile_off(int row, int ncomp, int N, int tx, int rs, long long cstride,
+                                        long long astride, long long& goff) {
+  int c, n;
+  if (IL) { n = row / ncomp; c = row - n * ncomp; }
+  else { c = row / N; n = row - c * N; }
+  goff = c * cstride + n * astride;
+  const int m = SW ? swap16(n) : n;
+  return IL ? m * rs + c * tx : (c * N + m) * tx;
+}
+
+template <typename R, bool IL = false, bool SW = false>
 __device__ __forceinline__ void tile_load_async(C2<R>* buf, const C2<R>* src, int ncomp, long long cstride,
-                                                int N, long long astride, int tx, int cols) {
+                                                int N, long long astride, int tx, int cols, int rs = 0) {
   constexpr int PER = 16 / (int)sizeof(C2<R>);
   const int cpr = (cols + PER - 1) / PER;
   const int total = ncomp * N * cpr;
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int row = e / cpr, ch = e - row * cpr;
-    const int c = row / N, n = row - c * N;
     const int col = ch * PER;
-    C2<R>* d = buf + (c * N + n) * tx + col;
-    const C2<R>* sp = src + c * cstride + n * astride + col;
+    long long goff;
+    C2<R>* d = buf + tile_off<IL, SW>(row, ncomp, N, tx, rs, cstride, astride, goff) + col;
+    const C2<R>* sp = src + goff + col;
     if (PER == 2 && col + 1 >= cols) cp_async8(d, sp);
     else cp_async16(d, sp);
   }
   cp_async_wait_all();
 }
 
-template <typename R>
+template <typename R, bool IL = false, bool SW = false>
 __device__ __forceinline__ void tile_store(const C2<R>* buf, C2<R>* dst, int ncomp, long long cstride, int N,
-                                           long long astride, int tx, int cols) {
+                                           long long astride, int tx, int cols, int rs = 0) {
   constexpr int PER = 16 / (int)sizeof(C2<R>);
   const int cpr = (cols + PER - 1) / PER;
   const int total = ncomp * N * cpr;
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int row = e / cpr, ch = e - row * cpr;
-    const int c = row / N, n = row - c * N;
     const int col = ch * PER;
-    const C2<R>* sp = buf + (c * N + n) * tx + col;
-    C2<R>* d = dst + c * cstride + n * astride + col;
+    long long goff;
+    const C2<R>* sp = buf + tile_off<IL, SW>(row, ncomp, N, tx, rs, cstride, astride, goff) + col;
+    C2<R>* d = dst + goff + col;
     if (PER == 2 && col + 1 >= cols) {
       d[0] = sp[0];
     } else if (PER == 2) {
@@ -496,26 +516,49 @@ static StrideInfo<R> stride_of(const Geo& g, int axis) {
   return s;
 }
 
-// NCT > 0: compile-time axis length NCT and tile width TXC.
-template <typename R, int SIGN, int NCT = 0, int TXC = 0>
+// Tile widths of the 256-point register-pass kernels (columns per CTA) for
+// NCOMP components per tile: NCOMP * TX * 16 tasks per pass, about three per
+// thread or fewer, and at most ~100 KB of shared memory.
+template <typename R, int NCOMP> struct RegTx {
+  static constexpr int v = sizeof(R) == 4 ? (NCOMP >= 6 ? 8 : 16) : (NCOMP >= 6 ? 4 : NCOMP >= 2 ? 8 : 16);
+};
+// Point stride of the interleaved tile: six-component tiles (four rows of a
+// 32-lane warp per projection step) get 32 bytes of padding per point so
+// that those rows fall on different banks.
+template <typename R, int NCOMP> struct RegRs {
+  static constexpr int v = NCOMP * RegTx<R, NCOMP>::v + (NCOMP >= 6 ? 32 / (int)sizeof(C2<R>) : 0);
+};
+
+// TXR > 0: 256-point axis through the register passes, TXR columns per CTA.
+template <typename R, int SIGN, int TXR = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
                 long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = pl.N;
+  const int N = TXR ? 256 : pl.N;
+  if (TXR) tx = TXR;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   C2<R>* base = S + blockIdx.z * g.sstride + blockIdx.y * ostride + q0;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  tile_load_async(buf, base, 1, 0, N, astride, tx, cols);
-  __syncthreads();
-  if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, SIGN, false, 1>(buf, tws);
-  else fft_lines<R, E, SIGN>(buf, pl, cols, tx, 1, false, tws, 1);
-  tile_store(buf, base, 1, 0, N, astride, tx, cols);
+  if constexpr (TXR > 0) {
+    // forward: natural rows in, spectrum stored from the swap16 order;
+    // inverse: spectrum loaded into the swap16 order, natural rows out
+    tile_load_async<R, false, (SIGN > 0)>(buf, base, 1, 0, 256, astride, TXR, cols);
+    __syncthreads();
+    if constexpr (SIGN < 0) fft256_forward<R, TXR>(buf, tws);
+    else fft256_inverse<R, TXR>(buf, tws);
+    tile_store<R, false, (SIGN < 0)>(buf, base, 1, 0, 256, astride, TXR, cols);
+  } else {
+    tile_load_async(buf, base, 1, 0, N, astride, tx, cols);
+    __syncthreads();
+    fft_lines<R, E, SIGN>(buf, pl, cols, tx, 1, false, tws, 1);
+    tile_store(buf, base, 1, 0, N, astride, tx, cols);
+  }
 }
 
 // mode indices of element (n, col) of a last-axis tile
@@ -526,7 +569,10 @@ __device__ __forceinline__ void last_modes(const Geo& g, int q0, int col, int n,
   else { m1 = n; m2 = 0; }
 }
 
-template <typename R, int NC, int NCT = 0, int TXC = 0>
+// TXR > 0: 256-point last axis through the register passes, TXR columns per
+// CTA, the NC components interleaved in the tile and transformed as one
+// batch of NC TXR lines; the projection runs on the swap16 spectrum order.
+template <typename R, int NC, int TXR = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
         long long astride, long long ostride, Mask6 mask, int dc_mode,
@@ -534,33 +580,41 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   constexpr int nc = NC;
+  constexpr bool IL = TXR > 0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = pl.N;
+  const int N = TXR ? 256 : pl.N;
+  if (TXR) tx = TXR;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   C2<R>* base = S + blockIdx.y * ostride + q0;
   const int tile = N * tx;
+  constexpr int RS = IL ? RegRs<R, NC>::v : 0;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  tile_load_async(buf, base, nc, g.sstride, N, astride, tx, cols);
+  tile_load_async<R, IL>(buf, base, nc, g.sstride, N, astride, tx, cols, RS);
   __syncthreads();
-  for (int c = 0; c < nc; c++) {
-    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, -1, false, 1>(buf + c * tile, tws);
-    else fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  if constexpr (IL) {
+    fft256_forward<R, NC * TXR, RS>(buf, tws);
+  } else {
+    for (int c = 0; c < nc; c++) fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
   }
   for (int e = threadIdx.x; e < tile; e += kThreads) {
     const int n = e / tx, col = e - n * tx;
     if (col >= cols) continue;
+    // element of component c: buf[e0 + c cst] with the tile's layout; the
+    // register passes leave frequency swap16(n) at tile row n
+    const int e0 = IL ? n * RS + col : e;
+    const int cst = IL ? tx : tile;
     int m0, m1, m2;
-    last_modes(g, q0, col, n, m0, m1, m2);
+    last_modes(g, q0, col, IL ? swap16(n) : n, m0, m1, m2);
     R a[3];
     C2<R> ph;
     symbol(g, t, m0, m1, m2, a, ph);
     const R a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
     C2<R> tv[NC];
 #pragma unroll
-    for (int c = 0; c < nc; c++) tv[c] = buf[c * tile + e];
+    for (int c = 0; c < nc; c++) tv[c] = buf[e0 + c * cst];
     if (a2 > R(0)) {
       const R inv = R(1) / sqrt(a2);
       R nv[3] = {a[0] * inv, a[1] * inv, a[2] * inv};
@@ -571,14 +625,15 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
       for (int c = 0; c < nc; c++) tv[c] = (dc && !dc_mode) ? cscale(tv[c], (R)mask.m[c]) : mk<R>(0, 0);
     }
 #pragma unroll
-    for (int c = 0; c < nc; c++) buf[c * tile + e] = tv[c];
+    for (int c = 0; c < nc; c++) buf[e0 + c * cst] = tv[c];
   }
   __syncthreads();
-  for (int c = 0; c < nc; c++) {
-    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, +1, false, 1>(buf + c * tile, tws);
-    else fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
+  if constexpr (IL) {
+    fft256_inverse<R, NC * TXR, RS>(buf, tws);
+  } else {
+    for (int c = 0; c < nc; c++) fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
   }
-  tile_store(buf, base, nc, g.sstride, N, astride, tx, cols);
+  tile_store<R, IL>(buf, base, nc, g.sstride, N, astride, tx, cols, RS);
 }
 
 template <typename R>
@@ -588,7 +643,7 @@ __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
 
 // Helmholtz: p <- M r + beta p (M = 1/(1 + <l^2>|k|^2)); W_j = k_j p; inverse
 // transform along the last axis.
-template <typename R, int D, int NCT = 0, int TXC = 0>
+template <typename R, int D, int TXR = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
          C2<R>* __restrict__ p, const C2<R>* __restrict__ r, int tx, long long astride,
@@ -596,8 +651,10 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = pl.N;
+  const int N = TXR ? 256 : pl.N;
+  if (TXR) tx = TXR;
   constexpr int d = D;
+  constexpr bool IL = TXR > 0;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
@@ -626,19 +683,23 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
       p[idx] = pn;
     }
     const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
-    for (int j = 0; j < d; j++) buf[j * tile + e] = cscale(ipp, a[j]);
+    // the register passes take frequency n at tile row swap16(n)
+    const int e0 = IL ? swap16(n) * d * tx + col : e;
+    const int cst = IL ? tx : tile;
+    for (int j = 0; j < d; j++) buf[e0 + j * cst] = cscale(ipp, a[j]);
   }
   __syncthreads();
-  for (int j = 0; j < d; j++) {
-    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, +1, false, 1>(buf + j * tile, tws);
-    else fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  if constexpr (IL) {
+    fft256_inverse<R, D * TXR>(buf, tws);
+  } else {
+    for (int j = 0; j < d; j++) fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
-  tile_store(buf, W + off, d, g.sstride, N, astride, tx, cols);
+  tile_store<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, cols, d * tx);
 }
 
 // Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
 // partial Hermitian-weighted (p, y).
-template <typename R, int D, int NCT = 0, int TXC = 0>
+template <typename R, int D, int TXR = 0>
 __global__ void __launch_bounds__(kThreads, 2)
 k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C2<R>* __restrict__ W,
            const C2<R>* __restrict__ p, C2<R>* __restrict__ y, int tx, long long astride,
@@ -647,8 +708,10 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = pl.N;
+  const int N = TXR ? 256 : pl.N;
+  if (TXR) tx = TXR;
   constexpr int d = D;
+  constexpr bool IL = TXR > 0;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
   const int q0 = blockIdx.x * tx;
@@ -656,11 +719,12 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   const long long off = blockIdx.y * ostride + q0;
   const int tile = N * tx;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  tile_load_async(buf, W + off, d, g.sstride, N, astride, tx, cols);
+  tile_load_async<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, cols, d * tx);
   __syncthreads();
-  for (int j = 0; j < d; j++) {
-    if constexpr (NCT > 0) fft_lines_ct<R, NCT, TXC, TXC, 1, -1, false, 1>(buf + j * tile, tws);
-    else fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
+  if constexpr (IL) {
+    fft256_forward<R, D * TXR>(buf, tws);
+  } else {
+    for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
   double acc[1] = {0.0};
   for (int e = threadIdx.x; e < tile; e += kThreads) {
@@ -671,8 +735,10 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
     R a[3];
     C2<R> ph;
     symbol(g, t, m0, m1, m2, a, ph);
+    const int e0 = IL ? swap16(n) * d * tx + col : e;
+    const int cst = IL ? tx : tile;
     C2<R> s = mk<R>(0, 0);
-    for (int j = 0; j < d; j++) s = s + cscale(buf[j * tile + e], a[j]);
+    for (int j = 0; j < d; j++) s = s + cscale(buf[e0 + j * cst], a[j]);
     // conj(k_j) = -i e^{-i phi} a_j
     const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
     const long long idx = off + n * astride + col;
@@ -965,8 +1031,18 @@ static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrow
     }                                                                                                   \
   } while (0)
 
-// tile width of the compile-time strided passes on a 256-point axis
-template <typename R> struct Tx256 { static constexpr int v = StridedE<R>::E * kThreads / 256; };
+// tile width of the strided / last-axis kernels with ncomp components per
+// tile: the register-pass width on a 256-point axis, else the runtime width
+template <typename R>
+static int axis_tx(const LaunchCfg& lc, int N, int ncomp) {
+  if (N != 256) return lc.tx;
+  switch (ncomp) {
+    case 1: return RegTx<R, 1>::v;
+    case 2: return RegTx<R, 2>::v;
+    case 3: return RegTx<R, 3>::v;
+    default: return RegTx<R, 6>::v;
+  }
+}
 
 template <typename R, int NC>
 static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
@@ -1081,31 +1157,19 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
                            C2<R>* S, int ncomp, int axis, int sign, const KrylovCtl* ctl) {
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
-  const int tx = lc.tx;
+  const int tx = axis_tx<R>(lc, si.N, 1);
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? g.n3 : g.n2, ncomp);
-  constexpr int TXC = Tx256<R>::v;
-  const bool ct = si.N == 256 && tx == TXC;
+  constexpr int TXR = RegTx<R, 1>::v;
+  const bool reg = si.N == 256;
   if (sign < 0) {
-    if (ct) {
-      auto k = k_strided_plain<R, -1, 256, TXC>;
-      set_smem(k, sm);
-      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
-    } else {
-      auto k = k_strided_plain<R, -1>;
-      set_smem(k, sm);
-      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
-    }
+    auto k = reg ? k_strided_plain<R, -1, TXR> : k_strided_plain<R, -1>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
   } else {
-    if (ct) {
-      auto k = k_strided_plain<R, 1, 256, TXC>;
-      set_smem(k, sm);
-      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
-    } else {
-      auto k = k_strided_plain<R, 1>;
-      set_smem(k, sm);
-      k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
-    }
+    auto k = reg ? k_strided_plain<R, 1, TXR> : k_strided_plain<R, 1>;
+    set_smem(k, sm);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
   }
 }
 
@@ -1115,22 +1179,19 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
   const int axis = g.d - 1;
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
-  const int tx = lc.tx;
-  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.nc * tx;
+  const int tx = axis_tx<R>(lc, si.N, g.nc);
+  const bool reg = si.N == 256;
+  const int rs = !reg ? g.nc * tx : g.nc == 6 ? RegRs<R, 6>::v : RegRs<R, 3>::v;
+  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * rs;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   Mask6 m;
   for (int c = 0; c < 6; c++) m.m[c] = c < g.nc ? stress_mask[c] : 0.f;
-  constexpr int TXC = Tx256<R>::v;
-  if (g.nc == 6 && si.N == 256 && tx == TXC) {
-    auto k = k_gamma<R, 6, 256, TXC>;
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
-  } else if (g.nc == 6) {
-    auto k = k_gamma<R, 6>;
+  if (g.nc == 6) {
+    auto k = reg ? k_gamma<R, 6, RegTx<R, 6>::v> : k_gamma<R, 6>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
   } else {
-    auto k = k_gamma<R, 3>;
+    auto k = reg ? k_gamma<R, 3, RegTx<R, 3>::v> : k_gamma<R, 3>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
   }
@@ -1142,26 +1203,27 @@ void Ops<R>::helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
   const int axis = g.d - 1;
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
-  const int tx = lc.tx;
+  const int tx = axis_tx<R>(lc, si.N, g.d);
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  constexpr int TXC = Tx256<R>::v;
-  if (g.d == 3 && si.N == 256 && tx == TXC) {
-    auto k = k_expand<R, 3, 256, TXC>;
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
-                                  raw);
-  } else if (g.d == 3) {
-    auto k = k_expand<R, 3>;
+  const bool reg = si.N == 256;
+  if (g.d == 3) {
+    auto k = reg ? k_expand<R, 3, RegTx<R, 3>::v> : k_expand<R, 3>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
                                   raw);
   } else {
-    auto k = k_expand<R, 2>;
+    auto k = reg ? k_expand<R, 2, RegTx<R, 2>::v> : k_expand<R, 2>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
                                   raw);
   }
+}
+
+template <typename R>
+int Ops<R>::contract_blocks(const Geo& g, const LaunchCfg& lc) {
+  const int tx = axis_tx<R>(lc, g.d == 3 ? g.n3 : g.n2, g.d);
+  return ((g.P1 + tx - 1) / tx) * (g.d == 3 ? g.n2 : 1);
 }
 
 template <typename R>
@@ -1170,22 +1232,17 @@ void Ops<R>::helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const int axis = g.d - 1;
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
-  const int tx = lc.tx;
+  const int tx = axis_tx<R>(lc, si.N, g.d);
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  constexpr int TXC = Tx256<R>::v;
-  if (g.d == 3 && si.N == 256 && tx == TXC) {
-    auto k = k_contract<R, 3, 256, TXC>;
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
-                                  lc.max_blocks, ctl);
-  } else if (g.d == 3) {
-    auto k = k_contract<R, 3>;
+  const bool reg = si.N == 256;
+  if (g.d == 3) {
+    auto k = reg ? k_contract<R, 3, RegTx<R, 3>::v> : k_contract<R, 3>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
                                   lc.max_blocks, ctl);
   } else {
-    auto k = k_contract<R, 2>;
+    auto k = reg ? k_contract<R, 2, RegTx<R, 2>::v> : k_contract<R, 2>;
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
                                   lc.max_blocks, ctl);

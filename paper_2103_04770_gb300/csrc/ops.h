@@ -86,6 +86,8 @@ struct Ops {
                           C2<R>* W, C2<R>* p, const C2<R>* r, double ell2_mean, const KrylovCtl* ctl,
                           int raw = 0);
   // last axis forward; y = p + sum_j conj(k_j) W_j; partial (p, y)
+  // CTAs of helm_contract (rows of partial sums it writes)
+  static int contract_blocks(const Geo& g, const LaunchCfg& lc);
   static void helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                             const C2<R>* W, const C2<R>* p, C2<R>* y, double* part,
                             const KrylovCtl* ctl);

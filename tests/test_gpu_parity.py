@@ -129,7 +129,7 @@ GAMMA_GRIDS = [(32, 30), (40, 16), (2, 2), (6, 5), (16, 12, 10), (12, 15, 8), (8
                # several q1 tiles per line and two-stage radix-8 axes
                (96, 20), (128, 64), (80, 12, 10), (64, 64, 16), (64, 24, 64),
                # compile-time FFT paths: N1 = 256 rows, 256-point y and last axes
-               (256, 256), (256, 8, 8), (16, 256, 8), (16, 8, 256)]
+               (256, 256), (256, 8, 8), (16, 256, 8), (16, 8, 256), (40, 6, 256)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -207,7 +207,7 @@ def test_matvec_and_cg(n, prec):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [(32, 30), (40, 16), (16, 12, 10), (12, 15, 8), (6, 5),
                                # compile-time paths: 256-point rows and last axis
-                               (256, 24), (256, 8, 16), (16, 8, 256)])
+                               (256, 24), (24, 256), (256, 8, 16), (16, 8, 256)])
 def test_helmholtz(n, prec):
     g = O.Grid(n)
     rng = np.random.default_rng(6)
