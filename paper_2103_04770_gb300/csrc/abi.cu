@@ -54,12 +54,14 @@ enum {
   KC_PCG_UPDATE,
   KC_FINALIZE,
   KC_MISC,
+  KC_RES_Y_PASS,
+  KC_RES_GAMMA,
   KC_COUNT
 };
 const char* const kClassNames[KC_COUNT] = {
     "return_map", "x1_fwd_tangent", "x1_fwd_field", "y_pass", "gamma_last_axis", "x1_inv_matvec",
     "x1_inv_residual", "x1_inv_store", "helmholtz_expand", "helmholtz_x1_mid", "helmholtz_contract",
-    "cg_update", "pcg_update", "finalize", "misc"};
+    "cg_update", "pcg_update", "finalize", "misc", "residual_y_pass", "residual_gamma"};
 
 struct PendingEv {
   int cls;
@@ -318,12 +320,12 @@ struct Alg {
             Ops<double>::xfwd_field64(g, t64, h->lc64, h->st, h->sigma, g.nc, g.cmap, h->dscal + OFF_SIGMEAN,
                                       S64));
     if (g.d == 3)
-      LAUNCHB(h, KC_Y_PASS, 2.0 * nc * VS(h) * cs64,
+      LAUNCHB(h, KC_RES_Y_PASS, 2.0 * nc * VS(h) * cs64,
               Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, -1, nullptr));
-    LAUNCHB(h, KC_GAMMA, 2.0 * nc * VS(h) * cs64,
+    LAUNCHB(h, KC_RES_GAMMA, 2.0 * nc * VS(h) * cs64,
             Ops<double>::gamma(g, t64, h->lc64, h->st, S64, h->smask_f, 1, nullptr));
     if (g.d == 3)
-      LAUNCHB(h, KC_Y_PASS, 2.0 * nc * VS(h) * cs64,
+      LAUNCHB(h, KC_RES_Y_PASS, 2.0 * nc * VS(h) * cs64,
               Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, +1, nullptr));
     LAUNCHB(h, KC_X_INV_RESIDUAL, nc * (VS(h) * cs64 + VV(h) * RS),
             Ops<double>::template xinv_residual<R>(g, t64, h->lc64, h->st, S64, (R*)h->r,

@@ -520,7 +520,7 @@ static StrideInfo<R> stride_of(const Geo& g, int axis) {
 // NCOMP components per tile: NCOMP * TX * 16 tasks per pass, about three per
 // thread or fewer, and at most ~100 KB of shared memory.
 template <typename R, int NCOMP> struct RegTx {
-  static constexpr int v = sizeof(R) == 4 ? (NCOMP >= 6 ? 8 : 16) : (NCOMP >= 6 ? 4 : NCOMP >= 2 ? 8 : 16);
+  static constexpr int v = sizeof(R) == 4 ? (NCOMP >= 3 ? 8 : 16) : (NCOMP >= 6 ? 4 : NCOMP >= 2 ? 8 : 16);
 };
 // Point stride of the interleaved tile: six-component tiles (four rows of a
 // 32-lane warp per projection step) get 32 bytes of padding per point so
@@ -569,6 +569,64 @@ __device__ __forceinline__ void last_modes(const Geo& g, int q0, int col, int n,
   else { m1 = n; m2 = 0; }
 }
 
+// Symbol factors of the last-axis kernels with the register passes: a
+// thread keeps one column (axis-0 mode m0) and, in 3D, the CTA's y-plane
+// (axis-1 mode m1) for all its points, so only the last-axis factors are
+// looked up per point.  Same products, in the same order, as symbol().
+template <typename R>
+struct LastSym {
+  R s0, c0, s1, c1;
+  int m0, m1;
+  __device__ __forceinline__ void init(const Geo& g, const Tables<R>& t, int m0_) {
+    m0 = m0_;
+    s0 = t.s[0][m0];
+    c0 = t.c[0][m0];
+    m1 = g.d == 3 ? (int)blockIdx.y : 0;
+    s1 = t.s[1][m1];
+    c1 = t.c[1][m1];
+  }
+  // modes (m0, m1, f) in 3D, (m0, f) in 2D
+  __device__ __forceinline__ void at(const Geo& g, const Tables<R>& t, int f, R a[3], C2<R>& ph,
+                                     bool& dc) const {
+    if (g.d == 3) {
+      const R s2 = t.s[2][f], c2 = t.c[2][f];
+      a[0] = t.two_over_h[0] * s0 * c1 * c2;
+      a[1] = t.two_over_h[1] * s1 * c0 * c2;
+      a[2] = t.two_over_h[2] * s2 * c0 * c1;
+      ph = cmul(cmul(mk<R>(c0, s0), mk<R>(c1, s1)), mk<R>(c2, s2));
+      dc = m0 == 0 && m1 == 0 && f == 0;
+    } else {
+      const R sf = t.s[1][f], cf = t.c[1][f];
+      a[0] = t.two_over_h[0] * s0 * cf;
+      a[1] = t.two_over_h[1] * sf * c0;
+      a[2] = R(0);
+      ph = cmul(mk<R>(c0, s0), mk<R>(cf, sf));
+      dc = m0 == 0 && f == 0;
+    }
+  }
+};
+
+template <typename R> __device__ __forceinline__ R inv_sqrt(R x);
+template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return 1.0 / sqrt(x); }
+
+// Gamma* at one mode of symbol a: the projection for k != 0, the
+// stress-control mask at the zero frequency (dc_mode 0), zero at the hidden
+// zeros of the symbol
+template <typename R, int NC>
+__device__ __forceinline__ void gamma_apply(const R a[3], bool dc, const Mask6& mask, int dc_mode,
+                                            C2<R> (&tv)[NC]) {
+  const R a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+  if (a2 > R(0)) {
+    const R inv = inv_sqrt<R>(a2);
+    R nv[3] = {a[0] * inv, a[1] * inv, a[2] * inv};
+    gamma_mode<R>(NC == 6 ? 3 : 2, nv, tv);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; c++) tv[c] = (dc && !dc_mode) ? cscale(tv[c], (R)mask.m[c]) : mk<R>(0, 0);
+  }
+}
+
 // TXR > 0: 256-point last axis through the register passes, TXR columns per
 // CTA, the NC components interleaved in the tile and transformed as one
 // batch of NC TXR lines; the projection runs on the swap16 spectrum order.
@@ -599,33 +657,43 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   } else {
     for (int c = 0; c < nc; c++) fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
   }
-  for (int e = threadIdx.x; e < tile; e += kThreads) {
-    const int n = e / tx, col = e - n * tx;
-    if (col >= cols) continue;
-    // element of component c: buf[e0 + c cst] with the tile's layout; the
-    // register passes leave frequency swap16(n) at tile row n
-    const int e0 = IL ? n * RS + col : e;
-    const int cst = IL ? tx : tile;
-    int m0, m1, m2;
-    last_modes(g, q0, col, IL ? swap16(n) : n, m0, m1, m2);
-    R a[3];
-    C2<R> ph;
-    symbol(g, t, m0, m1, m2, a, ph);
-    const R a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
-    C2<R> tv[NC];
+  if constexpr (IL) {
+    // the register passes leave frequency swap16(n) at tile row n
+    constexpr int RPT = kThreads / TXR;
+    const int col = threadIdx.x % TXR;
+    if (col < cols) {
+      LastSym<R> sy;
+      sy.init(g, t, q0 + col);
+#pragma unroll 2
+      for (int n = threadIdx.x / TXR; n < 256; n += RPT) {
+        R a[3];
+        C2<R> ph;
+        bool dc;
+        sy.at(g, t, swap16(n), a, ph, dc);
+        C2<R> tv[NC];
 #pragma unroll
-    for (int c = 0; c < nc; c++) tv[c] = buf[e0 + c * cst];
-    if (a2 > R(0)) {
-      const R inv = R(1) / sqrt(a2);
-      R nv[3] = {a[0] * inv, a[1] * inv, a[2] * inv};
-      gamma_mode<R>(NC == 6 ? 3 : 2, nv, tv);
-    } else {
-      const bool dc = (m0 == 0) && (m1 == 0) && (m2 == 0);
+        for (int c = 0; c < nc; c++) tv[c] = buf[n * RS + c * TXR + col];
+        gamma_apply<R, NC>(a, dc, mask, dc_mode, tv);
 #pragma unroll
-      for (int c = 0; c < nc; c++) tv[c] = (dc && !dc_mode) ? cscale(tv[c], (R)mask.m[c]) : mk<R>(0, 0);
+        for (int c = 0; c < nc; c++) buf[n * RS + c * TXR + col] = tv[c];
+      }
     }
+  } else {
+    for (int e = threadIdx.x; e < tile; e += kThreads) {
+      const int n = e / tx, col = e - n * tx;
+      if (col >= cols) continue;
+      int m0, m1, m2;
+      last_modes(g, q0, col, n, m0, m1, m2);
+      R a[3];
+      C2<R> ph;
+      symbol(g, t, m0, m1, m2, a, ph);
+      C2<R> tv[NC];
 #pragma unroll
-    for (int c = 0; c < nc; c++) buf[e0 + c * cst] = tv[c];
+      for (int c = 0; c < nc; c++) tv[c] = buf[e + c * tile];
+      gamma_apply<R, NC>(a, m0 == 0 && m1 == 0 && m2 == 0, mask, dc_mode, tv);
+#pragma unroll
+      for (int c = 0; c < nc; c++) buf[e + c * tile] = tv[c];
+    }
   }
   __syncthreads();
   if constexpr (IL) {
@@ -664,29 +732,57 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   const bool first = ctl ? ctl->iter == 0 : true;
   const R beta = ctl ? (R)ctl->beta : R(0);
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  for (int e = threadIdx.x; e < tile; e += kThreads) {
-    const int n = e / tx, col = e - n * tx;
-    if (col >= cols) continue;
-    int m0, m1, m2;
-    last_modes(g, q0, col, n, m0, m1, m2);
-    R a[3];
-    C2<R> ph;
-    symbol(g, t, m0, m1, m2, a, ph);
-    const R Mk = R(1) / (R(1) + ell2m * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
-    const long long idx = off + n * astride + col;
-    C2<R> pn;
-    if (raw) {
-      pn = r[idx];
-    } else {
-      pn = cscale(r[idx], Mk);
-      if (!first) pn = pn + cscale(p[idx], beta);
-      p[idx] = pn;
+  if constexpr (IL) {
+    // one column per thread; frequency n goes to tile row swap16(n)
+    constexpr int RPT = kThreads / TXR;
+    const int col = threadIdx.x % TXR;
+    if (col < cols) {
+      LastSym<R> sy;
+      sy.init(g, t, q0 + col);
+#pragma unroll 4
+      for (int n = threadIdx.x / TXR; n < 256; n += RPT) {
+        R a[3];
+        C2<R> ph;
+        bool dc;
+        sy.at(g, t, n, a, ph, dc);
+        const R Mk = R(1) / (R(1) + ell2m * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+        const long long idx = off + n * astride + col;
+        C2<R> pn;
+        if (raw) {
+          pn = r[idx];
+        } else {
+          pn = cscale(r[idx], Mk);
+          if (!first) pn = pn + cscale(p[idx], beta);
+          p[idx] = pn;
+        }
+        const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
+        const int e0 = swap16(n) * (d * TXR) + col;
+#pragma unroll
+        for (int j = 0; j < d; j++) buf[e0 + j * TXR] = cscale(ipp, a[j]);
+      }
     }
-    const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
-    // the register passes take frequency n at tile row swap16(n)
-    const int e0 = IL ? swap16(n) * d * tx + col : e;
-    const int cst = IL ? tx : tile;
-    for (int j = 0; j < d; j++) buf[e0 + j * cst] = cscale(ipp, a[j]);
+  } else {
+    for (int e = threadIdx.x; e < tile; e += kThreads) {
+      const int n = e / tx, col = e - n * tx;
+      if (col >= cols) continue;
+      int m0, m1, m2;
+      last_modes(g, q0, col, n, m0, m1, m2);
+      R a[3];
+      C2<R> ph;
+      symbol(g, t, m0, m1, m2, a, ph);
+      const R Mk = R(1) / (R(1) + ell2m * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+      const long long idx = off + n * astride + col;
+      C2<R> pn;
+      if (raw) {
+        pn = r[idx];
+      } else {
+        pn = cscale(r[idx], Mk);
+        if (!first) pn = pn + cscale(p[idx], beta);
+        p[idx] = pn;
+      }
+      const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
+      for (int j = 0; j < d; j++) buf[e + j * tile] = cscale(ipp, a[j]);
+    }
   }
   __syncthreads();
   if constexpr (IL) {
@@ -719,6 +815,18 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   const long long off = blockIdx.y * ostride + q0;
   const int tile = N * tx;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
+  // register path: this thread's entries of p, fetched while the tile is
+  // transformed
+  constexpr int RPT = TXR ? kThreads / TXR : 1;
+  constexpr int PER = TXR ? 256 / RPT : 1;
+  C2<R> pv[PER];
+  if constexpr (IL) {
+    const int col = threadIdx.x % TXR;
+    if (col < cols) {
+#pragma unroll
+      for (int k = 0; k < PER; k++) pv[k] = p[off + (threadIdx.x / TXR + k * RPT) * astride + col];
+    }
+  }
   tile_load_async<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, cols, d * tx);
   __syncthreads();
   if constexpr (IL) {
@@ -727,25 +835,49 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
     for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
   double acc[1] = {0.0};
-  for (int e = threadIdx.x; e < tile; e += kThreads) {
-    const int n = e / tx, col = e - n * tx;
-    if (col >= cols) continue;
-    int m0, m1, m2;
-    last_modes(g, q0, col, n, m0, m1, m2);
-    R a[3];
-    C2<R> ph;
-    symbol(g, t, m0, m1, m2, a, ph);
-    const int e0 = IL ? swap16(n) * d * tx + col : e;
-    const int cst = IL ? tx : tile;
-    C2<R> s = mk<R>(0, 0);
-    for (int j = 0; j < d; j++) s = s + cscale(buf[e0 + j * cst], a[j]);
-    // conj(k_j) = -i e^{-i phi} a_j
-    const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
-    const long long idx = off + n * astride + col;
-    const C2<R> pv = p[idx];
-    const C2<R> yv = pv + ks;
-    y[idx] = yv;
-    acc[0] += (double)q1_weight<R>(g, m0) * ((double)pv.x * (double)yv.x + (double)pv.y * (double)yv.y);
+  if constexpr (IL) {
+    const int col = threadIdx.x % TXR;
+    if (col < cols) {
+      LastSym<R> sy;
+      sy.init(g, t, q0 + col);
+      const R w1 = q1_weight<R>(g, q0 + col);
+#pragma unroll
+      for (int k = 0; k < PER; k++) {
+        const int n = threadIdx.x / TXR + k * RPT;
+        R a[3];
+        C2<R> ph;
+        bool dc;
+        sy.at(g, t, n, a, ph, dc);
+        const int e0 = swap16(n) * (d * TXR) + col;
+        C2<R> s = mk<R>(0, 0);
+#pragma unroll
+        for (int j = 0; j < d; j++) s = s + cscale(buf[e0 + j * TXR], a[j]);
+        // conj(k_j) = -i e^{-i phi} a_j
+        const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
+        const C2<R> yv = pv[k] + ks;
+        y[off + n * astride + col] = yv;
+        acc[0] += (double)w1 * ((double)pv[k].x * (double)yv.x + (double)pv[k].y * (double)yv.y);
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < tile; e += kThreads) {
+      const int n = e / tx, col = e - n * tx;
+      if (col >= cols) continue;
+      int m0, m1, m2;
+      last_modes(g, q0, col, n, m0, m1, m2);
+      R a[3];
+      C2<R> ph;
+      symbol(g, t, m0, m1, m2, a, ph);
+      C2<R> s = mk<R>(0, 0);
+      for (int j = 0; j < d; j++) s = s + cscale(buf[e + j * tile], a[j]);
+      // conj(k_j) = -i e^{-i phi} a_j
+      const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
+      const long long idx = off + n * astride + col;
+      const C2<R> pn = p[idx];
+      const C2<R> yv = pn + ks;
+      y[idx] = yv;
+      acc[0] += (double)q1_weight<R>(g, m0) * ((double)pn.x * (double)yv.x + (double)pn.y * (double)yv.y);
+    }
   }
   block_sum_store<1>(acc, part, pstride);
 }
