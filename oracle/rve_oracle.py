@@ -45,6 +45,13 @@ R1..R26 of the design notes):
       0.01 TOL_N sqrt(V) ||<sigma>||: the linear solve is not pushed below the
       accuracy the Newton test (R4) can use, where the right-hand side is
       dominated by the round-off of -G*(sigma - Sigma_bar).
+  R20 Particle cracking (law 2; not in the paper, an extension of Section
+      3.1's multi-variable framework): the local variable is the history
+      kappa = max(kappa_n, ||<eps>_+||), the Euclidean norm of the positive
+      principal strains; it feeds its own non-local variable, and
+      D = clamp((kappa_bar - kappa_C)/(kappa_R - kappa_C), 0, D_max) scales an
+      elastic stress, sigma = (1 - D) C : eps, with tangent (1 - D) C (R11).
+      kappa_C, kappa_R reuse the eps_C, eps_R slots of the phase.
 
 Parity: every function below is pinned by the CPU tests (closed forms,
 invariants, dense brute-force solves built from real-space stencils, finite
@@ -250,7 +257,7 @@ class Phase:
     nu: float
     sigma_y: float = 0.0
     H: float = 0.0
-    law: int = 0            # 0 linear elastic, 1 J2 + Lemaitre damage
+    law: int = 0            # 0 linear elastic, 1 J2 + Lemaitre damage, 2 particle cracking (R20)
     eps_C: float = 0.0
     eps_R: float = 1.0
     D_max: float = 0.0
@@ -272,11 +279,19 @@ def phases_from_dicts(ds):
 
 def damage_of(abar, ph):
     """Linear damage law driven by the non-local equivalent plastic strain
-    (Eq. non-local_damage_lemaitre), capped at D_max (Section 4.1, R10)."""
-    if ph.law != 1:
+    (Eq. non-local_damage_lemaitre), capped at D_max (Section 4.1, R10); the
+    same ramp on the non-local kappa for particle cracking (R20)."""
+    if ph.law not in (1, 2):
         return np.zeros_like(abar)
     D = (abar - ph.eps_C) / (ph.eps_R - ph.eps_C)
     return np.clip(D, 0.0, ph.D_max)
+
+
+def positive_principal_norm(e):
+    """||<eps>_+|| for Mandel strains e (n, 6): the Euclidean norm of the
+    positive parts of the eigenvalues of the strain tensor (R20)."""
+    lam = np.linalg.eigvalsh(mandel_to_tensor(e))
+    return np.sqrt(np.sum(np.maximum(lam, 0.0) ** 2, axis=-1))
 
 
 def return_map(eps, epsp_n, ep_n, abar, phase, phases):
@@ -297,6 +312,8 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
       C = (1 - D) [K I(x)I + 2 mu theta P_dev - 2 mu thetabar nhat(x)nhat]
           theta = 1 - 2 mu dlambda / q, thetabar = 1/(1 + H/(3 mu)) - (1 - theta)
     (the consistent tangent of radial return with linear isotropic hardening).
+    Particle cracking (law 2, R20): kappa = max(kappa_n, ||<e>_+||) is kept
+    in the ep slot, D from abar of the phase's variable, sigma = (1 - D) C e.
     """
     Vn = eps.shape[0]
     J = abar.shape[0]
@@ -337,6 +354,12 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
             D[sel] = Dq
             if ph.var >= 0:
                 alpha[ph.var, sel] = ep[sel]
+        elif ph.law == 2:
+            kap = np.maximum(ep_n[sel], positive_principal_norm(e))
+            ep[sel] = kap
+            if ph.var >= 0:
+                D[sel] = damage_of(abar[ph.var][sel], ph)
+                alpha[ph.var, sel] = kap
         Dq = D[sel]
         sigma[sel] = (1.0 - Dq)[:, None] * sig_eff
         Cq = (K * np.outer(IVEC, IVEC)[None] + 2.0 * mu * theta[:, None, None] * Pdev[None]

@@ -36,6 +36,12 @@ MATRIX = dict(E=70000.0, nu=0.33, sigma_y=100.0, H=500.0, law=1,
 PARTICLE = dict(E=400000.0, nu=0.2, sigma_y=0.0, H=0.0, law=0,
                 eps_C=0.0, eps_R=1.0, D_max=0.0, var=-1)
 
+# Cracking particle (builder extension of Section 3.1's multi-variable
+# framework, not in the paper): elastic, damaged by its own non-local
+# positive-principal-strain history with thresholds kappa_C = 0.005,
+# kappa_R = 0.02 (stored in the eps_C / eps_R slots) and the same cap.
+PARTICLE_CRACKING = dict(PARTICLE, law=2, eps_C=0.005, eps_R=0.02, D_max=0.99, var=1)
+
 # ratio between the own-phase and other-phase characteristic length
 # (Section 4.1: l_M / l_I = 50)
 ELL_CONTRAST = 50.0

@@ -245,3 +245,57 @@ def test_newton_step_matches_dense_galerkin(n):
     y = np.linalg.lstsq(K, rhs, rcond=1e-12)[0]
     ref = (B @ y).reshape(x.shape)
     np.testing.assert_allclose(x, ref, atol=1e-10 * np.abs(ref).max())
+
+
+# ------------------------------------------------- particle cracking (R20)
+def _rotation(seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+    return q * np.sign(np.diag(r))
+
+
+def test_positive_principal_norm_closed_forms():
+    """||<eps>_+|| for diagonal tensors, their rotations and pure shear."""
+    diag = np.array([[3e-3, -1e-3, 2e-3], [-2e-3, -1e-3, -5e-4], [1e-3, 1e-3, 1e-3],
+                     [4e-3, -4e-3, 0.0]])
+    want = np.sqrt(np.sum(np.maximum(diag, 0.0) ** 2, axis=1))
+    for k, dg in enumerate(diag):
+        Q = _rotation(k)
+        T = Q @ np.diag(dg) @ Q.T
+        e = O.tensor_to_mandel(T[None])[0]
+        assert O.positive_principal_norm(e[None])[0] == pytest.approx(want[k], rel=1e-12, abs=1e-18)
+    g = 2.5e-3                               # eps12 = g: eigenvalues g, -g, 0
+    e = np.array([[0, 0, 0, 0, 0, math.sqrt(2.0) * g]])
+    assert O.positive_principal_norm(e)[0] == pytest.approx(g, rel=1e-13)
+
+
+def test_particle_cracking_history_is_kept():
+    """kappa = max(kappa_n, ||<eps>_+||): a smaller current strain keeps the
+    stored history, a larger one replaces it; alpha carries kappa."""
+    ph = O.phases_from_dicts([dict(I.PARTICLE_CRACKING, var=0)])
+    eps = np.array([[4e-3, -8e-4, -8e-4, 0, 0, 0], [2e-2, -4e-3, -4e-3, 0, 0, 0]])
+    ep_n = np.array([1e-2, 1e-2])
+    out = O.return_map(eps, np.zeros((2, 6)), ep_n, np.zeros((1, 2)), np.zeros(2, dtype=int), ph)
+    np.testing.assert_allclose(out["ep"], [1e-2, 2e-2], rtol=1e-14)
+    np.testing.assert_allclose(out["alpha"][0], [1e-2, 2e-2], rtol=1e-14)
+    P = ph[0]
+    C = _iso_C(P.E, P.nu)
+    np.testing.assert_allclose(out["sigma"][0], C @ eps[0], rtol=1e-13, atol=1e-15 * P.E)   # D = 0
+
+
+def test_particle_cracking_uniaxial_through_staggered_loop():
+    """Homogeneous cracking-particle RVE under uniaxial stress: kappa = E11
+    (the lateral principal strains are -nu E11 < 0), abar = kappa for a
+    uniform field, so Sigma11 = (1 - D(E11)) E E11 in closed form."""
+    g = O.Grid((4, 4, 4))
+    phm = np.zeros(g.shape, dtype=np.uint8)
+    ctrl, tgt = I.uniaxial_path(6, 2.5e-3)
+    mat = dict(I.PARTICLE_CRACKING, var=0)
+    st = O.run_load_path(g, phm, [mat, I.MATRIX], np.array([[3.0, 0.06]]), ctrl, tgt,
+                         O.PARITY_OPTIONS)
+    P = O.phases_from_dicts([mat])[0]
+    for rec, t in zip(st.curve, tgt):
+        D = min(max((t[0] - P.eps_C) / (P.eps_R - P.eps_C), 0.0), P.D_max)
+        assert rec["S"][0] == pytest.approx((1.0 - D) * P.E * t[0], rel=1e-10)
+        assert rec["D_max"] == pytest.approx(D, abs=1e-10)
+        assert rec["E"][1] == pytest.approx(-P.nu * t[0], rel=1e-9)
+    assert st.curve[-1]["D_max"] > 0.5
