@@ -62,8 +62,13 @@ typedef enum {
  * cap).  damage_law: 0 = linear elastic (E, nu only); 1 = J2 plasticity with
  * linear hardening sigma_0 = sigma_y + H eps_p on the effective stress and
  * Lemaitre damage D = clamp((abar - eps_C)/(eps_R - eps_C), 0, D_max)
- * (Eq. non-local_damage_lemaitre).  nonlocal_var: index j of the non-local
- * variable this phase feeds with alpha_j = eps_p and reads abar_j from, or -1
+ * (Eq. non-local_damage_lemaitre); 2 = cracking elastic particle, an
+ * extension of the multi-variable framework of Section 3.1 that the paper
+ * does not print: local variable kappa = max(kappa_n, ||<eps>_+||) (norm of
+ * the positive principal strains), D = clamp((abar - eps_C)/(eps_R - eps_C),
+ * 0, D_max) with eps_C, eps_R read as kappa_C, kappa_R, sigma = (1 - D) C eps.
+ * nonlocal_var: index j of the non-local variable this phase feeds with
+ * alpha_j = eps_p (law 1) or kappa (law 2) and reads abar_j from, or -1
  * (Section 3.1: alpha_j = 0 outside the damaging phase). */
 typedef struct {
   double E, nu, sigma_y, H;
@@ -228,6 +233,59 @@ int rve_op_helmholtz_apply(rve_t* h, int j, const double* a, double* out);
  * alpha, abar: [V]. */
 int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, double rtol,
                            int maxit, int* iters);
+
+/* ------------------------------------------------ graphs, autotuning, batches
+ * The paper solves one RVE at a time; these calls serve many RVEs of
+ * different grids advanced together on one GPU. */
+
+/* Replay each Krylov chunk (check_every CG or PCG iterations, Algorithms 1
+ * and 2) from a CUDA graph captured on its first use instead of launching
+ * its kernels one by one.  Results are identical.  Captured chunks are
+ * dropped by rve_set_options, rve_set_phases, rve_set_load_path and
+ * rve_autotune; profiling (rve_profile) launches directly.  A capture the
+ * runtime refuses falls back to direct launches.  Off by default.
+ * Errors: RVE_ERR_ARG, RVE_ERR_CUDA. */
+int rve_set_graphs(rve_t* h, int enable);
+
+/* Pick the FFT schedule of the handle's mechanical matvec by timing:
+ * for every axis transformed by the runtime mixed-radix code, each radix
+ * order with the fewest stages; then the column-tile width of the strided
+ * passes.  Each candidate is timed over `reps` matvecs G*(C_T : p) that
+ * overwrite only the Krylov scratch vectors (CUDA events on the handle's
+ * stream); a candidate replaces
+ * the current choice when it is at least 2 % faster.  Axes with compile-time
+ * schedules (256-point y / last axes, N1 = 256 rows) are left alone.  Allowed
+ * after rve_set_phases and before the first rve_step_increment (else
+ * RVE_ERR_STATE); the state is not changed.  best_ms (nullable): time of
+ * one matvec with the chosen schedule; tx (nullable): chosen tile width;
+ * radix (nullable): radices per axis, 0-terminated.
+ * Errors: RVE_ERR_ARG, RVE_ERR_STATE, RVE_ERR_CUDA. */
+int rve_autotune(rve_t* h, int reps, double* best_ms, int* tx, int radix[3][8]);
+
+/* A batch of independent handles advanced together: each member gets its
+ * own non-blocking stream (its previous stream is restored by
+ * rve_batch_free) and CUDA-graph replay of its Krylov chunks, and each
+ * rve_batch_step runs one increment of every member, one host worker thread
+ * per member, so the members' kernels overlap on the GPU.  members: handles
+ * with phases and load path set, distinct, owned by the caller, which must
+ * not use them directly while the batch exists.  autotune_reps > 0 runs
+ * rve_autotune(member, autotune_reps) on members that have not stepped yet.
+ * Errors: RVE_ERR_ARG, RVE_ERR_STATE, RVE_ERR_CUDA, RVE_ERR_OOM. */
+typedef struct rve_batch rve_batch_t;
+int rve_batch_create(rve_batch_t** out, int count, rve_t* const* members, int autotune_reps);
+
+/* One increment of every member (members whose load path is finished report
+ * RVE_ERR_LOAD_PATH_END in their info and are skipped).  infos: [count],
+ * filled per member as by rve_step_increment.  Returns RVE_OK when every
+ * member returned RVE_OK (or had finished), else the first member's error. */
+int rve_batch_step(rve_batch_t* b, rve_step_info* infos);
+
+/* Number of members (0 for NULL). */
+int rve_batch_size(const rve_batch_t* b);
+
+/* Synchronise and release the batch; the members keep their state and get
+ * their original streams back. */
+void rve_batch_free(rve_batch_t* b);
 
 /* ------------------------------------------------ allocation-free variant
  * The paper has no counterpart to this entry point; it exists for callers

@@ -90,6 +90,12 @@ _SIGNATURES = {
     "rve_op_helmholtz_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(_I)]),
     "rve_op_apply_gamma_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D),
                                         ctypes.POINTER(ctypes.c_uint8), _P, _P, _P]),
+    "rve_set_graphs": (_I, [_P, _I]),
+    "rve_autotune": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rve_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _I]),
+    "rve_batch_step": (_I, [_P, ctypes.POINTER(StepInfo)]),
+    "rve_batch_size": (_I, [_P]),
+    "rve_batch_free": (None, [_P]),
     "rve_profile": (_I, [_P, _I]),
     "rve_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                               ctypes.POINTER(_D)]),
@@ -287,6 +293,46 @@ def rve_op_apply_gamma_noalloc(dim, n, L, strain_ctrl, tau, out, stream=None):
                                             _stream_handle(stream)), "rve_op_apply_gamma_noalloc")
 
 
+# ------------------------------------------- graphs, autotuning, batches
+def rve_set_graphs(h, enable=True):
+    _check(lib().rve_set_graphs(h, 1 if enable else 0), "rve_set_graphs")
+
+
+def rve_autotune(h, reps=3):
+    """Time candidate FFT schedules of the mechanical matvec and keep the
+    fastest; returns (ms per matvec, tile width, radices per axis)."""
+    ms = ctypes.c_double()
+    tx = ctypes.c_int()
+    rad = (ctypes.c_int * 24)()
+    _check(lib().rve_autotune(h, int(reps), ctypes.byref(ms), ctypes.byref(tx), rad), "rve_autotune")
+    radices = [[v for v in rad[8 * j:8 * j + 8] if v] for j in range(3)]
+    return ms.value, tx.value, radices
+
+
+def rve_batch_create(handles, autotune_reps=3):
+    arr = (_P * len(handles))(*handles)
+    b = _P()
+    _check(lib().rve_batch_create(ctypes.byref(b), len(handles), arr, int(autotune_reps)),
+           "rve_batch_create")
+    return b.value
+
+
+def rve_batch_step(b, count, raise_on_error=True):
+    infos = (StepInfo * count)()
+    s = lib().rve_batch_step(b, infos)
+    if raise_on_error:
+        _check(s, "rve_batch_step")
+    return s, [i.as_dict() for i in infos]
+
+
+def rve_batch_size(b):
+    return lib().rve_batch_size(b)
+
+
+def rve_batch_free(b):
+    lib().rve_batch_free(b)
+
+
 # -------------------------------------------------------------- profiling
 def rve_profile(h, enable=True):
     _check(lib().rve_profile(h, 1 if enable else 0), "rve_profile")
@@ -347,6 +393,49 @@ class RVE:
         if self.h:
             rve_free(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RVEBatch:
+    """Owning wrapper of a batch of RVE configs advanced together (one
+    stream, graph-replayed Krylov chunks and one host worker per member)."""
+
+    def __init__(self, cfgs, precision=None, options=None, autotune_reps=3):
+        self.members = []
+        self.b = None
+        try:
+            for c in cfgs:
+                self.members.append(RVE(c, precision=precision, options=options))
+            self.b = rve_batch_create([m.h for m in self.members], autotune_reps)
+        except Exception:
+            self.close()
+            raise
+
+    def step(self, raise_on_error=True):
+        s, infos = rve_batch_step(self.b, len(self.members), raise_on_error)
+        return infos
+
+    def stresses(self):
+        return np.array([m.stress() for m in self.members])
+
+    def close(self):
+        if self.b:
+            rve_batch_free(self.b)
+            self.b = None
+        for m in self.members:
+            m.close()
+        self.members = []
 
     def __enter__(self):
         return self

@@ -8,11 +8,14 @@
 // iterations, and decides convergence.
 #include <cuda_runtime.h>
 
+#include <thread>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -135,6 +138,15 @@ struct rve {
   cudaEvent_t ev_cur_a = nullptr;
   int fail_stage = 0;
   int verbose = 0;      // RVE_VERBOSE=1: trace solver progress on stderr
+  // CUDA graphs of the Krylov chunks (captured at first use, replayed after)
+  bool graphs = false;
+  cudaGraphExec_t g_cg = nullptr;
+  cudaGraphExec_t g_pcg[kMaxVars] = {};
+  long long g_cg_n[KC_COUNT] = {};
+  double g_cg_b[KC_COUNT] = {};
+  long long g_pcg_n[kMaxVars][KC_COUNT] = {};
+  double g_pcg_b[kMaxVars][KC_COUNT] = {};
+  bool stepped = false;  // an increment has been attempted (autotuning closed)
 };
 
 namespace {
@@ -280,6 +292,66 @@ int sync_read(rve* h) {
   return RVE_OK;
 }
 
+// drop the captured Krylov chunks (their launches bake in the load path's
+// stress mask, the characteristic lengths, the chunk length and the launch
+// shapes)
+void graphs_reset(rve* h) {
+  if (h->g_cg) cudaGraphExecDestroy(h->g_cg);
+  h->g_cg = nullptr;
+  for (int j = 0; j < kMaxVars; j++) {
+    if (h->g_pcg[j]) cudaGraphExecDestroy(h->g_pcg[j]);
+    h->g_pcg[j] = nullptr;
+  }
+}
+
+// Launch one Krylov chunk: directly, or (graphs on, profiling off) from a
+// graph captured the first time.  The launch tallies of the capture are
+// replayed with the graph.  A capture the runtime refuses falls back to
+// direct launches for the rest of the handle's life.
+template <class F>
+int run_chunk(rve* h, cudaGraphExec_t* ex, long long* tn, double* tb, F&& chunk) {
+  if (!h->graphs || h->prof) {
+    chunk();
+    return RVE_OK;
+  }
+  if (!*ex) {
+    long long n0[KC_COUNT];
+    double b0[KC_COUNT];
+    std::memcpy(n0, h->launches, sizeof(n0));
+    std::memcpy(b0, h->prof_bytes, sizeof(b0));
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs = false;
+      chunk();
+      return RVE_OK;
+    }
+    chunk();
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->st, &gr);
+    for (int k = 0; k < KC_COUNT; k++) {
+      tn[k] = h->launches[k] - n0[k];
+      tb[k] = h->prof_bytes[k] - b0[k];
+      h->launches[k] = n0[k];
+      h->prof_bytes[k] = b0[k];
+    }
+    if (e == cudaSuccess && gr) e = cudaGraphInstantiate(ex, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *ex = nullptr;
+      h->graphs = false;
+      chunk();
+      return RVE_OK;
+    }
+  }
+  CK(cudaGraphLaunch(*ex, h->st));
+  for (int k = 0; k < KC_COUNT; k++) {
+    h->launches[k] += tn[k];
+    h->prof_bytes[k] += tb[k];
+  }
+  return RVE_OK;
+}
+
 int xblocks(const rve* h, int nc) {
   return (int)((h->g.nlines + h->lc.nrows_c[nc] - 1) / h->lc.nrows_c[nc]);
 }
@@ -344,16 +416,19 @@ struct Alg {
     const int chunk = std::max(1, h->opt.check_every);
     const int nbx = xblocks(h, g.nc);
     for (;;) {
-      for (int i = 0; i < chunk; i++) {
-        LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S,
-                         h->ctl));
-        gamma_sweep(h, t, 0, h->ctl);
-        LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 2.0 * VV(h) * RS), Op::xinv_matvec(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, h->ctl));
-        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
-        LAUNCHB(h, KC_CG_UPDATE, 6.0 * g.nc * VV(h) * RS, Op::cg_update(g, h->lc, h->st, (R*)h->x, (R*)h->r, (const R*)h->p, (const R*)h->Ap, h->part, h->ctl));
-        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
-      }
-      int s = sync_read(h);
+      int s = run_chunk(h, &h->g_cg, h->g_cg_n, h->g_cg_b, [&]() {
+        for (int i = 0; i < chunk; i++) {
+          LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S,
+                           h->ctl));
+          gamma_sweep(h, t, 0, h->ctl);
+          LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 2.0 * VV(h) * RS), Op::xinv_matvec(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, h->ctl));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_CG_UPDATE, 6.0 * g.nc * VV(h) * RS, Op::cg_update(g, h->lc, h->st, (R*)h->x, (R*)h->r, (const R*)h->p, (const R*)h->Ap, h->part, h->ctl));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
+        }
+      });
+      if (s) return s;
+      s = sync_read(h);
       if (s) return s;
       if (h->hctl->done) break;
     }
@@ -460,13 +535,16 @@ struct Alg {
     const int chunk = std::max(1, h->opt.check_every);
     const int nbl = Op::contract_blocks(g, h->lc);
     for (;;) {
-      for (int i = 0; i < chunk; i++) {
-        helm_matvec(h, t, j, hp, hr, hy, h->ctl, 0);
-        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbl, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
-        LAUNCHB(h, KC_PCG_UPDATE, 6.0 * VS(h) * CS, Op::pcg_update(g, t, h->lc, h->st, hx, hr, hp, hy, h->ell2_mean[j], h->part, h->ctl));
-        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_BETA, h->ctl, nullptr, 1.0));
-      }
-      int s = sync_read(h);
+      int s = run_chunk(h, &h->g_pcg[j], h->g_pcg_n[j], h->g_pcg_b[j], [&]() {
+        for (int i = 0; i < chunk; i++) {
+          helm_matvec(h, t, j, hp, hr, hy, h->ctl, 0);
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbl, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_PCG_UPDATE, 6.0 * VS(h) * CS, Op::pcg_update(g, t, h->lc, h->st, hx, hr, hp, hy, h->ell2_mean[j], h->part, h->ctl));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_BETA, h->ctl, nullptr, 1.0));
+        }
+      });
+      if (s) return s;
+      s = sync_read(h);
       if (s) return s;
       if (h->hctl->done) break;
     }
@@ -975,6 +1053,7 @@ int rve_create(rve_t** out, int dim, const int n[3], const double L[3], int prec
 void rve_free(rve_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  graphs_reset(h);
   prof_resolve(h);
   for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
   h->ev_free.clear();
@@ -989,6 +1068,7 @@ int rve_set_options(rve_t* h, const rve_solver_options* o) {
       o->check_every < 1)
     return RVE_ERR_ARG;
   h->opt = *o;
+  graphs_reset(h);
   return RVE_OK;
 }
 
@@ -1019,13 +1099,12 @@ int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase
   for (int q = 0; q < n_phases; q++) {
     const rve_phase_params& P = params[q];
     if (!(P.E > 0.0) || !(P.nu > -1.0 && P.nu < 0.5)) return RVE_ERR_ARG;
-    if (P.damage_law != 0 && P.damage_law != 1) return RVE_ERR_ARG;
+    if (P.damage_law < 0 || P.damage_law > 2) return RVE_ERR_ARG;
     if (P.nonlocal_var < -1 || P.nonlocal_var >= h->J) return RVE_ERR_ARG;
-    if (P.damage_law == 1) {
-      if (!(P.sigma_y > 0.0) || !(P.H >= 0.0)) return RVE_ERR_ARG;
-      if (P.nonlocal_var >= 0 && (!(P.eps_R > P.eps_C) || !(P.D_max >= 0.0 && P.D_max < 1.0)))
-        return RVE_ERR_ARG;
-    }
+    if (P.damage_law == 1 && (!(P.sigma_y > 0.0) || !(P.H >= 0.0))) return RVE_ERR_ARG;
+    if (P.damage_law != 0 && P.nonlocal_var >= 0 &&
+        (!(P.eps_R > P.eps_C) || !(P.D_max >= 0.0 && P.D_max < 1.0)))
+      return RVE_ERR_ARG;
     PhaseDev& d = pt.p[q];
     d.K = P.E / (3.0 * (1.0 - 2.0 * P.nu));
     d.mu = P.E / (2.0 * (1.0 + P.nu));
@@ -1035,7 +1114,7 @@ int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase
     d.eps_R = P.eps_R;
     d.D_max = P.D_max;
     d.law = P.damage_law;
-    d.var = P.damage_law == 1 ? P.nonlocal_var : -1;
+    d.var = P.damage_law != 0 ? P.nonlocal_var : -1;
   }
   for (int j = 0; j < h->J; j++) {
     double m = 0.0;
@@ -1057,6 +1136,8 @@ int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase
   s = reset_state(h);
   if (s) return s;
   h->phases_set = true;
+  h->stepped = false;
+  graphs_reset(h);
   return RVE_OK;
 }
 
@@ -1083,6 +1164,7 @@ int rve_set_load_path(rve_t* h, int n_incr, const uint8_t strain_ctrl[6], const 
     h->smask_f[c] = (float)m;
   }
   h->path_set = true;
+  graphs_reset(h);
   return RVE_OK;
 }
 
@@ -1091,6 +1173,7 @@ int rve_step_increment(rve_t* h, rve_step_info* info) {
   if (info) std::memset(info, 0, sizeof(*info));
   if (!h->phases_set || !h->path_set) return RVE_ERR_STATE;
   if (h->n_done >= h->n_incr) return RVE_ERR_LOAD_PATH_END;
+  h->stepped = true;
   try {
     return h->prec == RVE_MIXED ? Alg<float>::step(h, info) : Alg<double>::step(h, info);
   } catch (...) {
@@ -1200,3 +1283,234 @@ int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, d
 }
 
 }  // extern "C"
+
+// ============================================================ graphs, autotuning, batches
+int rve_set_graphs(rve_t* h, int enable) {
+  if (!h) return RVE_ERR_ARG;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return RVE_ERR_CUDA;
+  graphs_reset(h);
+  h->graphs = enable != 0;
+  return RVE_OK;
+}
+
+namespace {
+
+// ordered factorisations of N into the radices of the runtime FFT with the
+// fewest stages (at most 12)
+void radix_orders(int N, std::vector<FftPlan>& out) {
+  const int rad[5] = {8, 5, 4, 3, 2};
+  std::vector<std::vector<int>> found;
+  std::vector<int> cur;
+  size_t best = 100;
+  std::function<void(int)> rec = [&](int m) {
+    if (cur.size() > best || found.size() >= 64) return;
+    if (m == 1) {
+      if (cur.size() < best) { best = cur.size(); found.clear(); }
+      found.push_back(cur);
+      return;
+    }
+    if ((int)cur.size() >= kMaxRadixStages) return;
+    for (int r : rad)
+      if (m % r == 0) {
+        cur.push_back(r);
+        rec(m / r);
+        cur.pop_back();
+      }
+  };
+  rec(N);
+  for (const auto& f : found) {
+    if (f.size() != best) continue;
+    FftPlan pl{};
+    pl.N = N;
+    pl.nst = (int)f.size();
+    for (size_t i = 0; i < f.size(); i++) pl.radix[i] = f[i];
+    out.push_back(pl);
+    if (out.size() >= 12) break;
+  }
+}
+
+// mean time of `reps` mechanical matvecs G*(C_T : p) with the handle's
+// current launch shape and plans (Krylov scratch only; state untouched)
+template <typename R>
+double time_matvec(rve* h, int reps) {
+  const Geo& g = h->g;
+  const Tables<R> t = tables<R>(h);
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return 1e30;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 1e30; }
+  auto once = [&]() {
+    Ops<R>::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S, nullptr);
+    Alg<R>::gamma_sweep(h, t, 0, nullptr);
+    Ops<R>::xinv_matvec(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, nullptr);
+  };
+  once();
+  cudaEventRecord(a, h->st);
+  for (int i = 0; i < reps; i++) once();
+  cudaEventRecord(b, h->st);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = 1e30f;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaGetLastError();
+  return ms / reps;
+}
+
+template <typename R>
+int autotune_impl(rve* h, int reps, double* best_ms) {
+  const Geo& g = h->g;
+  const bool prof = h->prof;
+  h->prof = false;
+  long long n0[KC_COUNT];
+  double b0[KC_COUNT];
+  std::memcpy(n0, h->launches, sizeof(n0));
+  std::memcpy(b0, h->prof_bytes, sizeof(b0));
+  // the timed matvecs read r and the tangent descriptor as they are and
+  // overwrite only the Krylov scratch (p, spectrum, Ap, partial sums)
+  int s = RVE_OK;
+  double best = time_matvec<R>(h, reps);
+  // plan of each axis whose transforms run on the runtime mixed-radix path
+  for (int ax = 0; ax < g.d && !s; ax++) {
+    const int N = h->plan[ax].N;
+    if (N <= 1 || (ax == 0 && N == 128) || (ax > 0 && N == 256)) continue;
+    std::vector<FftPlan> cands;
+    radix_orders(N, cands);
+    FftPlan keep = h->plan[ax];
+    for (const FftPlan& pl : cands) {
+      h->plan[ax] = pl;
+      const double ms = time_matvec<R>(h, reps);
+      if (ms < best * 0.98) { best = ms; keep = pl; }
+    }
+    h->plan[ax] = keep;
+  }
+  // tile width of the runtime strided passes (its partial-sum rows must fit)
+  if (!s) {
+    const int nmax = std::max(g.n2, g.n3);
+    const int ET = (int)(sizeof(R) == 4 ? 8 : 4) * kThreads;
+    const int keep0 = h->lc.tx;
+    int keep = keep0;
+    for (int tx = 1; tx <= 32; tx *= 2) {
+      if (tx == keep0 || tx * nmax > ET) continue;
+      const size_t smem = (size_t)nmax * sizeof(C2<R>) * (g.nc * tx + 1) + 16;
+      if (smem > 200 * 1024) continue;
+      const long long rows = (long long)((g.P1 + tx - 1) / tx) * (g.d == 3 ? g.n2 : 1);
+      if (rows > h->lc.max_blocks) continue;
+      h->lc.tx = tx;
+      const double ms = time_matvec<R>(h, reps);
+      if (ms < best * 0.98) { best = ms; keep = tx; }
+    }
+    h->lc.tx = keep;
+  }
+  std::memcpy(h->launches, n0, sizeof(n0));
+  std::memcpy(h->prof_bytes, b0, sizeof(b0));
+  h->prof = prof;
+  graphs_reset(h);
+  if (best_ms) *best_ms = best;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return RVE_ERR_CUDA;
+  return s;
+}
+
+}  // namespace
+
+int rve_autotune(rve_t* h, int reps, double* best_ms, int* tx, int radix[3][8]) {
+  if (!h || reps < 1) return RVE_ERR_ARG;
+  if (!h->phases_set || h->stepped) return RVE_ERR_STATE;
+  int s;
+  try {
+    s = h->prec == RVE_MIXED ? autotune_impl<float>(h, reps, best_ms) : autotune_impl<double>(h, reps, best_ms);
+  } catch (...) {
+    return RVE_ERR_OOM;
+  }
+  if (s) return s;
+  if (tx) *tx = h->lc.tx;
+  if (radix)
+    for (int j = 0; j < 3; j++)
+      for (int i = 0; i < 8; i++) radix[j][i] = i < h->plan[j].nst ? h->plan[j].radix[i] : 0;
+  return RVE_OK;
+}
+
+struct rve_batch {
+  std::vector<rve*> m;
+  std::vector<cudaStream_t> own, old;
+};
+
+int rve_batch_create(rve_batch_t** out, int count, rve_t* const* members, int autotune_reps) {
+  if (!out || count < 1 || !members || autotune_reps < 0) return RVE_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; i++) {
+    if (!members[i]) return RVE_ERR_ARG;
+    if (!members[i]->phases_set || !members[i]->path_set) return RVE_ERR_STATE;
+    for (int k = 0; k < i; k++)
+      if (members[k] == members[i]) return RVE_ERR_ARG;
+  }
+  rve_batch* b = new (std::nothrow) rve_batch();
+  if (!b) return RVE_ERR_OOM;
+  b->m.assign(members, members + count);
+  for (int i = 0; i < count; i++) {
+    rve* h = b->m[i];
+    cudaStream_t st = nullptr;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      rve_batch_free(b);
+      return RVE_ERR_CUDA;
+    }
+    b->own.push_back(st);
+    b->old.push_back(h->st);
+    h->st = st;
+    graphs_reset(h);
+    h->graphs = true;
+  }
+  if (autotune_reps > 0) {
+    for (rve* h : b->m) {
+      if (h->stepped) continue;
+      const int s = rve_autotune(h, autotune_reps, nullptr, nullptr, nullptr);
+      if (s) {
+        rve_batch_free(b);
+        return s;
+      }
+    }
+  }
+  *out = b;
+  return RVE_OK;
+}
+
+int rve_batch_step(rve_batch_t* b, rve_step_info* infos) {
+  if (!b || !infos) return RVE_ERR_ARG;
+  const size_t n = b->m.size();
+  std::vector<int> st(n, RVE_OK);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (size_t i = 0; i < n; i++) {
+    rve* h = b->m[i];
+    rve_step_info* inf = infos + i;
+    int* out = &st[i];
+    th.emplace_back([h, inf, out]() {
+      if (h->n_done >= h->n_incr) {
+        std::memset(inf, 0, sizeof(*inf));
+        inf->status = RVE_ERR_LOAD_PATH_END;
+        inf->increment = h->n_done;
+        *out = RVE_OK;
+        return;
+      }
+      *out = rve_step_increment(h, inf);
+    });
+  }
+  for (auto& t : th) t.join();
+  for (size_t i = 0; i < n; i++)
+    if (st[i] != RVE_OK) return st[i];
+  return RVE_OK;
+}
+
+int rve_batch_size(const rve_batch_t* b) { return b ? (int)b->m.size() : 0; }
+
+void rve_batch_free(rve_batch_t* b) {
+  if (!b) return;
+  for (size_t i = 0; i < b->own.size(); i++) {
+    rve* h = b->m[i];
+    cudaStreamSynchronize(b->own[i]);
+    graphs_reset(h);
+    h->graphs = false;
+    h->st = b->old[i];
+    cudaStreamDestroy(b->own[i]);
+  }
+  delete b;
+}

@@ -1013,6 +1013,48 @@ k_pcg_update(Geo g, Tables<R> t, C2<R>* __restrict__ x, C2<R>* __restrict__ r,
 // Backward-Euler Lemaitre update (Appendix A.2; readings R8-R11) at every
 // voxel: radial return on the effective stress, D from the frozen non-local
 // variable, sigma = (1 - D) sigma_eff, consistent tangent descriptor.
+// One Jacobi rotation of a symmetric 3x3 matrix zeroing entry (P, Q)
+// (Golub & Van Loan, Sec. 8.5: t = tan of the rotation angle, the smaller
+// root of t^2 + 2 theta t - 1 = 0 with theta = (a_QQ - a_PP) / (2 a_PQ)).
+template <int P, int Q>
+__device__ __forceinline__ void jacobi_rot3(double (&A)[3][3]) {
+  const double apq = A[P][Q];
+  if (apq == 0.0) return;
+  constexpr int Rr = 3 - P - Q;
+  const double th = (A[Q][Q] - A[P][P]) / (2.0 * apq);
+  const double at = fabs(th);
+  const double t = (at > 1e150 ? 0.5 / at : 1.0 / (at + sqrt(th * th + 1.0))) * (th >= 0.0 ? 1.0 : -1.0);
+  const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+  A[P][P] -= t * apq;
+  A[Q][Q] += t * apq;
+  A[P][Q] = A[Q][P] = 0.0;
+  const double arp = A[Rr][P], arq = A[Rr][Q];
+  A[Rr][P] = A[P][Rr] = c * arp - s * arq;
+  A[Rr][Q] = A[Q][Rr] = s * arp + c * arq;
+}
+
+// ||<eps>_+||: Euclidean norm of the positive eigenvalues of the symmetric
+// strain tensor given in Mandel components (cyclic Jacobi sweeps until the
+// off-diagonal part is below 1e-32 of the squared norm, at most 12 sweeps).
+__device__ __forceinline__ double positive_principal_norm(const double (&e)[6]) {
+  const double r2 = 0.70710678118654752440;
+  double A[3][3] = {{e[0], e[5] * r2, e[4] * r2}, {e[5] * r2, e[1], e[3] * r2}, {e[4] * r2, e[3] * r2, e[2]}};
+  const double n2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + e[3] * e[3] + e[4] * e[4] + e[5] * e[5];
+  for (int sweep = 0; sweep < 12; sweep++) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    if (!(off > 1e-32 * n2)) break;
+    jacobi_rot3<0, 1>(A);
+    jacobi_rot3<0, 2>(A);
+    jacobi_rot3<1, 2>(A);
+  }
+  double k = 0.0;
+  for (int i = 0; i < 3; i++) {
+    const double l = A[i][i] > 0.0 ? A[i][i] : 0.0;
+    k += l * l;
+  }
+  return sqrt(k);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __restrict__ phase,
@@ -1056,6 +1098,17 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
         D = D < 0.0 ? 0.0 : (D > P.D_max ? P.D_max : D);
       }
     }
+    // particle cracking: history kappa = max(kappa_n, ||<eps>_+||) in the ep
+    // slot, damage from the non-local kappa on an elastic stress
+    double kap = 0.0;
+    if (P.law == 2) {
+      kap = fmax(epn, positive_principal_norm(e));
+      if (P.var >= 0) {
+        const double ab = abar[P.var * V + v];
+        D = (ab - P.eps_C) / (P.eps_R - P.eps_C);
+        D = D < 0.0 ? 0.0 : (D > P.D_max ? P.D_max : D);
+      }
+    }
     const double om = 1.0 - D;
     double sg[6];
     for (int c = 0; c < 6; c++) {
@@ -1065,7 +1118,7 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
       epsp[c * V + v] = pn[c] + dl * nh[c];
       acc[c] += sg[c];
     }
-    const double epv = epn + s23 * dl;
+    const double epv = P.law == 2 ? kap : epn + s23 * dl;
     ep[v] = epv;
     Dout[v] = D;
     for (int j = 0; j < J; j++) alpha[j * V + v] = (P.var == j) ? epv : 0.0;

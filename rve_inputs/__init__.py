@@ -257,3 +257,57 @@ def config_3d_spheres(N=256, radius=10.0, vf=0.25, seed=0, ell_vox=4.0,
                      _ell_table(ell_vox), ctrl, tgt, precision,
                      dict(radius=radius, count=count, seed=seed,
                           vf_voxel=float(ph.mean()), sha256=phase_sha256(ph)))
+
+
+# ------------------------------------------------- two-variable 3D sphere RVEs
+def _ell_table_two(ell_matrix, ell_particle):
+    """Two non-local variables: 0 = matrix eps_p (l_M in the matrix, l_M/50
+    in the particles), 1 = particle-cracking kappa (l_P in the particles,
+    l_P/50 in the matrix)."""
+    return np.array([[ell_matrix, ell_matrix / ELL_CONTRAST],
+                     [ell_particle / ELL_CONTRAST, ell_particle]])
+
+
+def config_spheres_two_var(n, vf, count, seed, ell_m=3.0, ell_p=6.0, n_incr=40, dE=1e-3,
+                           precision=1, name=None):
+    """3D RVE of ``count`` random non-overlapping spheres (radius from the
+    volume fraction, r = (3 vf V / (4 pi count))^(1/3)) in the damaging
+    matrix, the spheres cracking (law 2) with their own non-local variable;
+    uniaxial tension E11 in ``n_incr`` steps of ``dE``, other Sigma = 0."""
+    n = tuple(int(x) for x in n)
+    r = sphere_radius_for_count(n, count, vf)
+    cen = rsa_sphere_centres(n, r, count, seed)
+    ph = voxelize_spheres(n, cen, r)
+    ctrl, tgt = uniaxial_path(n_incr, dE)
+    nm = name or "spheres2_%dx%dx%d_s%d" % (n + (seed,))
+    return RVEConfig(nm, n, tuple(float(x) for x in n), ph, [dict(MATRIX), dict(PARTICLE_CRACKING)],
+                     _ell_table_two(ell_m, ell_p), ctrl, tgt, precision,
+                     dict(radius=r, count=count, seed=seed, vf=vf, vf_voxel=float(ph.mean()),
+                          sha256=phase_sha256(ph)))
+
+
+BATCH_GRIDS = (64, 96, 128)
+
+
+def config_batch_member(seed, n_incr=40, dE=1e-3, precision=1):
+    """Member ``seed`` of the batched workload: grid drawn uniformly from
+    {64, 96, 128}^3 and sphere volume fraction uniform in [0.10, 0.30] with
+    numpy.random.default_rng(seed); 30 spheres; l = 3 (matrix) / 6 (particle)
+    voxels."""
+    rng = np.random.default_rng(seed)
+    N = BATCH_GRIDS[int(rng.integers(len(BATCH_GRIDS)))]
+    vf = float(rng.uniform(0.10, 0.30))
+    return config_spheres_two_var((N, N, N), vf, 30, seed, n_incr=n_incr, dE=dE, precision=precision,
+                                  name="batch_s%d_%d" % (seed, N))
+
+
+def config_batch(count=32, n_incr=40, dE=1e-3, precision=1):
+    """The batched workload: members for seeds 0 .. count-1."""
+    return [config_batch_member(s, n_incr, dE, precision) for s in range(count)]
+
+
+def config_adjoint(N=96, n_incr=30, dE=1e-3, precision=0):
+    """The adjoint workload: N^3, 30 spheres at volume fraction 0.20, seed 0,
+    two non-local variables, 30 increments of 1e-3, FP64."""
+    return config_spheres_two_var((N, N, N), 0.20, 30, 0, n_incr=n_incr, dE=dE, precision=precision,
+                                  name="adjoint_%d" % N)

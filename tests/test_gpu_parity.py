@@ -85,6 +85,47 @@ def rand_state(g, seed):
 GRIDS = [(24, 20), (40, 15), (8, 6, 10), (12, 15, 8), (16, 10, 6)]
 
 
+PARAMS3 = [I.MATRIX, I.PARTICLE, dict(I.PARTICLE_CRACKING, eps_C=5e-4, eps_R=4e-3)]
+
+
+@pytest.mark.parametrize("n", [(24, 20), (12, 15, 8)])
+def test_return_map_particle_cracking(n):
+    """Three phases, two non-local variables: the cracking phase's kappa
+    (Jacobi eigenvalues on the GPU, LAPACK in the oracle), its history max
+    and its damage against the oracle."""
+    g = O.Grid(n)
+    d = g.d
+    rng = np.random.default_rng(7)
+    phase = rng.integers(0, 3, g.shape).astype(np.uint8)
+    _, eps, epsp_n, ep_n, _ = rand_state(g, 3)
+    crack = phase.ravel() == 2
+    epsp_n[crack | (phase.ravel() == 1)] = 0.0
+    ep_n[crack] = rng.uniform(0.0, 4e-3, crack.sum())
+    abar = np.stack([rng.uniform(0.0, 0.12, g.V), rng.uniform(0.0, 5e-3, g.V)])
+    h = handle(n, phase, 0, ell=np.array([[2.0, 0.04, 0.04], [0.03, 0.03, 1.5]]), params=PARAMS3)
+    try:
+        rm = O.return_map(O.embed(eps, d), epsp_n, ep_n, abar, phase.ravel().astype(int),
+                          O.phases_from_dicts(PARAMS3))
+        V = g.V
+        outs = dict(sigma=torch.empty(6, V, device="cuda", dtype=torch.float64),
+                    epsp=torch.empty(6, V, device="cuda", dtype=torch.float64),
+                    ep=torch.empty(V, device="cuda", dtype=torch.float64),
+                    D=torch.empty(V, device="cuda", dtype=torch.float64),
+                    alpha=torch.empty(2, V, device="cuda", dtype=torch.float64))
+        pkg.rve_op_return_map(h, dev(eps.T), dev(epsp_n.T), dev(ep_n), dev(abar), outs["sigma"],
+                              outs["epsp"], outs["ep"], outs["D"], outs["alpha"])
+        s_ref = rm["sigma"].T
+        assert np.abs(host(outs["sigma"]) - s_ref).max() <= 1e-12 * np.abs(s_ref).max()
+        assert np.abs(host(outs["ep"]) - rm["ep"]).max() <= 1e-15
+        assert np.abs(host(outs["D"]) - rm["D"]).max() <= 1e-12
+        assert np.abs(host(outs["alpha"]) - rm["alpha"]).max() <= 1e-15
+        kept = crack & (rm["ep"] == ep_n)
+        assert kept.sum() > 0 and (crack & ~kept).sum() > 0   # both branches of the max
+        assert ((rm["D"][crack] > 0) & (rm["D"][crack] < 0.99)).sum() > 0.05 * crack.sum()
+    finally:
+        pkg.rve_free(h)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", GRIDS)
 def test_return_map_and_tangent(n, prec):
@@ -257,9 +298,21 @@ def _sphere_cfg(N, r, n_incr, dE):
                        np.array([[2.0, 0.04]]), ctrl, tgt, 0)
 
 
+# two non-local variables: matrix eps_p and the cracking particle's kappa
+EARLY_CRACKING = dict(I.PARTICLE_CRACKING, eps_C=0.0003, eps_R=0.002)
+
+
+def _sphere2_cfg(N, r, n_incr, dE):
+    cfg = _sphere_cfg(N, r, n_incr, dE)
+    cfg.params = [EARLY_DAMAGE_3D, EARLY_CRACKING]
+    cfg.ell = np.array([[2.0, 0.04], [0.03, 1.5]])
+    return cfg
+
+
 CASES = {
     "2d_disc_16": lambda: _disc_cfg(16, 3.0, 6, 1e-3),
     "3d_sphere_8": lambda: _sphere_cfg(8, 2.6, 5, 1.5e-3),
+    "3d_sphere_cracking_8": lambda: _sphere2_cfg(8, 2.6, 5, 1.5e-3),
 }
 
 
