@@ -260,6 +260,17 @@ inline void prof_end(rve* h, int cls) {
   h->ev_cur_a = nullptr;
 }
 
+// RVE_VERBOSE=2: synchronise after every launch and name the first one
+// that fails (debugging aid; graphs are not captured in this mode)
+inline void launch_check(rve* h, int cls) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "[rve] launch of class %s failed: %s\n", kClassNames[cls], cudaGetErrorString(e));
+    h->verbose = 1;
+  }
+}
+
 // every launch is counted with its algorithmic bytes (each operand read
 // once, each result written once) and, when profiling, timed by events
 #define LAUNCHB(h, cls, bytes, call)     \
@@ -267,6 +278,7 @@ inline void prof_end(rve* h, int cls) {
     prof_begin((h), (cls), (bytes));     \
     call;                                \
     prof_end((h), (cls));                \
+    if ((h)->verbose >= 2) launch_check((h), (cls)); \
   } while (0)
 
 Tables<double> tables64(const rve* h) {
@@ -310,7 +322,7 @@ void graphs_reset(rve* h) {
 // direct launches for the rest of the handle's life.
 template <class F>
 int run_chunk(rve* h, cudaGraphExec_t* ex, long long* tn, double* tb, F&& chunk) {
-  if (!h->graphs || h->prof) {
+  if (!h->graphs || h->prof || h->verbose >= 2) {
     chunk();
     return RVE_OK;
   }
@@ -835,7 +847,7 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   rve_default_options(precision, &h->opt);
   {
     const char* v = std::getenv("RVE_VERBOSE");
-    h->verbose = (v && v[0] && v[0] != '0') ? 1 : 0;
+    h->verbose = (v && v[0] >= '1' && v[0] <= '9') ? v[0] - '0' : 0;
   }
 
   Geo& g = h->g;

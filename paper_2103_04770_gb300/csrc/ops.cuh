@@ -13,6 +13,9 @@
 #pragma once
 #include <math.h>
 
+#include <mutex>
+#include <unordered_set>
+
 #include "fft.cuh"
 #include "fft256.cuh"
 #include "fft_ct.cuh"
@@ -30,7 +33,34 @@ __device__ __forceinline__ long long lmin_(long long a, long long b) { return a 
 
 template <typename K>
 static void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // The limit is a per-kernel attribute shared by every handle and thread.
+  // It is raised once per kernel to the largest value the kernel accepts
+  // (the device's opt-in maximum less the kernel's static shared memory) and
+  // never lowered, so a concurrent caller with a smaller tile cannot shrink
+  // it between another caller's check and launch.  Each launch still gets
+  // only its own dynamic size.
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::unordered_set<const void*> done;
+  const void* key = reinterpret_cast<const void*>(kernel);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(key)) return;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return;
+  }
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes) == cudaSuccess) {
+    done.insert(key);
+  } else {
+    cudaGetLastError();
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
 }
 
 // ---------------------------------------------------------- Fourier symbols

@@ -154,3 +154,21 @@ def test_graphs_match_direct_launches():
     for (c0, s0), (c1, s1) in zip(*out):
         assert c0 == c1
         np.testing.assert_array_equal(s0, s1)
+
+
+@pytest.mark.parametrize("N", [64, 96, 128])
+def test_batch_member_grids_mixed_vs_fp64(N):
+    """One increment of a full-size member of the batched workload for each
+    grid (two variables, runtime mixed-radix FFT schedules with tiles above
+    48 KB of shared memory): the mixed form agrees with the FP64 form within
+    1e-4 of Sigma11, and both converge."""
+    seed = next(s for s in range(64) if I.config_batch_member(s, n_incr=1).n[0] == N)
+    cfg = I.config_batch_member(seed, n_incr=1)
+    out = {}
+    for prec in (0, 1):
+        with pkg.RVE(cfg, precision=prec) as r:
+            info = r.step()
+            assert info["status"] == 0 and info["cg_iters"] > 0 and info["pcg_iters"] > 0
+            out[prec] = r.stress().copy()
+    assert abs(out[1][0] - out[0][0]) <= 1e-4 * abs(out[0][0])
+    assert np.abs(out[1] - out[0]).max() <= 1e-4 * abs(out[0][0])
