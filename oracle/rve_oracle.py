@@ -294,7 +294,7 @@ def positive_principal_norm(e):
     return np.sqrt(np.sum(np.maximum(lam, 0.0) ** 2, axis=-1))
 
 
-def return_map(eps, epsp_n, ep_n, abar, phase, phases):
+def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None):
     """Backward-Euler update of the Lemaitre model (Appendix A.2 with R8-R11)
     at every voxel.
 
@@ -314,6 +314,8 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
     (the consistent tangent of radial return with linear isotropic hardening).
     Particle cracking (law 2, R20): kappa = max(kappa_n, ||<e>_+||) is kept
     in the ep slot, D from abar of the phase's variable, sigma = (1 - D) C e.
+    stiff: optional (V,) field scaling the Young's modulus voxel by voxel
+    (K and mu of the voxel's phase times stiff; 1 where absent).
     """
     Vn = eps.shape[0]
     J = abar.shape[0]
@@ -328,12 +330,13 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
         sel = phase == q
         if not np.any(sel):
             continue
-        K, mu = ph.K, ph.mu
+        sc = np.ones(int(sel.sum())) if stiff is None else np.asarray(stiff, dtype=np.float64)[sel]
+        K, mu = ph.K * sc, ph.mu * sc
         e = eps[sel] - epsp_n[sel]
         tr = e[:, 0] + e[:, 1] + e[:, 2]
         dev = e - tr[:, None] * IVEC[None, :] / 3.0
-        s_tr = 2.0 * mu * dev
-        sig_tr = K * tr[:, None] * IVEC[None, :] + s_tr
+        s_tr = 2.0 * mu[:, None] * dev
+        sig_tr = K[:, None] * tr[:, None] * IVEC[None, :] + s_tr
         qn = np.sqrt(np.einsum("ij,ij->i", s_tr, s_tr))
         theta = np.ones(qn.shape)
         thetabar = np.zeros(qn.shape)
@@ -347,7 +350,7 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
             nhat = np.where(pl[:, None], s_tr / safe_q[:, None], 0.0)
             epsp[sel] = epsp_n[sel] + dl[:, None] * nhat
             ep[sel] = ep_n[sel] + math.sqrt(2.0 / 3.0) * dl
-            sig_eff = sig_tr - 2.0 * mu * dl[:, None] * nhat
+            sig_eff = sig_tr - 2.0 * mu[:, None] * dl[:, None] * nhat
             theta = np.where(pl, 1.0 - 2.0 * mu * dl / safe_q, 1.0)
             thetabar = np.where(pl, 1.0 / (1.0 + ph.H / (3.0 * mu)) - (1.0 - theta), 0.0)
             Dq = damage_of(abar[ph.var][sel], ph) if ph.var >= 0 else np.zeros(qn.shape)
@@ -362,8 +365,9 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases):
                 alpha[ph.var, sel] = kap
         Dq = D[sel]
         sigma[sel] = (1.0 - Dq)[:, None] * sig_eff
-        Cq = (K * np.outer(IVEC, IVEC)[None] + 2.0 * mu * theta[:, None, None] * Pdev[None]
-              - 2.0 * mu * thetabar[:, None, None] * np.einsum("vi,vj->vij", nhat, nhat))
+        Cq = (K[:, None, None] * np.outer(IVEC, IVEC)[None]
+              + 2.0 * (mu * theta)[:, None, None] * Pdev[None]
+              - 2.0 * (mu * thetabar)[:, None, None] * np.einsum("vi,vj->vij", nhat, nhat))
         C[sel] = (1.0 - Dq)[:, None, None] * Cq
     return dict(sigma=sigma, C=C, epsp=epsp, ep=ep, D=D, alpha=alpha)
 
@@ -486,7 +490,7 @@ class Options:
 PARITY_OPTIONS = Options(tol_stag=1e-11, tol_newton=1e-12, cg_rtol=1e-13, pcg_rtol=1e-13)
 
 
-def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_bar_c, opt):
+def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_bar_c, opt, stiff=None):
     """Newton-Raphson on the Galerkin residual at fixed abar (step (i) of
     Algorithm 1, Eq. lin_stress and the CG solve after it):
 
@@ -503,7 +507,7 @@ def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_
     cg_total = 0
     de_rel = None
     while True:
-        rm = return_map(embed(eps_c, d).reshape(Vn, 6), epsp_n, ep_n, abar, phase, phases)
+        rm = return_map(embed(eps_c, d).reshape(Vn, 6), epsp_n, ep_n, abar, phase, phases, stiff)
         sig_c = rm["sigma"][:, comps].reshape(sh + (len(comps),))
         Cc = rm["C"][:, comps][:, :, comps].reshape(sh + (len(comps), len(comps)))
         res = -G_apply(sig_c - sig_bar_c, grid, stress_mask)
@@ -537,17 +541,19 @@ class State:
     abar: np.ndarray            # (J, V)
     sigma: np.ndarray           # (V, 6)
     D: np.ndarray               # (V,)
+    stiff: np.ndarray = None    # (V,) Young's modulus scaling, None = 1
     n_done: int = 0
     curve: list = field(default_factory=list)
 
 
-def make_state(grid, phase_map, phases, ell):
+def make_state(grid, phase_map, phases, ell, stiff=None):
     Vn = grid.V
     nc = len(carried(grid.d))
     J = np.asarray(ell).shape[0]
+    sf = None if stiff is None else np.asarray(stiff, dtype=np.float64).reshape(Vn)
     return State(grid, np.asarray(phase_map).reshape(Vn).astype(np.int64), phases,
                  np.asarray(ell, dtype=np.float64), np.zeros((Vn, nc)), np.zeros((Vn, 6)),
-                 np.zeros(Vn), np.zeros((J, Vn)), np.zeros((Vn, 6)), np.zeros(Vn))
+                 np.zeros(Vn), np.zeros((J, Vn)), np.zeros((Vn, 6)), np.zeros(Vn), sf)
 
 
 def to_mandel_target(t6):
@@ -587,7 +593,7 @@ def step_increment(st, strain_ctrl, target_prev, target, opt):
     while True:
         eps_new, rm, nn, nc_it = mech_solve(g, eps_k.reshape(sh + (nc,)), st.epsp, st.ep,
                                             abar_k, st.phase, st.phases, stress_mask,
-                                            sig_bar, opt)
+                                            sig_bar, opt, st.stiff)
         eps_new = eps_new.reshape(Vn, nc)
         newton_tot += nn
         cg_tot += nc_it
@@ -637,9 +643,10 @@ def homogenized_strain(st):
     return e / MANDEL_W
 
 
-def run_load_path(grid, phase_map, phase_dicts, ell, strain_ctrl, target, opt, n_incr=None):
+def run_load_path(grid, phase_map, phase_dicts, ell, strain_ctrl, target, opt, n_incr=None,
+                  stiff=None):
     """Algorithm 1's time loop over a load path; returns the state."""
-    st = make_state(grid, phase_map, phases_from_dicts(phase_dicts), ell)
+    st = make_state(grid, phase_map, phases_from_dicts(phase_dicts), ell, stiff)
     tgt = np.asarray(target, dtype=np.float64)
     n = len(tgt) if n_incr is None else n_incr
     prev = np.zeros(6)
