@@ -287,6 +287,63 @@ int rve_batch_size(const rve_batch_t* b);
  * their original streams back. */
 void rve_batch_free(rve_batch_t* b);
 
+/* ------------------------------------------------ adjoint over the load path
+ * The paper has no adjoint; these calls give the exact derivative of the
+ * discrete converged load path, for inverse problems and gradient-based
+ * design.  Objective: J = <sigma_N>_11, the homogenised axial stress after
+ * the last increment N of the load path.  FP64 handles only. */
+
+/* Per-voxel factor s(x) > 0 on the Young's modulus of the voxel's phase (K
+ * and mu scale with it) for the forward solve and the adjoint; s: host array
+ * [V] (x1 fastest), copied; NULL removes the field (s = 1).
+ * Errors: RVE_ERR_ARG (non-positive or non-finite entry), RVE_ERR_OOM,
+ * RVE_ERR_CUDA. */
+int rve_set_stiffness_field(rve_t* h, const double* s);
+
+/* Forward pass of the adjoint: re-initialise the state, run every increment
+ * of the load path (Algorithm 1) and keep a checkpoint of the converged
+ * state after 0, k, 2k, ... increments (k = checkpoint_every) in device
+ * memory owned by the handle (about (nc + 8 + J) V doubles each, plus k
+ * increments' states for the recomputation).  J (nullable): the objective.
+ * Errors: RVE_ERR_ARG (FP32/mixed handle, k < 1), RVE_ERR_STATE (phases or
+ * load path not set), the step errors of rve_step_increment. */
+int rve_adjoint_forward(rve_t* h, int checkpoint_every, double* J);
+
+typedef struct {
+  int status;
+  int increments;       /* N */
+  int recomputed;       /* increments re-solved from checkpoints */
+  int checkpoints;
+  int transposed_staggered_iters;      /* sum over increments */
+  int max_transposed_staggered_iters;
+  long long cg_iters, pcg_iters;       /* adjoint linear solves */
+} rve_adjoint_info;
+
+/* Reverse pass after rve_adjoint_forward: for n = N .. 1, re-solve the
+ * increments of each checkpoint segment from its checkpoint, then solve the
+ * adjoint of increment n: the transposed staggered scheme alternates
+ *   P C_T lambda_n = P [d(sigma, alpha, h)/d eps]^T (s_n, mu_n, eta_n)   (CG
+ *     on G* C_T, Eqs. eqdiscrete2 / lin_stress; P = G*, lambda_n in the
+ *     compatible, mixed-control space)
+ *   L_j mu_{n,j} = [d sigma / d abar_j]^T (s_n - lambda_n)   (Algorithm 2)
+ * until both change by at most tol_stag (relative, max_stag sweeps), with
+ * s_N = dJ e_11 / V, s_n = 0 before, and carries the history adjoint
+ * eta_{n-1} = [d(sigma, alpha, h_n)/d h_{n-1}]^T (s_n - lambda_n, mu_n,
+ * eta_n).  The linear solves use cg_rtol / pcg_rtol and max_cg / max_pcg of
+ * the handle's options.  Outputs, each scaled by dJ (the upstream
+ * derivative), any may be NULL:
+ *   grad_params [n_phases][4]: dJ/d(sigma_y, H, eps_C, eps_R) per phase
+ *     (kappa_C, kappa_R in the eps_C, eps_R slots of cracking phases);
+ *   grad_ell [J]: dJ/dl_j, l_j the largest entry of row j of the length
+ *     table, the whole row scaling with it;
+ *   grad_stiff [V] (host): dJ/ds(x) at the current stiffness field.
+ * The handle is left at the converged state after increment N (its
+ * per-voxel sigma and D buffers hold the last adjoint linearisation).
+ * Errors: RVE_ERR_STATE (no forward pass), RVE_ERR_NOT_CONVERGED,
+ * RVE_ERR_NUMERIC, RVE_ERR_CUDA. */
+int rve_adjoint_backward(rve_t* h, double dJ, double* grad_params, double* grad_ell, double* grad_stiff,
+                         rve_adjoint_info* info);
+
 /* ------------------------------------------------ allocation-free variant
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory, such as an application that hands

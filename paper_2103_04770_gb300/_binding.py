@@ -49,6 +49,16 @@ class SolverOptions(ctypes.Structure):
                 ("max_pcg", ctypes.c_int), ("min_stag", ctypes.c_int), ("check_every", ctypes.c_int)]
 
 
+class AdjointInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("increments", ctypes.c_int), ("recomputed", ctypes.c_int),
+                ("checkpoints", ctypes.c_int), ("transposed_staggered_iters", ctypes.c_int),
+                ("max_transposed_staggered_iters", ctypes.c_int), ("cg_iters", ctypes.c_longlong),
+                ("pcg_iters", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class StepInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("increment", ctypes.c_int),
                 ("staggered_iters", ctypes.c_int), ("newton_iters", ctypes.c_int),
@@ -90,6 +100,9 @@ _SIGNATURES = {
     "rve_op_helmholtz_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(_I)]),
     "rve_op_apply_gamma_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D),
                                         ctypes.POINTER(ctypes.c_uint8), _P, _P, _P]),
+    "rve_set_stiffness_field": (_I, [_P, _P]),
+    "rve_adjoint_forward": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "rve_adjoint_backward": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(AdjointInfo)]),
     "rve_set_graphs": (_I, [_P, _I]),
     "rve_autotune": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rve_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _I]),
@@ -291,6 +304,34 @@ def rve_op_apply_gamma_noalloc(dim, n, L, strain_ctrl, tau, out, stream=None):
     c = (ctypes.c_uint8 * 6)(*[int(x) for x in strain_ctrl])
     _check(lib().rve_op_apply_gamma_noalloc(int(dim), n3, L3, c, _ptr(tau), _ptr(out),
                                             _stream_handle(stream)), "rve_op_apply_gamma_noalloc")
+
+
+# ------------------------------------------------------------- adjoint
+def rve_set_stiffness_field(h, s):
+    """s: per-voxel Young's modulus factor (host array, x1 fastest) or None."""
+    if s is None:
+        _check(lib().rve_set_stiffness_field(h, None), "rve_set_stiffness_field")
+        return
+    a = np.ascontiguousarray(np.asarray(s, dtype=np.float64).reshape(-1))
+    _check(lib().rve_set_stiffness_field(h, a.ctypes.data), "rve_set_stiffness_field")
+
+
+def rve_adjoint_forward(h, checkpoint_every=5):
+    J = ctypes.c_double()
+    _check(lib().rve_adjoint_forward(h, int(checkpoint_every), ctypes.byref(J)), "rve_adjoint_forward")
+    return J.value
+
+
+def rve_adjoint_backward(h, dJ, n_phases, n_vars, n_voxels):
+    """Returns (grad_params [n_phases, 4], grad_ell [n_vars], grad_stiff [V], info)."""
+    gp = np.zeros((n_phases, 4))
+    ge = np.zeros(max(n_vars, 1))
+    gs = np.zeros(n_voxels)
+    info = AdjointInfo()
+    s = lib().rve_adjoint_backward(h, float(dJ), gp.ctypes.data, ge.ctypes.data, gs.ctypes.data,
+                                   ctypes.byref(info))
+    _check(s, "rve_adjoint_backward")
+    return gp, ge[:n_vars], gs, info.as_dict()
 
 
 # ------------------------------------------- graphs, autotuning, batches

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librve.so")
-SOURCES = ["abi.cu", "ops_f32.cu", "ops_f64.cu", "ops_common.cu", "noalloc.cu"]
+SOURCES = ["abi.cu", "ops_f32.cu", "ops_f64.cu", "ops_common.cu", "noalloc.cu", "adjoint_ops.cu"]
 
 
 def _nvcc():

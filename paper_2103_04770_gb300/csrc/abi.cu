@@ -19,6 +19,7 @@
 #include <new>
 #include <vector>
 
+#include "adjoint_ops.h"
 #include "ops.h"
 #include "rve.h"
 
@@ -72,6 +73,8 @@ struct PendingEv {
 };
 
 }  // namespace
+
+struct AdjointStore;
 
 struct rve {
   int dim = 0, prec = 0, J = 0;
@@ -147,6 +150,8 @@ struct rve {
   long long g_pcg_n[kMaxVars][KC_COUNT] = {};
   double g_pcg_b[kMaxVars][KC_COUNT] = {};
   bool stepped = false;  // an increment has been attempted (autotuning closed)
+  double* stiff = nullptr;  // per-voxel modulus factor (nullptr: 1 everywhere)
+  AdjointStore* adj = nullptr;
 };
 
 namespace {
@@ -386,7 +391,7 @@ struct Alg {
 
   static void return_map(rve* h, const double* abar_use) {
     LAUNCHB(h, KC_RETURN_MAP, VV(h) * (8.0 * h->g.nc + 169.0 + 16.0 * h->J + (2.0 + h->g.nc) * RS), Op::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, h->eps, h->epsp_n, h->ep_n, abar_use,
-                   h->sigma, h->epsp, h->ep, h->D, h->alpha, (R*)h->desc, h->part));
+                   h->sigma, h->epsp, h->ep, h->D, h->alpha, (R*)h->desc, h->part, h->stiff));
     LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 7, FIN_SUMS, nullptr,
                h->dscal + OFF_SIGMEAN, 1.0 / (double)h->g.V));
     LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 7 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
@@ -1062,10 +1067,15 @@ int rve_create(rve_t** out, int dim, const int n[3], const double L[3], int prec
   }
 }
 
+void adjoint_free(rve* h);
+
 void rve_free(rve_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   graphs_reset(h);
+  adjoint_free(h);
+  if (h->stiff) cudaFree(h->stiff);
+  h->stiff = nullptr;
   prof_resolve(h);
   for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
   h->ev_free.clear();
@@ -1244,10 +1254,10 @@ int rve_op_return_map(rve_t* h, const double* eps, const double* epsp_n, const d
   const double* abar_use = abar ? abar : h->abar_n;
   if (h->prec == RVE_MIXED)
     Ops<float>::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, eps, epsp_n, ep_n, abar_use, sigma,
-                           epsp, ep, D, alpha_use, (float*)h->desc, h->part);
+                           epsp, ep, D, alpha_use, (float*)h->desc, h->part, h->stiff);
   else
     Ops<double>::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, eps, epsp_n, ep_n, abar_use,
-                            sigma, epsp, ep, D, alpha_use, (double*)h->desc, h->part);
+                            sigma, epsp, ep, D, alpha_use, (double*)h->desc, h->part, h->stiff);
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   return RVE_OK;
@@ -1525,4 +1535,364 @@ void rve_batch_free(rve_batch_t* b) {
     cudaStreamDestroy(b->own[i]);
   }
   delete b;
+}
+
+// ============================================================ adjoint sweep
+// Saved converged state after n_done increments (restart point).
+struct AdjCkpt {
+  int n_done = 0;
+  double E_prev[6], sig_mean[6], eps_mean[6], D_mean = 0, D_max = 0;
+  double *eps_conv = nullptr, *epsp_n = nullptr, *ep_n = nullptr, *abar_n = nullptr;
+};
+
+struct AdjointStore {
+  int every = 0, n_total = 0;
+  double J = 0;
+  std::vector<AdjCkpt> ckpt;   // after 0, every, 2 every, ... increments
+  AdjCkpt last;                // after the last increment
+  // per increment of one segment: eps_n, abar_n and the history before it
+  std::vector<double*> seg_eps, seg_abar, seg_epsp, seg_ep;
+  double *eta_p = nullptr, *eta_e = nullptr, *eta_p2 = nullptr, *eta_e2 = nullptr;
+  double *lam = nullptr, *lam2 = nullptr, *mu = nullptr, *mu2 = nullptr;
+  double *v_eps = nullptr, *v_abar = nullptr, *v_theta = nullptr, *v_stiff = nullptr, *g_stiff = nullptr;
+  double *b = nullptr, *G1 = nullptr, *G2 = nullptr, *red = nullptr;
+  double* part = nullptr;      // [4 kMaxPhases][max_blocks] block partial sums
+  std::vector<void*> allocs;
+  bool forward_done = false;
+};
+
+void adjoint_free(rve* h) {
+  if (!h->adj) return;
+  for (void* p : h->adj->allocs) cudaFree(p);
+  delete h->adj;
+  h->adj = nullptr;
+}
+
+namespace {
+
+int adj_alloc(AdjointStore* a, double** p, size_t n) {
+  void* v = nullptr;
+  const cudaError_t e = cudaMalloc(&v, std::max<size_t>(n, 2) * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? RVE_ERR_OOM : RVE_ERR_CUDA;
+  }
+  a->allocs.push_back(v);
+  *p = (double*)v;
+  return RVE_OK;
+}
+
+int ckpt_alloc(rve* h, AdjointStore* a, AdjCkpt& c) {
+  const size_t V = (size_t)h->g.V, J = (size_t)std::max(h->J, 1);
+  int s;
+  if ((s = adj_alloc(a, &c.eps_conv, h->g.nc * V)) || (s = adj_alloc(a, &c.epsp_n, 6 * V)) ||
+      (s = adj_alloc(a, &c.ep_n, V)) || (s = adj_alloc(a, &c.abar_n, J * V)))
+    return s;
+  return RVE_OK;
+}
+
+int ckpt_save(rve* h, AdjCkpt& c) {
+  const size_t V = (size_t)h->g.V, J = (size_t)std::max(h->J, 1);
+  CK(cudaMemcpyAsync(c.eps_conv, h->eps_conv, h->g.nc * V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(c.epsp_n, h->epsp_n, 6 * V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(c.ep_n, h->ep_n, V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(c.abar_n, h->abar_n, J * V * 8, cudaMemcpyDeviceToDevice, h->st));
+  c.n_done = h->n_done;
+  for (int k = 0; k < 6; k++) {
+    c.E_prev[k] = h->E_prev[k];
+    c.sig_mean[k] = h->sig_mean[k];
+    c.eps_mean[k] = h->eps_mean[k];
+  }
+  c.D_mean = h->D_mean;
+  c.D_max = h->D_max;
+  return RVE_OK;
+}
+
+int ckpt_load(rve* h, const AdjCkpt& c) {
+  const size_t V = (size_t)h->g.V, J = (size_t)std::max(h->J, 1);
+  CK(cudaMemcpyAsync(h->eps_conv, c.eps_conv, h->g.nc * V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->eps, c.eps_conv, h->g.nc * V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->epsp_n, c.epsp_n, 6 * V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->ep_n, c.ep_n, V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->abar_n, c.abar_n, J * V * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->n_done = c.n_done;
+  for (int k = 0; k < 6; k++) {
+    h->E_prev[k] = c.E_prev[k];
+    h->sig_mean[k] = c.sig_mean[k];
+    h->eps_mean[k] = c.eps_mean[k];
+  }
+  h->D_mean = c.D_mean;
+  h->D_max = c.D_max;
+  return RVE_OK;
+}
+
+int adj_setup(rve* h, int every) {
+  adjoint_free(h);
+  AdjointStore* a = new (std::nothrow) AdjointStore();
+  if (!a) return RVE_ERR_OOM;
+  h->adj = a;
+  a->every = every;
+  a->n_total = h->n_incr;
+  const size_t V = (size_t)h->g.V, nc = h->g.nc, J = (size_t)std::max(h->J, 1);
+  const int nck = (h->n_incr + every - 1) / every;
+  a->ckpt.resize(nck);
+  int s;
+  for (auto& c : a->ckpt)
+    if ((s = ckpt_alloc(h, a, c))) return s;
+  if ((s = ckpt_alloc(h, a, a->last))) return s;
+  a->seg_eps.resize(every);
+  a->seg_abar.resize(every);
+  a->seg_epsp.resize(every);
+  a->seg_ep.resize(every);
+  for (int k = 0; k < every; k++)
+    if ((s = adj_alloc(a, &a->seg_eps[k], nc * V)) || (s = adj_alloc(a, &a->seg_abar[k], J * V)) ||
+        (s = adj_alloc(a, &a->seg_epsp[k], 6 * V)) || (s = adj_alloc(a, &a->seg_ep[k], V)))
+      return s;
+  if ((s = adj_alloc(a, &a->eta_p, 6 * V)) || (s = adj_alloc(a, &a->eta_e, V)) ||
+      (s = adj_alloc(a, &a->eta_p2, 6 * V)) || (s = adj_alloc(a, &a->eta_e2, V)) ||
+      (s = adj_alloc(a, &a->lam, nc * V)) || (s = adj_alloc(a, &a->lam2, nc * V)) ||
+      (s = adj_alloc(a, &a->mu, J * V)) || (s = adj_alloc(a, &a->mu2, J * V)) ||
+      (s = adj_alloc(a, &a->v_eps, nc * V)) || (s = adj_alloc(a, &a->v_abar, J * V)) ||
+      (s = adj_alloc(a, &a->v_theta, 4 * V)) || (s = adj_alloc(a, &a->v_stiff, V)) ||
+      (s = adj_alloc(a, &a->g_stiff, V)) || (s = adj_alloc(a, &a->b, nc * V)) ||
+      (s = adj_alloc(a, &a->G1, 3 * V)) || (s = adj_alloc(a, &a->G2, 3 * V)) ||
+      (s = adj_alloc(a, &a->red, 64)) || (s = adj_alloc(a, &a->part, (size_t)4 * kMaxPhases * h->lc.max_blocks)))
+    return s;
+  return RVE_OK;
+}
+
+struct AdjSums {
+  double theta[kMaxPhases][4];
+  double ell[kMaxVars];
+  long long cg, pcg;
+  int outer, outer_max;
+};
+
+// real-space gradient fields G_d a = F^-1(k_d F a), d = 0..dim-1, into out [d][V]
+void grad_field(rve* h, const Tables<double>& t, const double* a, double* out) {
+  const Geo& g = h->g;
+  using A = Alg<double>;
+  C2<double>* hr = (C2<double>*)h->hr;
+  C2<double>* W = (C2<double>*)h->S;
+  A::forward1(h, t, a, hr);
+  LAUNCHB(h, KC_MISC, 0.0, Ops<double>::helm_expand(g, t, h->lc, h->st, W, (C2<double>*)h->hp, hr, 0.0, nullptr, 1));
+  if (g.d == 3) LAUNCHB(h, KC_MISC, 0.0, Ops<double>::strided_plain(g, t, h->lc, h->st, W, g.d, 1, +1, nullptr));
+  LAUNCHB(h, KC_MISC, 0.0, Ops<double>::xinv_store64(g, t, h->lc, h->st, W, g.d, out));
+}
+
+// read `n` finalised scalars from the adjoint reduction area
+int red_read(rve* h, double* out, int n) {
+  CK(cudaMemcpyAsync(h->hscal, h->adj->red, n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
+  for (int i = 0; i < n; i++) out[i] = h->hscal[i];
+  return RVE_OK;
+}
+
+// One increment of the reverse sweep at segment slot k (state of increment
+// n: eps_n, abar_n, history h_{n-1}); seed = dJ/V on sigma_11 at the last
+// increment, 0 before.
+int adj_increment(rve* h, int k, double seed, AdjSums& acc) {
+  AdjointStore* a = h->adj;
+  const Geo& g = h->g;
+  const long long V = g.V;
+  const int nc = g.nc, J = h->J;
+  const Tables<double> t = tables<double>(h);
+  const int nb = h->lc.n_ew_blocks, ps = h->lc.max_blocks;
+  double* part = a->part;
+  AdjState st{h->phase, a->seg_eps[k], a->seg_epsp[k], a->seg_ep[k], a->seg_abar[k], h->stiff};
+  // consistent tangent at the converged state (descriptor used by CG)
+  LAUNCHB(h, KC_RETURN_MAP, 0.0, Ops<double>::return_map(g, h->lc, h->st, h->pt_dev, J, h->phase, st.eps, st.epsp_prev,
+                                                          st.ep_prev, st.abar, h->sigma, h->epsp, h->ep, h->D,
+                                                          h->alpha, (double*)h->desc, h->part, h->stiff));
+  CK(cudaMemsetAsync(a->lam, 0, nc * V * 8, h->st));
+  CK(cudaMemsetAsync(a->mu, 0, std::max(J, 1) * V * 8, h->st));
+  AdjDirs d_eps{nc, {}, {}}, d_abar{J, {}, {}}, d_hist{8, {}, {}}, d_theta{4, {}, {}};
+  for (int c = 0; c < nc; c++) { d_eps.kind[c] = AD_EPS; d_eps.idx[c] = c; }
+  for (int j = 0; j < J; j++) { d_abar.kind[j] = AD_ABAR; d_abar.idx[j] = j; }
+  for (int c = 0; c < 6; c++) { d_hist.kind[c] = AD_EPSP; d_hist.idx[c] = c; }
+  d_hist.kind[6] = AD_EP; d_hist.idx[6] = 0;
+  d_hist.kind[7] = AD_STIFF; d_hist.idx[7] = 0;
+  for (int i = 0; i < 4; i++) { d_theta.kind[i] = AD_THETA; d_theta.idx[i] = i; }
+  AdjOut out{a->v_eps, a->eta_p2, a->eta_e2, a->v_abar, a->v_theta, a->v_stiff};
+  const int maxo = std::max(1, h->opt.max_stag);
+  int it = 0;
+  for (;;) {
+    // mechanical adjoint: P C_T lam = P [d(sigma, alpha, h)/d eps]^T (seed, mu, eta)
+    LAUNCHB(h, KC_MISC, 0.0, adj_local_vjp(g, h->pt_dev, J, st, AdjCot{seed, nullptr, a->mu, a->eta_p, a->eta_e}, out, d_eps, nb, h->st));
+    int s = Alg<double>::op_apply_gamma(h, a->v_eps, a->b);
+    if (s) return s;
+    int iters = 0;
+    s = Alg<double>::op_cg(h, a->b, a->lam2, h->opt.cg_rtol, h->opt.max_cg, &iters);
+    acc.cg += iters;
+    if (s) return s;
+    // Helmholtz adjoints: L_j mu_j = [d sigma / d abar_j]^T (seed e_11 - lam)
+    if (J > 0) {
+      LAUNCHB(h, KC_MISC, 0.0, adj_local_vjp(g, h->pt_dev, J, st, AdjCot{seed, a->lam2, nullptr, nullptr, nullptr}, out, d_abar, nb, h->st));
+      for (int j = 0; j < J; j++) {
+        s = Alg<double>::op_helm_solve(h, j, a->v_abar + (size_t)j * V, a->mu2 + (size_t)j * V, h->opt.pcg_rtol,
+                                            h->opt.max_pcg, &iters);
+        acc.pcg += iters;
+        if (s) return s;
+      }
+    }
+    // change of both adjoints since the last sweep
+    double r[4] = {0, 0, 0, 0};
+    LAUNCHB(h, KC_MISC, 0.0, adj_absmax2((long long)nc * V, a->lam2, a->lam, part, ps, nb, h->st));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part, nb, ps, 2, FIN_MAXS, nullptr, a->red, 1.0));
+    if (J > 0) {
+      LAUNCHB(h, KC_MISC, 0.0, adj_absmax2((long long)J * V, a->mu2, a->mu, part, ps, nb, h->st));
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part, nb, ps, 2, FIN_MAXS, nullptr, a->red + 2, 1.0));
+    }
+    if ((s = red_read(h, r, 4))) return s;
+    std::swap(a->lam, a->lam2);
+    std::swap(a->mu, a->mu2);
+    it++;
+    const double dl = r[0] / std::max(r[1], 1e-300), dm = J > 0 ? r[2] / std::max(r[3], 1e-300) : 0.0;
+    if (h->verbose)
+      std::fprintf(stderr, "[rve] adjoint sweep %d d_lambda %.3e d_mu %.3e\n", it, dl, dm);
+    if (!(dl == dl) || !(dm == dm)) return RVE_ERR_NUMERIC;
+    if ((dl <= h->opt.tol_stag || r[1] == 0.0) && (dm <= h->opt.tol_stag || J == 0 || r[3] == 0.0)) break;
+    if (it >= maxo) return RVE_ERR_NOT_CONVERGED;
+  }
+  acc.outer += it;
+  acc.outer_max = std::max(acc.outer_max, it);
+  // history adjoint, modulus-field and parameter products with the full cotangent
+  const AdjCot full{seed, a->lam, a->mu, a->eta_p, a->eta_e};
+  LAUNCHB(h, KC_MISC, 0.0, adj_local_vjp(g, h->pt_dev, J, st, full, out, d_hist, nb, h->st));
+  LAUNCHB(h, KC_MISC, 0.0, adj_local_vjp(g, h->pt_dev, J, st, full, out, d_theta, nb, h->st));
+  LAUNCHB(h, KC_MISC, 0.0, adj_axpy(V, 1.0, a->v_stiff, a->g_stiff, nb, h->st));
+  LAUNCHB(h, KC_MISC, 0.0, adj_phase_sums(V, h->phase, a->v_theta, part, ps, nb, h->st));
+  // the finaliser reduces at most 16 slots per call
+  for (int half = 0; half < 4 * kMaxPhases; half += 16)
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part + (size_t)half * ps, nb, ps, 16, FIN_SUMS, nullptr, a->red + half, 1.0));
+  double th[4 * kMaxPhases];
+  int s = red_read(h, th, 4 * kMaxPhases);
+  if (s) return s;
+  for (int q = 0; q < kMaxPhases; q++)
+    for (int i = 0; i < 4; i++) acc.theta[q][i] += th[4 * q + i];
+  // characteristic lengths: - <mu_j, (dL_j/dl_j) abar_j>
+  for (int j = 0; j < J; j++) {
+    double own2 = 0.0;
+    for (int q = 0; q < h->n_phases; q++) own2 = std::max(own2, h->pt_host.ell2[j][q]);
+    if (!(own2 > 0.0)) continue;
+    PhaseWeights w{};
+    for (int q = 0; q < kMaxPhases; q++) w.w[q] = q < h->n_phases ? 2.0 * h->pt_host.ell2[j][q] / std::sqrt(own2) : 0.0;
+    grad_field(h, t, a->mu + (size_t)j * V, a->G1);
+    grad_field(h, t, a->seg_abar[k] + (size_t)j * V, a->G2);
+    LAUNCHB(h, KC_MISC, 0.0, adj_weighted_dot(V, g.d, h->phase, w, a->G1, a->G2, part, ps, nb, h->st));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part, nb, ps, 1, FIN_SUMS, nullptr, a->red, 1.0));
+    double dv = 0.0;
+    if ((s = red_read(h, &dv, 1))) return s;
+    acc.ell[j] -= dv;
+  }
+  std::swap(a->eta_p, a->eta_p2);
+  std::swap(a->eta_e, a->eta_e2);
+  return RVE_OK;
+}
+
+}  // namespace
+
+int rve_set_stiffness_field(rve_t* h, const double* s) {
+  if (!h) return RVE_ERR_ARG;
+  if (!s) {
+    if (h->stiff) cudaFree(h->stiff);
+    h->stiff = nullptr;
+    return RVE_OK;
+  }
+  const size_t V = (size_t)h->g.V;
+  for (size_t v = 0; v < V; v++)
+    if (!(s[v] > 0.0) || !std::isfinite(s[v])) return RVE_ERR_ARG;
+  if (!h->stiff) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, V * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return RVE_ERR_OOM;
+    }
+    h->stiff = (double*)p;
+  }
+  CK(cudaMemcpy(h->stiff, s, V * sizeof(double), cudaMemcpyHostToDevice));
+  return RVE_OK;
+}
+
+int rve_adjoint_forward(rve_t* h, int checkpoint_every, double* J) {
+  if (!h || checkpoint_every < 1) return RVE_ERR_ARG;
+  if (h->prec != RVE_FP64) return RVE_ERR_ARG;
+  if (!h->phases_set || !h->path_set) return RVE_ERR_STATE;
+  try {
+    int s = adj_setup(h, checkpoint_every);
+    if (s) { adjoint_free(h); return s; }
+    AdjointStore* a = h->adj;
+    if ((s = reset_state(h))) return s;
+    h->stepped = true;
+    for (int n = 0; n < h->n_incr; n++) {
+      if (n % checkpoint_every == 0 && (s = ckpt_save(h, a->ckpt[n / checkpoint_every]))) return s;
+      if ((s = Alg<double>::step(h, nullptr))) return s;
+    }
+    if ((s = ckpt_save(h, a->last))) return s;
+    CK(cudaStreamSynchronize(h->st));
+    a->J = h->sig_mean[0];
+    a->forward_done = true;
+    if (J) *J = a->J;
+    return RVE_OK;
+  } catch (...) {
+    return RVE_ERR_OOM;
+  }
+}
+
+int rve_adjoint_backward(rve_t* h, double dJ, double* grad_params, double* grad_ell, double* grad_stiff,
+                         rve_adjoint_info* info) {
+  if (!h) return RVE_ERR_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!h->adj || !h->adj->forward_done) return RVE_ERR_STATE;
+  AdjointStore* a = h->adj;
+  const long long V = h->g.V;
+  AdjSums acc{};
+  int recomputed = 0;
+  try {
+    CK(cudaMemsetAsync(a->eta_p, 0, 6 * V * 8, h->st));
+    CK(cudaMemsetAsync(a->eta_e, 0, V * 8, h->st));
+    CK(cudaMemsetAsync(a->g_stiff, 0, V * 8, h->st));
+    const int N = a->n_total, every = a->every;
+    int s = RVE_OK;
+    for (int seg = (N - 1) / every; seg >= 0 && !s; seg--) {
+      const int c0 = seg * every, c1 = std::min(N, c0 + every);
+      if ((s = ckpt_load(h, a->ckpt[seg]))) break;
+      // recompute the segment, keeping each increment's state
+      for (int n = c0; n < c1 && !s; n++) {
+        const int k = n - c0;
+        CK(cudaMemcpyAsync(a->seg_epsp[k], h->epsp_n, 6 * V * 8, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(a->seg_ep[k], h->ep_n, V * 8, cudaMemcpyDeviceToDevice, h->st));
+        if ((s = Alg<double>::step(h, nullptr))) break;
+        recomputed++;
+        CK(cudaMemcpyAsync(a->seg_eps[k], h->eps_conv, h->g.nc * V * 8, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(a->seg_abar[k], h->abar_n, std::max(h->J, 1) * V * 8, cudaMemcpyDeviceToDevice, h->st));
+      }
+      for (int n = c1 - 1; n >= c0 && !s; n--)
+        s = adj_increment(h, n - c0, n == N - 1 ? dJ / (double)V : 0.0, acc);
+    }
+    int s2 = ckpt_load(h, a->last);
+    if (info) {
+      info->status = s;
+      info->increments = N;
+      info->recomputed = recomputed;
+      info->checkpoints = (int)a->ckpt.size();
+      info->transposed_staggered_iters = acc.outer;
+      info->max_transposed_staggered_iters = acc.outer_max;
+      info->cg_iters = acc.cg;
+      info->pcg_iters = acc.pcg;
+    }
+    if (s) return s;
+    if (s2) return s2;
+    if (grad_params)
+      for (int q = 0; q < h->n_phases; q++)
+        for (int i = 0; i < 4; i++) grad_params[4 * q + i] = acc.theta[q][i];
+    if (grad_ell)
+      for (int j = 0; j < h->J; j++) grad_ell[j] = acc.ell[j];
+    if (grad_stiff) CK(cudaMemcpy(grad_stiff, a->g_stiff, V * 8, cudaMemcpyDeviceToHost));
+    return RVE_OK;
+  } catch (...) {
+    return RVE_ERR_OOM;
+  }
 }

@@ -1092,7 +1092,7 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
              const double* __restrict__ ep_n, const double* __restrict__ abar,
              double* __restrict__ sigma, double* __restrict__ epsp, double* __restrict__ ep,
              double* __restrict__ Dout, double* __restrict__ alpha, R* __restrict__ desc,
-             double* __restrict__ part, int pstride) {
+             double* __restrict__ part, int pstride, const double* __restrict__ stiff) {
   const long long V = g.V;
   const int nc = g.nc;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -1107,7 +1107,9 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
     const double tr = e[0] + e[1] + e[2];
     double dev[6];
     for (int c = 0; c < 6; c++) dev[c] = e[c] - (c < 3 ? tr / 3.0 : 0.0);
-    const double K = P.K, mu = P.mu;
+    // per-voxel modulus factor (1 without a stiffness field)
+    const double sc = stiff ? stiff[v] : 1.0;
+    const double K = P.K * sc, mu = P.mu * sc;
     double q = 0.0;
     for (int c = 0; c < 6; c++) q += dev[c] * dev[c];
     q = 2.0 * mu * sqrt(q);
@@ -1494,9 +1496,9 @@ template <typename R>
 void Ops<R>::return_map(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const PhaseTable* pt, int J,
                         const uint8_t* phase, const double* eps, const double* epsp_n, const double* ep_n,
                         const double* abar, double* sigma, double* epsp, double* ep, double* D,
-                        double* alpha, R* desc, double* part) {
+                        double* alpha, R* desc, double* part, const double* stiff) {
   k_return_map<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, pt, J, phase, eps, epsp_n, ep_n, abar, sigma,
-                                                       epsp, ep, D, alpha, desc, part, lc.max_blocks);
+                                                       epsp, ep, D, alpha, desc, part, lc.max_blocks, stiff);
 }
 
 template <typename R>

@@ -107,7 +107,8 @@ struct Ops {
   static void return_map(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const PhaseTable* pt,
                          int J, const uint8_t* phase, const double* eps, const double* epsp_n,
                          const double* ep_n, const double* abar, double* sigma, double* epsp,
-                         double* ep, double* D, double* alpha, R* desc, double* part);
+                         double* ep, double* D, double* alpha, R* desc, double* part,
+                         const double* stiff = nullptr);
   static void tangent_apply64(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const R* desc,
                               const double* p, double* tau);
   // eps += x; partials: max |x| per comp, sum eps per comp
