@@ -49,8 +49,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=1)
-    ap.add_argument("--workload", default="spheres256", choices=["spheres256", "batch"],
-                    help="batch: the 32-RVE {64,96,128}^3 two-variable workload (its own JSON line)")
+    ap.add_argument("--workload", default="spheres256", choices=["spheres256", "batch", "adjoint"],
+                    help="batch: the 32-RVE {64,96,128}^3 two-variable workload; adjoint: gradients of "
+                         "the final stress of the 96^3 two-variable RVE (each its own JSON line)")
+    ap.add_argument("--adj-incr", type=int, default=30)
+    ap.add_argument("--adj-every", type=int, default=5)
+    ap.add_argument("--adj-fd", default="0:sigma_y,ell0",
+                    help="comma list of gradients to check by central differences (h = 1e-6 relative)")
     ap.add_argument("--batch-count", type=int, default=32)
     ap.add_argument("--autotune-reps", type=int, default=2)
     ap.add_argument("--no-seq", action="store_true", help="batch: skip the one-at-a-time comparison")
@@ -418,9 +423,89 @@ def run_batch(args, rank, ws, dist):
     return out
 
 
+# ------------------------------------------------------------------ adjoint
+def run_adjoint(args):
+    """The adjoint workload: 96^3, 30 spheres at 20 %, two non-local
+    variables, FP64, checkpoint every 5 increments; d<sigma_N>_11 with
+    respect to the per-phase parameters, both lengths and the per-voxel
+    modulus field, timed, with central-difference checks."""
+    import torch
+    import rve_inputs as I
+    import paper_2103_04770_gb300 as pkg
+
+    torch.cuda.init()
+    cfg = I.config_adjoint(n_incr=args.adj_incr)
+    V = int(np.prod(cfg.n))
+    J = int(cfg.ell.shape[0])
+    opt = pkg.rve_default_options(0)
+    opt.tol_stag, opt.tol_newton, opt.cg_rtol, opt.pcg_rtol = 1e-10, 1e-11, 1e-12, 1e-12
+    opt.max_stag, opt.max_newton, opt.max_cg, opt.max_pcg = 200, 50, 20000, 20000
+
+    def handle(params=None, ell=None):
+        h = pkg.rve_create(3, cfg.n, cfg.L, 0, J)
+        pkg.rve_set_options(h, opt)
+        pkg.rve_set_phases(h, cfg.phase, params or cfg.params, cfg.ell if ell is None else ell)
+        pkg.rve_set_load_path(h, cfg.strain_ctrl, cfg.target)
+        return h
+
+    h = handle()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    Jv = pkg.rve_adjoint_forward(h, args.adj_every)
+    t1 = time.time()
+    gp, ge, gs, info = pkg.rve_adjoint_backward(h, 1.0, len(cfg.params), J, V)
+    t2 = time.time()
+    D = float(pkg.rve_homogenized_stress(h)[0])
+    pkg.rve_free(h)
+    names = ["sigma_y", "H", "eps_C", "eps_R"]
+    grads = {"matrix": dict(zip(names, gp[0].tolist())),
+             "particle": {"kappa_C": gp[1][2], "kappa_R": gp[1][3]},
+             "ell": ge.tolist(), "stiff_sum": float(gs.sum()), "stiff_absmax": float(np.abs(gs).max())}
+    fd = {}
+    hrel = 1e-6
+    for item in [x for x in args.adj_fd.split(",") if x]:
+        def J_of(sign):
+            params = [dict(p) for p in cfg.params]
+            ell = cfg.ell.copy()
+            if item.startswith("ell"):
+                j = int(item[3:])
+                ell[j] *= 1 + sign * hrel
+            else:
+                q, k = item.split(":")
+                params[int(q)][k] *= 1 + sign * hrel
+            hh = handle(params, ell)
+            for _ in range(cfg.target.shape[0]):
+                pkg.rve_step_increment(hh)
+            v = float(pkg.rve_homogenized_stress(hh)[0])
+            pkg.rve_free(hh)
+            return v
+        if item.startswith("ell"):
+            j = int(item[3:])
+            ref, scale = ge[j], float(cfg.ell[j].max())
+        else:
+            q, k = item.split(":")
+            ref, scale = gp[int(q)][names.index(k)], cfg.params[int(q)][k]
+        fdv = (J_of(1) - J_of(-1)) / (2 * hrel * scale)
+        fd[item] = {"adjoint": float(ref), "central_difference": fdv, "rel_err": abs(ref - fdv) / abs(fdv)}
+    return {"metric": "adjoint gradient of the final <sigma>_11, 96^3 two-variable RVE (FP64)",
+            "value": t2 - t0, "unit": "s (forward with checkpoints + reverse sweep)",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "grid": list(cfg.n), "spheres": 30,
+                       "radius_vox": round(cfg.meta["radius"], 3), "vf": round(cfg.meta["vf_voxel"], 4),
+                       "increments": cfg.target.shape[0], "checkpoint_every": args.adj_every,
+                       "tolerances": {"stag": opt.tol_stag, "newton": opt.tol_newton, "cg": opt.cg_rtol,
+                                      "pcg": opt.pcg_rtol}},
+           "J": Jv, "J_after_backward": D, "forward_s": t1 - t0, "backward_s": t2 - t1, "info": info,
+           "gradients": grads, "finite_differences": fd}
+
+
 def main():
     args = parse()
     rank, ws, dist = dist_init()
+    if args.workload == "adjoint" and args.impl == "ours":
+        if rank == 0:
+            print(json.dumps(run_adjoint(args)))
+        return
     if args.workload == "batch" and args.impl == "ours":
         out = run_batch(args, rank, ws, dist)
         if rank == 0:
