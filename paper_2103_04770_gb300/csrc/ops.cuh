@@ -168,6 +168,11 @@ k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, 
        const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   constexpr int PS = XPad<R, MCT>::v;
+  // row lengths: compile-time on the MCT path, so the index divisions fold
+  const int n1 = MCT > 0 ? 2 * MCT : g.n1;
+  const int M = MCT > 0 ? MCT : g.M;
+  const int P1 = MCT > 0 ? MCT + 1 : g.P1;
+  const int ps = MCT > 0 ? ((MCT + 1 + 15) / 16) * 16 : g.ps;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
@@ -176,27 +181,27 @@ k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, 
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
   pro.begin(ctl);
-  const int nvox = rows * g.n1;
+  const int nvox = rows * n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
-    const int r = e / g.n1, x = e - r * g.n1;
-    const long long v = (row0 + r) * g.n1 + x;
+    const int r = e / n1, x = e - r * n1;
+    const long long v = (row0 + r) * n1 + x;
     R val[NC];
     pro(v, val);
 #pragma unroll
-    for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * g.n1 + x) = val[c];
+    for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * n1 + x) = val[c];
   }
   __syncthreads();
   if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, -1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
-  const int nout = rows * NC * g.P1;
+  const int nout = rows * NC * P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
-    const int l = e / g.P1, k = e - l * g.P1;
+    const int l = e / P1, k = e - l * P1;
     const int r = l / NC, c = l - r * NC;
-    const C2<R> zk = cbuf[cpad<PS>(l * g.M + (k == g.M ? 0 : k))];
-    const C2<R> zm = cbuf[cpad<PS>(l * g.M + (k == 0 ? 0 : g.M - k))];
+    const C2<R> zk = cbuf[cpad<PS>(l * M + (k == M ? 0 : k))];
+    const C2<R> zm = cbuf[cpad<PS>(l * M + (k == 0 ? 0 : M - k))];
     const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
     const C2<R> Ok = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-    S[c * g.sstride + (row0 + r) * g.ps + k] = Ek + cmul(tws[k], Ok);
+    S[c * g.sstride + (row0 + r) * ps + k] = Ek + cmul(tws[k], Ok);
   }
 }
 
@@ -206,23 +211,44 @@ __host__ __device__ __forceinline__ size_t xstage_off(int n1, int rows, int nc) 
   return (((size_t)n1 * sizeof(C2<R>) + xbuf_c(rows, nc, n1 / 2) * sizeof(C2<R>)) + 15) & ~(size_t)15;
 }
 
-// Stage the spectrum rows of the CTA with cp.async (xs[c][r][ps]), then
-// split them into the half-length complex sequences (cbuf line r*NC + c).
-template <typename R, int NC, int PS>
+// Stage the spectrum rows of the CTA with cp.async (xs[c][r][ps], r below
+// XR rows per component slot), then split them into the half-length complex
+// sequences (cbuf line r*NC + c).  MCT > 0: compile-time row length MCT and
+// XR, so every index division folds into a multiply-shift.
+template <typename R, int NC, int PS, int MCT = 0>
 __device__ __forceinline__ void xinv_pre_staged(const Geo& g, const C2<R>* __restrict__ S, long long row0,
-                                                int rows, const C2<R>* tws, C2<R>* cbuf, C2<R>* xs) {
-  tile_load_async(xs, S + row0 * g.ps, NC, g.sstride, rows, (long long)g.ps, g.ps, g.P1);
+                                                int rows, int XRr, const C2<R>* tws, C2<R>* cbuf, C2<R>* xs) {
+  const int M = MCT > 0 ? MCT : g.M;
+  const int P1 = MCT > 0 ? MCT + 1 : g.P1;
+  const int ps = MCT > 0 ? ((MCT + 1 + 15) / 16) * 16 : g.ps;
+  const int XR = MCT > 0 ? XRows<MCT, NC>::v : XRr;
+  {
+    constexpr int PER = 16 / (int)sizeof(C2<R>);
+    const int cpr = (P1 + PER - 1) / PER;
+    const int total = NC * XR * cpr;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int l = e / cpr, ch = e - l * cpr;
+      const int c = l / XR, r = l - c * XR;
+      if (r >= rows) continue;
+      const int col = ch * PER;
+      C2<R>* d = xs + (size_t)(c * XR + r) * ps + col;
+      const C2<R>* sp = S + c * g.sstride + (row0 + r) * ps + col;
+      if (PER == 2 && col + 1 >= P1) cp_async8(d, sp);
+      else cp_async16(d, sp);
+    }
+    cp_async_wait_all();
+  }
   __syncthreads();
-  const int nin = rows * NC * g.M;
+  const int nin = rows * NC * M;
   for (int e = threadIdx.x; e < nin; e += kThreads) {
-    const int l = e / g.M, k = e - l * g.M;
+    const int l = e / M, k = e - l * M;
     const int r = l / NC, c = l - r * NC;
-    const C2<R>* row = xs + (c * rows + r) * g.ps;
-    const C2<R> xk = row[k], xm = row[g.M - k];
+    const C2<R>* row = xs + (size_t)(c * XR + r) * ps;
+    const C2<R> xk = row[k], xm = row[M - k];
     const C2<R> E = mk<R>(R(0.5) * (xk.x + xm.x), R(0.5) * (xk.y - xm.y));
     const C2<R> Dd = mk<R>(R(0.5) * (xk.x - xm.x), R(0.5) * (xk.y + xm.y));
     const C2<R> O = cmul(Dd, conj_(tws[k]));
-    cbuf[cpad<PS>(l * g.M + k)] = mk<R>(E.x - O.y, E.y + O.x);
+    cbuf[cpad<PS>(l * M + k)] = mk<R>(E.x - O.y, E.y + O.x);
   }
 }
 
@@ -238,6 +264,7 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
        EPI epi, double* __restrict__ part, int pstride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   constexpr int PS = XPad<R, MCT>::v;
+  const int n1 = MCT > 0 ? 2 * MCT : g.n1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
@@ -248,8 +275,8 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
   // rows of the epilogue's input field, fetched together with the spectrum
   R* pre = reinterpret_cast<R*>(xs + (size_t)nrows * NC * g.ps);
-  if constexpr (EPI::kPrefetch) epi.prefetch(pre, row0, rows, g.n1);
-  xinv_pre_staged<R, NC, PS>(g, S, row0, rows, tws, cbuf, xs);
+  if constexpr (EPI::kPrefetch) epi.prefetch(pre, row0, rows, n1);
+  xinv_pre_staged<R, NC, PS, MCT>(g, S, row0, rows, nrows, tws, cbuf, xs);
   __syncthreads();
   if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, +1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
@@ -258,14 +285,14 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
 #pragma unroll
   for (int s = 0; s < NSA; s++) acc[s] = 0.0;
   epi.begin(ctl);
-  const int nvox = rows * g.n1;
+  const int nvox = rows * n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
-    const int r = e / g.n1, x = e - r * g.n1;
-    const long long v = (row0 + r) * g.n1 + x;
+    const int r = e / n1, x = e - r * n1;
+    const long long v = (row0 + r) * n1 + x;
     R val[NC];
 #pragma unroll
-    for (int c = 0; c < NC; c++) val[c] = rpad<R, PS>(rbuf, (r * NC + c) * g.n1 + x) * scale;
-    if constexpr (EPI::kPrefetch) epi(v, val, acc, pre + (r * NC) * g.n1 + x, g.n1);
+    for (int c = 0; c < NC; c++) val[c] = rpad<R, PS>(rbuf, (r * NC + c) * n1 + x) * scale;
+    if constexpr (EPI::kPrefetch) epi(v, val, acc, pre + (r * NC) * n1 + x, n1);
     else epi(v, val, acc);
   }
   if (NS > 0) block_sum_store<NSA>(acc, part, pstride);
@@ -278,6 +305,10 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
        const uint8_t* __restrict__ phase, const R* __restrict__ ell2, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   constexpr int PS = XPad<R, MCT>::v;
+  const int n1 = MCT > 0 ? 2 * MCT : g.n1;
+  const int M = MCT > 0 ? MCT : g.M;
+  const int P1 = MCT > 0 ? MCT + 1 : g.P1;
+  const int ps = MCT > 0 ? ((MCT + 1 + 15) / 16) * 16 : g.ps;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   R* rbuf = reinterpret_cast<R*>(tws + g.n1);
@@ -286,30 +317,30 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
   const long long row0 = (long long)blockIdx.x * nrows;
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
-  xinv_pre_staged<R, NC, PS>(g, W, row0, rows, tws, cbuf, xs);
+  xinv_pre_staged<R, NC, PS, MCT>(g, W, row0, rows, nrows, tws, cbuf, xs);
   __syncthreads();
   if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, +1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
-  const int nvox = rows * g.n1;
+  const int nvox = rows * n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
-    const int r = e / g.n1, x = e - r * g.n1;
-    const long long v = (row0 + r) * g.n1 + x;
+    const int r = e / n1, x = e - r * n1;
+    const long long v = (row0 + r) * n1 + x;
     const R w = ell2[phase[v]] * scale;
 #pragma unroll
-    for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * g.n1 + x) *= w;
+    for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * n1 + x) *= w;
   }
   __syncthreads();
   if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, -1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
-  const int nout = rows * NC * g.P1;
+  const int nout = rows * NC * P1;
   for (int e = threadIdx.x; e < nout; e += kThreads) {
-    const int l = e / g.P1, k = e - l * g.P1;
+    const int l = e / P1, k = e - l * P1;
     const int r = l / NC, c = l - r * NC;
-    const C2<R> zk = cbuf[cpad<PS>(l * g.M + (k == g.M ? 0 : k))];
-    const C2<R> zm = cbuf[cpad<PS>(l * g.M + (k == 0 ? 0 : g.M - k))];
+    const C2<R> zk = cbuf[cpad<PS>(l * M + (k == M ? 0 : k))];
+    const C2<R> zm = cbuf[cpad<PS>(l * M + (k == 0 ? 0 : M - k))];
     const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
     const C2<R> Ok = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-    W[c * g.sstride + (row0 + r) * g.ps + k] = Ek + cmul(tws[k], Ok);
+    W[c * g.sstride + (row0 + r) * ps + k] = Ek + cmul(tws[k], Ok);
   }
 }
 
@@ -578,11 +609,13 @@ k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restri
   if constexpr (TXR > 0) {
     // forward: natural rows in, spectrum stored from the swap16 order;
     // inverse: spectrum loaded into the swap16 order, natural rows out
-    tile_load_async<R, false, (SIGN > 0)>(buf, base, 1, 0, 256, astride, TXR, cols);
+    // full-width tiles (rows are padded to a multiple of 16 entries, so the
+    // columns past P1 stay inside the row; their values are never used)
+    tile_load_async<R, false, (SIGN > 0)>(buf, base, 1, 0, 256, astride, TXR, TXR);
     __syncthreads();
     if constexpr (SIGN < 0) fft256_forward<R, TXR>(buf, tws);
     else fft256_inverse<R, TXR>(buf, tws);
-    tile_store<R, false, (SIGN < 0)>(buf, base, 1, 0, 256, astride, TXR, cols);
+    tile_store<R, false, (SIGN < 0)>(buf, base, 1, 0, 256, astride, TXR, TXR);
   } else {
     tile_load_async(buf, base, 1, 0, N, astride, tx, cols);
     __syncthreads();
@@ -680,7 +713,7 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   const int tile = N * tx;
   constexpr int RS = IL ? RegRs<R, NC>::v : 0;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  tile_load_async<R, IL>(buf, base, nc, g.sstride, N, astride, tx, cols, RS);
+  tile_load_async<R, IL>(buf, base, nc, g.sstride, N, astride, tx, IL ? TXR : cols, RS);
   __syncthreads();
   if constexpr (IL) {
     fft256_forward<R, NC * TXR, RS>(buf, tws);
@@ -731,7 +764,7 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   } else {
     for (int c = 0; c < nc; c++) fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
   }
-  tile_store<R, IL>(buf, base, nc, g.sstride, N, astride, tx, cols, RS);
+  tile_store<R, IL>(buf, base, nc, g.sstride, N, astride, tx, IL ? TXR : cols, RS);
 }
 
 template <typename R>
@@ -820,7 +853,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   } else {
     for (int j = 0; j < d; j++) fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
-  tile_store<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, cols, d * tx);
+  tile_store<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, IL ? TXR : cols, d * tx);
 }
 
 // Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
@@ -857,7 +890,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
       for (int k = 0; k < PER; k++) pv[k] = p[off + (threadIdx.x / TXR + k * RPT) * astride + col];
     }
   }
-  tile_load_async<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, cols, d * tx);
+  tile_load_async<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, IL ? TXR : cols, d * tx);
   __syncthreads();
   if constexpr (IL) {
     fft256_forward<R, D * TXR>(buf, tws);
