@@ -423,6 +423,23 @@ struct Alg {
                                             h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
   }
 
+  // b = -G*(sigma - Sigma_bar) swept in the working precision (mixed form,
+  // far from Newton convergence: FP32 rounding of the transform, about 1e-7
+  // of |sigma|, is then at most 1 % of the residual itself).
+  static void residual_lo(rve* h, const Tables<R>& t, const double* sbar_c, double rtol, int maxit) {
+    const Geo& g = h->g;
+    const double nc = g.nc;
+    C2<R>* S = (C2<R>*)h->S;
+    LAUNCHB(h, KC_X_FWD_FIELD, nc * (8.0 * VV(h) + VS(h) * CS),
+            Op::xfwd_field64(g, t, h->lc, h->st, h->sigma, g.nc, g.cmap, h->dscal + OFF_SIGMEAN, S));
+    gamma_sweep(h, t, 1, nullptr);
+    LAUNCHB(h, KC_X_INV_RESIDUAL, nc * (VS(h) * CS + VV(h) * RS),
+            Op::template xinv_residual<R>(g, t, h->lc, h->st, S, (R*)h->r, h->dscal + OFF_SIGMEAN, h->smask_d,
+                                          sbar_c, h->part));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
+                                            h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
+  }
+
   // FP32 Krylov solves stop when (r, r) has not fallen below a quarter of its
   // best value for this many iterations (attainable accuracy reached).
   static int stall_window() { return sizeof(R) == sizeof(float) ? 150 : 0; }
@@ -459,19 +476,32 @@ struct Alg {
   static int mech_solve(rve* h, const Tables<R>& t, const double* abar_use, const double* sbar_c,
                         int* newton_out, long long* cg_out) {
     const Geo& g = h->g;
-    double de_rel = -1.0;
+    double de_rel = -1.0, last_res = -1.0;
     int newton = 0;
+    // mixed form: the residual is swept in FP32 while it exceeds res_lo
+    // (relative), in FP64 below it and for every convergence decision
+    const double res_lo = std::max(100.0 * h->opt.tol_newton, 1e-4);
     for (;;) {
       return_map(h, abar_use);
-      residual(h, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
+      bool lo = sizeof(R) == sizeof(float) && (last_res < 0.0 || last_res > res_lo);
+      if (lo) residual_lo(h, t, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
+      else residual(h, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
       int s = sync_read(h);
       if (s) return s;
       double sm = 0.0;
       for (int c = 0; c < g.nc; c++) sm += h->hscal[OFF_SIGMEAN + g.cmap[c]] * h->hscal[OFF_SIGMEAN + g.cmap[c]];
       sm = std::sqrt(sm);
-      const double b2 = h->hctl->b2;
+      double b2 = h->hctl->b2;
       if (!(b2 == b2)) { h->fail_stage = 5; return RVE_ERR_NUMERIC; }
-      const double res_rel = std::sqrt(b2) / (std::sqrt((double)g.V) * std::max(sm, 1e-300));
+      double res_rel = std::sqrt(b2) / (std::sqrt((double)g.V) * std::max(sm, 1e-300));
+      if (lo && res_rel <= res_lo) {
+        residual(h, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
+        if ((s = sync_read(h))) return s;
+        b2 = h->hctl->b2;
+        if (!(b2 == b2)) { h->fail_stage = 5; return RVE_ERR_NUMERIC; }
+        res_rel = std::sqrt(b2) / (std::sqrt((double)g.V) * std::max(sm, 1e-300));
+      }
+      last_res = res_rel;
       if (h->verbose)
         std::fprintf(stderr, "[rve] newton %d res_rel %.3e de_rel %.3e |<sigma>| %.6e\n", newton, res_rel,
                      de_rel, sm);

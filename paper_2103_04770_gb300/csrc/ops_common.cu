@@ -14,11 +14,21 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
   __shared__ double vals[16];
   const bool is_max = mode == FIN_MAXS;
   for (int s = 0; s < nslots; s++) {
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kThreads) {
-      const double x = part[(long long)s * stride + b];
-      acc = is_max ? fmax(acc, x) : acc + x;
+    // four independent partial accumulators per thread (loads in flight
+    // together), combined in a fixed order: deterministic
+    const double* ps = part + (long long)s * stride;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = threadIdx.x;
+    for (; b + 3 * kThreads < nblocks; b += 4 * kThreads) {
+      const double x0 = ps[b], x1 = ps[b + kThreads], x2 = ps[b + 2 * kThreads], x3 = ps[b + 3 * kThreads];
+      if (is_max) {
+        a0 = fmax(a0, x0); a1 = fmax(a1, x1); a2 = fmax(a2, x2); a3 = fmax(a3, x3);
+      } else {
+        a0 += x0; a1 += x1; a2 += x2; a3 += x3;
+      }
     }
+    for (; b < nblocks; b += kThreads) a0 = is_max ? fmax(a0, ps[b]) : a0 + ps[b];
+    const double acc = is_max ? fmax(fmax(a0, a1), fmax(a2, a3)) : (a0 + a1) + (a2 + a3);
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int o = kThreads / 2; o > 0; o >>= 1) {
