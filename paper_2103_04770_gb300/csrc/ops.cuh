@@ -671,7 +671,7 @@ struct LastSym {
 
 template <typename R> __device__ __forceinline__ R inv_sqrt(R x);
 template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return rsqrtf(x); }
-template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return rsqrt(x); }
 
 // Gamma* at one mode of symbol a: the projection for k != 0, the
 // stress-control mask at the zero frequency (dc_mode 0), zero at the hidden
@@ -1152,10 +1152,13 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
     if (P.law == 1) {
       const double f = q - s23 * (P.sigma_y + P.H * epn);
       if (f > 0.0) {
+        // three FP64 divisions per plastic voxel (division is slow on the
+        // FP64 pipe): 1/q is shared by the flow direction and theta
         dl = f / (2.0 * mu + 2.0 * P.H / 3.0);
-        for (int c = 0; c < 6; c++) nh[c] = 2.0 * mu * dev[c] / q;
-        theta = 1.0 - 2.0 * mu * dl / q;
-        thetab = 1.0 / (1.0 + P.H / (3.0 * mu)) - (1.0 - theta);
+        const double iq = 1.0 / q;
+        for (int c = 0; c < 6; c++) nh[c] = 2.0 * mu * dev[c] * iq;
+        theta = 1.0 - 2.0 * mu * dl * iq;
+        thetab = (3.0 * mu) / (3.0 * mu + P.H) - (1.0 - theta);
       }
       if (P.var >= 0) {
         const double ab = abar[P.var * V + v];
