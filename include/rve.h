@@ -254,7 +254,8 @@ int rve_set_graphs(rve_t* h, int enable);
  * overwrite only the Krylov scratch vectors (CUDA events on the handle's
  * stream); a candidate replaces
  * the current choice when it is at least 2 % faster.  Axes with compile-time
- * schedules (256-point y / last axes, N1 = 256 rows) are left alone.  Allowed
+ * schedules (64-, 128- and 256-point y / last axes; N1 = 64, 96, 128 and
+ * 256 rows) are left alone.  Allowed
  * after rve_set_phases and before the first rve_step_increment (else
  * RVE_ERR_STATE); the state is not changed.  best_ms (nullable): time of
  * one matvec with the chosen schedule; tx (nullable): chosen tile width;

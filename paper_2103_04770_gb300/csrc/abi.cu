@@ -906,7 +906,8 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   for (int c = 1; c <= 6; c++) {
     const int e = (c * g.M <= 4 * kThreads) ? 4 : 16;
     lc.xe_c[c] = e;
-    lc.nrows_c[c] = std::max(1, std::min(32, (e * kThreads) / (c * g.M)));
+    lc.nrows_c[c] = (e == 4 && x1_ct_length(g.M)) ? x1_ct_rows(g.M, c)
+                                                  : std::max(1, std::min(32, (e * kThreads) / (c * g.M)));
   }
   lc.nrows_c[0] = 1;
   lc.xe_c[0] = 16;
@@ -1423,7 +1424,7 @@ int autotune_impl(rve* h, int reps, double* best_ms) {
   // plan of each axis whose transforms run on the runtime mixed-radix path
   for (int ax = 0; ax < g.d && !s; ax++) {
     const int N = h->plan[ax].N;
-    if (N <= 1 || (ax == 0 && N == 128) || (ax > 0 && N == 256)) continue;
+    if (N <= 1 || (ax == 0 && x1_ct_length(N)) || (ax > 0 && reg_axis(N))) continue;
     std::vector<FftPlan> cands;
     radix_orders(N, cands);
     FftPlan keep = h->plan[ax];

@@ -33,6 +33,23 @@ struct FftPlan {
 };
 
 // Per-phase constitutive constants (device copy of rve_phase_params).
+// Rows per CTA of the x1 passes.  Rows of a compile-time length (half
+// length M in {32, 48, 64, 128}) are grouped so that about kX1CtElems
+// complex points are transformed per CTA; other lengths stage at most
+// e = 4 (or 16 for long rows) points per thread.  Shared by the launch
+// configuration and the compile-time kernels.
+#ifndef RVK_X1_CT_ELEMS
+#define RVK_X1_CT_ELEMS 2048
+#endif
+constexpr int kX1CtElems = RVK_X1_CT_ELEMS;
+__host__ __device__ constexpr bool x1_ct_length(int M) { return M == 32 || M == 48 || M == 64 || M == 128; }
+__host__ __device__ constexpr int x1_ct_rows(int M, int c) {
+  return kX1CtElems / (M * c) < 1 ? 1 : (kX1CtElems / (M * c) > 32 ? 32 : kX1CtElems / (M * c));
+}
+
+// strided / last axes of these lengths run the compile-time register passes
+__host__ __device__ constexpr bool reg_axis(int N) { return N == 64 || N == 128 || N == 256; }
+
 struct PhaseDev {
   double K, mu, sigma_y, H;
   double eps_C, eps_R, D_max;

@@ -145,4 +145,88 @@ __device__ __forceinline__ void fft256_inverse(C2<R>* buf, const C2<R>* tw) {
   __syncthreads();
 }
 
+
+// ------------------------------------------------ other lengths N = R1 R2
+// The same two-pass scheme for N = R1 R2 (position p = a + R1 b):
+//   forward  pass A: for each a < R1, the R2-point DFT over b of x[a + R1 b],
+//                    output r times W_N^(a r) written to a + R1 r;
+//            pass B: for each r < R2, the R1-point DFT over a of the entries
+//                    a + R1 r, output k written to k + R1 r,
+// leaving X[r + R2 k] at position k + R1 r; the inverse runs pass B (twiddles
+// W_N^(-r a) after its DFT) then pass A and ends in natural order.  R1 = R2 =
+// 16 is the 256-point scheme above.
+template <int N> struct RegSplit;
+template <> struct RegSplit<256> { static constexpr int r1 = 16, r2 = 16; };
+template <> struct RegSplit<128> { static constexpr int r1 = 8, r2 = 16; };
+template <> struct RegSplit<64> { static constexpr int r1 = 8, r2 = 8; };
+
+// position of spectrum entry f after the forward transform
+template <int N>
+__host__ __device__ __forceinline__ int reg_pos(int f) {
+  return f / RegSplit<N>::r2 + RegSplit<N>::r1 * (f % RegSplit<N>::r2);
+}
+// frequency held at position p after the forward transform
+template <int N>
+__host__ __device__ __forceinline__ int reg_freq(int p) {
+  return p / RegSplit<N>::r1 + RegSplit<N>::r2 * (p % RegSplit<N>::r1);
+}
+
+template <typename R, int RAD, int SIGN>
+__device__ __forceinline__ void dft_reg(C2<R> (&v)[RAD]) {
+  if constexpr (RAD == 16) dft16<R, SIGN>(v);
+  else Dft<R, RAD, SIGN>::run(v);
+}
+
+// One pass over NL lines of N = R1 R2 points (element n of line l at
+// buf[n ES + l]): STRIDED takes, for task (l, a), a < R1, the R2 entries
+// a + R1 i; otherwise, for task (l, r), r < R2, the R1 entries i + R1 r.
+// TWID multiplies output i by tw[q i] (conjugated for SIGN > 0), q the
+// task's a or r; tw[m] = exp(-2 pi i m / N).
+template <typename R, int N, int NL, int ES, int SIGN, bool STRIDED, bool TWID>
+__device__ __forceinline__ void fftreg_pass(C2<R>* buf, const C2<R>* tw) {
+  constexpr int R1 = RegSplit<N>::r1, R2 = RegSplit<N>::r2;
+  constexpr int L = STRIDED ? R2 : R1;          // DFT length
+  constexpr int Q = STRIDED ? R1 : R2;          // tasks per line
+  constexpr int NT = NL * Q;
+#pragma unroll 1
+  for (int t = threadIdx.x; t < NT; t += kThreads) {
+    const int l = t % NL, q = t / NL;
+    C2<R>* p = buf + l + (STRIDED ? q : R1 * q) * ES;
+    constexpr int step = (STRIDED ? R1 : 1) * ES;
+    C2<R> v[L];
+#pragma unroll
+    for (int i = 0; i < L; i++) v[i] = p[i * step];
+    dft_reg<R, L, SIGN>(v);
+    if constexpr (TWID) {
+#pragma unroll
+      for (int i = 1; i < L; i++) {
+        C2<R> w = tw[q * i];
+        if (SIGN > 0) w.y = -w.y;
+        v[i] = cmul(v[i], w);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < L; i++) p[i * step] = v[i];
+  }
+}
+
+// Forward transform of NL lines, natural order in, reg_pos order out.  The
+// caller synchronises before the call; the call ends with a barrier.
+template <typename R, int N, int NL, int ES = NL>
+__device__ __forceinline__ void fftreg_forward(C2<R>* buf, const C2<R>* tw) {
+  fftreg_pass<R, N, NL, ES, -1, true, true>(buf, tw);
+  __syncthreads();
+  fftreg_pass<R, N, NL, ES, -1, false, false>(buf, tw);
+  __syncthreads();
+}
+
+// Inverse transform of NL lines, reg_pos order in, natural order out.
+template <typename R, int N, int NL, int ES = NL>
+__device__ __forceinline__ void fftreg_inverse(C2<R>* buf, const C2<R>* tw) {
+  fftreg_pass<R, N, NL, ES, 1, false, true>(buf, tw);
+  __syncthreads();
+  fftreg_pass<R, N, NL, ES, 1, true, false>(buf, tw);
+  __syncthreads();
+}
+
 }  // namespace rvk

@@ -126,7 +126,8 @@ extern "C" int rve_op_apply_gamma_noalloc(int dim, const int n[3], const double 
   for (int c = 1; c <= 6; c++) {
     const int e = (c * g.M <= 4 * kThreads) ? 4 : 16;
     lc.xe_c[c] = e;
-    lc.nrows_c[c] = std::max(1, std::min(32, (e * kThreads) / (c * g.M)));
+    lc.nrows_c[c] = (e == 4 && x1_ct_length(g.M)) ? x1_ct_rows(g.M, c)
+                                                  : std::max(1, std::min(32, (e * kThreads) / (c * g.M)));
   }
   lc.nrows_c[0] = 1;
   lc.xe_c[0] = 16;

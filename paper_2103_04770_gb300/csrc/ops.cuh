@@ -145,7 +145,7 @@ __host__ __device__ __forceinline__ size_t xbuf_c(int rows, int nc, int M) {
 // rows per CTA of the compile-time x1 kernels: the E = 4 row rule
 // min(32, 4 kThreads / (NC M)) for M = MCT
 template <int MCT, int NC> struct XRows {
-  static constexpr int v = MCT > 0 ? ((4 * kThreads) / (MCT * NC) < 32 ? (4 * kThreads) / (MCT * NC) : 32) : 0;
+  static constexpr int v = MCT > 0 ? x1_ct_rows(MCT, NC) : 0;
 };
 
 // real element ri of a padded complex buffer
@@ -511,21 +511,21 @@ __host__ __device__ __forceinline__ size_t tw_bytes(int N) {
 // interleaved) at n rs + c tx + col (rs >= ncomp tx: the stride of one
 // point's group of lines), where one batched transform of ncomp tx lines
 // covers every component.  With SW (256-point axes) global row n maps to
-// tile row swap16(n), the order of the register-pass spectrum.  Interleaved
+// tile row reg_pos(n), the order of the register-pass spectrum.  Interleaved
 // tiles are walked component-fastest so that a warp's shared-memory rows are
 // adjacent.
-template <bool IL, bool SW>
+template <bool IL, bool SW, int NAX = 256>
 __device__ __forceinline__ int tile_off(int row, int ncomp, int N, int tx, int rs, long long cstride,
                                         long long astride, long long& goff) {
   int c, n;
   if (IL) { n = row / ncomp; c = row - n * ncomp; }
   else { c = row / N; n = row - c * N; }
   goff = c * cstride + n * astride;
-  const int m = SW ? swap16(n) : n;
+  const int m = SW ? reg_pos<NAX>(n) : n;
   return IL ? m * rs + c * tx : (c * N + m) * tx;
 }
 
-template <typename R, bool IL = false, bool SW = false>
+template <typename R, bool IL = false, bool SW = false, int NAX = 256>
 __device__ __forceinline__ void tile_load_async(C2<R>* buf, const C2<R>* src, int ncomp, long long cstride,
                                                 int N, long long astride, int tx, int cols, int rs = 0) {
   constexpr int PER = 16 / (int)sizeof(C2<R>);
@@ -535,7 +535,7 @@ __device__ __forceinline__ void tile_load_async(C2<R>* buf, const C2<R>* src, in
     const int row = e / cpr, ch = e - row * cpr;
     const int col = ch * PER;
     long long goff;
-    C2<R>* d = buf + tile_off<IL, SW>(row, ncomp, N, tx, rs, cstride, astride, goff) + col;
+    C2<R>* d = buf + tile_off<IL, SW, NAX>(row, ncomp, N, tx, rs, cstride, astride, goff) + col;
     const C2<R>* sp = src + goff + col;
     if (PER == 2 && col + 1 >= cols) cp_async8(d, sp);
     else cp_async16(d, sp);
@@ -543,7 +543,7 @@ __device__ __forceinline__ void tile_load_async(C2<R>* buf, const C2<R>* src, in
   cp_async_wait_all();
 }
 
-template <typename R, bool IL = false, bool SW = false>
+template <typename R, bool IL = false, bool SW = false, int NAX = 256>
 __device__ __forceinline__ void tile_store(const C2<R>* buf, C2<R>* dst, int ncomp, long long cstride, int N,
                                            long long astride, int tx, int cols, int rs = 0) {
   constexpr int PER = 16 / (int)sizeof(C2<R>);
@@ -553,7 +553,7 @@ __device__ __forceinline__ void tile_store(const C2<R>* buf, C2<R>* dst, int nco
     const int row = e / cpr, ch = e - row * cpr;
     const int col = ch * PER;
     long long goff;
-    const C2<R>* sp = buf + tile_off<IL, SW>(row, ncomp, N, tx, rs, cstride, astride, goff) + col;
+    const C2<R>* sp = buf + tile_off<IL, SW, NAX>(row, ncomp, N, tx, rs, cstride, astride, goff) + col;
     C2<R>* d = dst + goff + col;
     if (PER == 2 && col + 1 >= cols) {
       d[0] = sp[0];
@@ -590,15 +590,16 @@ template <typename R, int NCOMP> struct RegRs {
   static constexpr int v = NCOMP * RegTx<R, NCOMP>::v + (NCOMP >= 6 ? 32 / (int)sizeof(C2<R>) : 0);
 };
 
-// TXR > 0: 256-point axis through the register passes, TXR columns per CTA.
-template <typename R, int SIGN, int TXR = 0>
+// TXR > 0: NAX-point axis (64, 128 or 256) through the register passes, TXR
+// columns per CTA.
+template <typename R, int SIGN, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 2)
 k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
                 long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = TXR ? 256 : pl.N;
+  const int N = TXR ? NAX : pl.N;
   if (TXR) tx = TXR;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
@@ -607,15 +608,15 @@ k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restri
   C2<R>* base = S + blockIdx.z * g.sstride + blockIdx.y * ostride + q0;
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
   if constexpr (TXR > 0) {
-    // forward: natural rows in, spectrum stored from the swap16 order;
-    // inverse: spectrum loaded into the swap16 order, natural rows out
+    // forward: natural rows in, spectrum stored from the reg_pos order;
+    // inverse: spectrum loaded into the reg_pos order, natural rows out
     // full-width tiles (rows are padded to a multiple of 16 entries, so the
     // columns past P1 stay inside the row; their values are never used)
-    tile_load_async<R, false, (SIGN > 0)>(buf, base, 1, 0, 256, astride, TXR, TXR);
+    tile_load_async<R, false, (SIGN > 0), NAX>(buf, base, 1, 0, NAX, astride, TXR, TXR);
     __syncthreads();
-    if constexpr (SIGN < 0) fft256_forward<R, TXR>(buf, tws);
-    else fft256_inverse<R, TXR>(buf, tws);
-    tile_store<R, false, (SIGN < 0)>(buf, base, 1, 0, 256, astride, TXR, TXR);
+    if constexpr (SIGN < 0) fftreg_forward<R, NAX, TXR>(buf, tws);
+    else fftreg_inverse<R, NAX, TXR>(buf, tws);
+    tile_store<R, false, (SIGN < 0), NAX>(buf, base, 1, 0, NAX, astride, TXR, TXR);
   } else {
     tile_load_async(buf, base, 1, 0, N, astride, tx, cols);
     __syncthreads();
@@ -690,10 +691,11 @@ __device__ __forceinline__ void gamma_apply(const R a[3], bool dc, const Mask6& 
   }
 }
 
-// TXR > 0: 256-point last axis through the register passes, TXR columns per
-// CTA, the NC components interleaved in the tile and transformed as one
-// batch of NC TXR lines; the projection runs on the swap16 spectrum order.
-template <typename R, int NC, int TXR = 0>
+// TXR > 0: NAX-point last axis (64, 128, 256) through the register passes,
+// TXR columns per CTA, the NC components interleaved in the tile and
+// transformed as one
+// batch of NC TXR lines; the projection runs on the reg_pos spectrum order.
+template <typename R, int NC, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 2)
 k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
         long long astride, long long ostride, Mask6 mask, int dc_mode,
@@ -703,7 +705,7 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   constexpr int nc = NC;
   constexpr bool IL = TXR > 0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = TXR ? 256 : pl.N;
+  const int N = TXR ? NAX : pl.N;
   if (TXR) tx = TXR;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
@@ -716,23 +718,23 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   tile_load_async<R, IL>(buf, base, nc, g.sstride, N, astride, tx, IL ? TXR : cols, RS);
   __syncthreads();
   if constexpr (IL) {
-    fft256_forward<R, NC * TXR, RS>(buf, tws);
+    fftreg_forward<R, NAX, NC * TXR, RS>(buf, tws);
   } else {
     for (int c = 0; c < nc; c++) fft_lines<R, E, -1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
   }
   if constexpr (IL) {
-    // the register passes leave frequency swap16(n) at tile row n
+    // the register passes leave frequency reg_freq(n) at tile row n
     constexpr int RPT = kThreads / TXR;
     const int col = threadIdx.x % TXR;
     if (col < cols) {
       LastSym<R> sy;
       sy.init(g, t, q0 + col);
 #pragma unroll 2
-      for (int n = threadIdx.x / TXR; n < 256; n += RPT) {
+      for (int n = threadIdx.x / TXR; n < NAX; n += RPT) {
         R a[3];
         C2<R> ph;
         bool dc;
-        sy.at(g, t, swap16(n), a, ph, dc);
+        sy.at(g, t, reg_freq<NAX>(n), a, ph, dc);
         C2<R> tv[NC];
 #pragma unroll
         for (int c = 0; c < nc; c++) tv[c] = buf[n * RS + c * TXR + col];
@@ -760,7 +762,7 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   }
   __syncthreads();
   if constexpr (IL) {
-    fft256_inverse<R, NC * TXR, RS>(buf, tws);
+    fftreg_inverse<R, NAX, NC * TXR, RS>(buf, tws);
   } else {
     for (int c = 0; c < nc; c++) fft_lines<R, E, +1>(buf + c * tile, pl, cols, tx, 1, false, tws, 1);
   }
@@ -774,7 +776,7 @@ __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
 
 // Helmholtz: p <- M r + beta p (M = 1/(1 + <l^2>|k|^2)); W_j = k_j p; inverse
 // transform along the last axis.
-template <typename R, int D, int TXR = 0>
+template <typename R, int D, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 2)
 k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
          C2<R>* __restrict__ p, const C2<R>* __restrict__ r, int tx, long long astride,
@@ -782,7 +784,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = TXR ? 256 : pl.N;
+  const int N = TXR ? NAX : pl.N;
   if (TXR) tx = TXR;
   constexpr int d = D;
   constexpr bool IL = TXR > 0;
@@ -796,14 +798,14 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   const R beta = ctl ? (R)ctl->beta : R(0);
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
   if constexpr (IL) {
-    // one column per thread; frequency n goes to tile row swap16(n)
+    // one column per thread; frequency n goes to tile row reg_pos(n)
     constexpr int RPT = kThreads / TXR;
     const int col = threadIdx.x % TXR;
     if (col < cols) {
       LastSym<R> sy;
       sy.init(g, t, q0 + col);
 #pragma unroll 4
-      for (int n = threadIdx.x / TXR; n < 256; n += RPT) {
+      for (int n = threadIdx.x / TXR; n < NAX; n += RPT) {
         R a[3];
         C2<R> ph;
         bool dc;
@@ -819,7 +821,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
           p[idx] = pn;
         }
         const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
-        const int e0 = swap16(n) * (d * TXR) + col;
+        const int e0 = reg_pos<NAX>(n) * (d * TXR) + col;
 #pragma unroll
         for (int j = 0; j < d; j++) buf[e0 + j * TXR] = cscale(ipp, a[j]);
       }
@@ -849,7 +851,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   }
   __syncthreads();
   if constexpr (IL) {
-    fft256_inverse<R, D * TXR>(buf, tws);
+    fftreg_inverse<R, NAX, D * TXR>(buf, tws);
   } else {
     for (int j = 0; j < d; j++) fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
@@ -858,7 +860,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
 
 // Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
 // partial Hermitian-weighted (p, y).
-template <typename R, int D, int TXR = 0>
+template <typename R, int D, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 2)
 k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C2<R>* __restrict__ W,
            const C2<R>* __restrict__ p, C2<R>* __restrict__ y, int tx, long long astride,
@@ -867,7 +869,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = TXR ? 256 : pl.N;
+  const int N = TXR ? NAX : pl.N;
   if (TXR) tx = TXR;
   constexpr int d = D;
   constexpr bool IL = TXR > 0;
@@ -881,7 +883,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   // register path: this thread's entries of p, fetched while the tile is
   // transformed
   constexpr int RPT = TXR ? kThreads / TXR : 1;
-  constexpr int PER = TXR ? 256 / RPT : 1;
+  constexpr int PER = TXR ? NAX / RPT : 1;
   C2<R> pv[PER];
   if constexpr (IL) {
     const int col = threadIdx.x % TXR;
@@ -893,7 +895,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   tile_load_async<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, IL ? TXR : cols, d * tx);
   __syncthreads();
   if constexpr (IL) {
-    fft256_forward<R, D * TXR>(buf, tws);
+    fftreg_forward<R, NAX, D * TXR>(buf, tws);
   } else {
     for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
@@ -911,7 +913,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
         C2<R> ph;
         bool dc;
         sy.at(g, t, n, a, ph, dc);
-        const int e0 = swap16(n) * (d * TXR) + col;
+        const int e0 = reg_pos<NAX>(n) * (d * TXR) + col;
         C2<R> s = mk<R>(0, 0);
 #pragma unroll
         for (int j = 0; j < d; j++) s = s + cscale(buf[e0 + j * TXR], a[j]);
@@ -1270,7 +1272,19 @@ static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrow
                                   + (STAGE == 2 ? (size_t)nr * NCC * g.n1 * sizeof(R) : 0)              \
                             : xsmem<R>(g, nr, NCC);                                                     \
     if (lc.xe_c[NCC] == 4 && g.M == 128 && nr == XRows<128, NCC>::v) {                                  \
-      auto k = KCT;                                                                                     \
+      auto k = KCT(128);                                                                                \
+      set_smem(k, sm);                                                                                  \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
+    } else if (lc.xe_c[NCC] == 4 && g.M == 64 && nr == XRows<64, NCC>::v) {                             \
+      auto k = KCT(64);                                                                                 \
+      set_smem(k, sm);                                                                                  \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
+    } else if (lc.xe_c[NCC] == 4 && g.M == 48 && nr == XRows<48, NCC>::v) {                             \
+      auto k = KCT(48);                                                                                 \
+      set_smem(k, sm);                                                                                  \
+      k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
+    } else if (lc.xe_c[NCC] == 4 && g.M == 32 && nr == XRows<32, NCC>::v) {                             \
+      auto k = KCT(32);                                                                                 \
       set_smem(k, sm);                                                                                  \
       k<<<xgrid(g, nr), kThreads, sm, st>>>(__VA_ARGS__);                                               \
     } else if (lc.xe_c[NCC] == 4) {                                                                     \
@@ -1285,10 +1299,11 @@ static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrow
   } while (0)
 
 // tile width of the strided / last-axis kernels with ncomp components per
-// tile: the register-pass width on a 256-point axis, else the runtime width
+// tile: the register-pass width on a 64/128/256-point axis, else the runtime
+// width
 template <typename R>
 static int axis_tx(const LaunchCfg& lc, int N, int ncomp) {
-  if (N != 256) return lc.tx;
+  if (!reg_axis(N)) return lc.tx;
   switch (ncomp) {
     case 1: return RegTx<R, 1>::v;
     case 2: return RegTx<R, 2>::v;
@@ -1303,9 +1318,11 @@ static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
   ProTangent<R, NC> pro;
   pro.p = p; pro.r = r; pro.desc = desc; pro.V = g.V;
   pro.update = ctl != nullptr; pro.beta = R(0); pro.first = true;
-  XLAUNCH((k_xfwd<R, NC, 4, ProTangent<R, NC>, 128>), (k_xfwd<R, NC, 4, ProTangent<R, NC>>),
+#define KCT_(M) (k_xfwd<R, NC, 4, ProTangent<R, NC>, M>)
+  XLAUNCH(KCT_, (k_xfwd<R, NC, 4, ProTangent<R, NC>>),
           (k_xfwd<R, NC, 16, ProTangent<R, NC>>), NC, false,
           g, t.plan_x, t.tw[0], S, nr, pro, ctl);
+#undef KCT_
 }
 
 template <typename R>
@@ -1321,9 +1338,11 @@ static void xfwd_field64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
   ProField64<R, NC> pro;
   pro.f = f; pro.mean = mean_dev; pro.V = g.V;
   for (int c = 0; c < NC; c++) pro.map[c] = fmap[c];
-  XLAUNCH((k_xfwd<R, NC, 4, ProField64<R, NC>, 128>), (k_xfwd<R, NC, 4, ProField64<R, NC>>),
+#define KCT_(M) (k_xfwd<R, NC, 4, ProField64<R, NC>, M>)
+  XLAUNCH(KCT_, (k_xfwd<R, NC, 4, ProField64<R, NC>>),
           (k_xfwd<R, NC, 16, ProField64<R, NC>>), NC, false,
           g, t.plan_x, t.tw[0], S, nr, pro, nullptr);
+#undef KCT_
 }
 
 template <typename R>
@@ -1339,9 +1358,11 @@ static void xinv_matvec_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
                            const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl) {
   EpiMatvec<R, NC> epi;
   epi.Ap = Ap; epi.p = p; epi.V = g.V;
-  XLAUNCH((k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1, 128>), (k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1>),
+#define KCT_(M) (k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1, M>)
+  XLAUNCH(KCT_, (k_xinv<R, NC, 4, EpiMatvec<R, NC>, 1>),
           (k_xinv<R, NC, 16, EpiMatvec<R, NC>, 1>), NC, 2,
           g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, ctl);
+#undef KCT_
 }
 
 template <typename R>
@@ -1363,8 +1384,10 @@ static void xinv_residual_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& 
     epi.map[c] = g.cmap[c];
     epi.dc[c] = 0.0;
   }
-  XLAUNCH((k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1, 128>), (k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1>),
+#define KCT_(M) (k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1, M>)
+  XLAUNCH(KCT_, (k_xinv<R, NC, 4, EpiResidual<R, RO, NC>, 1>),
           (k_xinv<R, NC, 16, EpiResidual<R, RO, NC>, 1>), NC, true, g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, nullptr);
+#undef KCT_
 }
 
 template <typename R>
@@ -1381,9 +1404,11 @@ static void xinv_store64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
                             const C2<R>* S, double* out) {
   EpiStore64<R, NC> epi;
   epi.out = out; epi.V = g.V;
-  XLAUNCH((k_xinv<R, NC, 4, EpiStore64<R, NC>, 0, 128>), (k_xinv<R, NC, 4, EpiStore64<R, NC>, 0>),
+#define KCT_(M) (k_xinv<R, NC, 4, EpiStore64<R, NC>, 0, M>)
+  XLAUNCH(KCT_, (k_xinv<R, NC, 4, EpiStore64<R, NC>, 0>),
           (k_xinv<R, NC, 16, EpiStore64<R, NC>, 0>), NC, true,
           g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, nullptr, 0, nullptr);
+#undef KCT_
 }
 
 template <typename R>
@@ -1397,12 +1422,16 @@ void Ops<R>::xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc,
 template <typename R>
 void Ops<R>::xmid_ell(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* W,
                       const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl) {
+#define KCT3_(M) (k_xmid<R, 3, 4, M>)
+#define KCT2_(M) (k_xmid<R, 2, 4, M>)
   if (g.d == 3)
-    XLAUNCH((k_xmid<R, 3, 4, 128>), (k_xmid<R, 3, 4>), (k_xmid<R, 3, 16>), 3, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
+    XLAUNCH(KCT3_, (k_xmid<R, 3, 4>), (k_xmid<R, 3, 16>), 3, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
             ell2_tab, ctl);
   else
-    XLAUNCH((k_xmid<R, 2, 4, 128>), (k_xmid<R, 2, 4>), (k_xmid<R, 2, 16>), 2, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
+    XLAUNCH(KCT2_, (k_xmid<R, 2, 4>), (k_xmid<R, 2, 16>), 2, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
             ell2_tab, ctl);
+#undef KCT3_
+#undef KCT2_
 }
 
 template <typename R>
@@ -1414,13 +1443,17 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? g.n3 : g.n2, ncomp);
   constexpr int TXR = RegTx<R, 1>::v;
-  const bool reg = si.N == 256;
+  auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
+    return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
+  };
   if (sign < 0) {
-    auto k = reg ? k_strided_plain<R, -1, TXR> : k_strided_plain<R, -1>;
+    auto k = pick(k_strided_plain<R, -1, TXR, 256>, k_strided_plain<R, -1, TXR, 128>,
+                  k_strided_plain<R, -1, TXR, 64>, k_strided_plain<R, -1>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
   } else {
-    auto k = reg ? k_strided_plain<R, 1, TXR> : k_strided_plain<R, 1>;
+    auto k = pick(k_strided_plain<R, 1, TXR, 256>, k_strided_plain<R, 1, TXR, 128>,
+                  k_strided_plain<R, 1, TXR, 64>, k_strided_plain<R, 1>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
   }
@@ -1433,18 +1466,23 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
   const int tx = axis_tx<R>(lc, si.N, g.nc);
-  const bool reg = si.N == 256;
+  const bool reg = reg_axis(si.N);
   const int rs = !reg ? g.nc * tx : g.nc == 6 ? RegRs<R, 6>::v : RegRs<R, 3>::v;
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * rs;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   Mask6 m;
   for (int c = 0; c < 6; c++) m.m[c] = c < g.nc ? stress_mask[c] : 0.f;
+  auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
+    return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
+  };
   if (g.nc == 6) {
-    auto k = reg ? k_gamma<R, 6, RegTx<R, 6>::v> : k_gamma<R, 6>;
+    constexpr int TX6 = RegTx<R, 6>::v;
+    auto k = pick(k_gamma<R, 6, TX6, 256>, k_gamma<R, 6, TX6, 128>, k_gamma<R, 6, TX6, 64>, k_gamma<R, 6>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
   } else {
-    auto k = reg ? k_gamma<R, 3, RegTx<R, 3>::v> : k_gamma<R, 3>;
+    constexpr int TX3 = RegTx<R, 3>::v;
+    auto k = pick(k_gamma<R, 3, TX3, 256>, k_gamma<R, 3, TX3, 128>, k_gamma<R, 3, TX3, 64>, k_gamma<R, 3>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], S, tx, si.astride, si.ostride, m, dc_mode, ctl);
   }
@@ -1459,14 +1497,18 @@ void Ops<R>::helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
   const int tx = axis_tx<R>(lc, si.N, g.d);
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  const bool reg = si.N == 256;
+  auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
+    return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
+  };
   if (g.d == 3) {
-    auto k = reg ? k_expand<R, 3, RegTx<R, 3>::v> : k_expand<R, 3>;
+    constexpr int T = RegTx<R, 3>::v;
+    auto k = pick(k_expand<R, 3, T, 256>, k_expand<R, 3, T, 128>, k_expand<R, 3, T, 64>, k_expand<R, 3>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
                                   raw);
   } else {
-    auto k = reg ? k_expand<R, 2, RegTx<R, 2>::v> : k_expand<R, 2>;
+    constexpr int T = RegTx<R, 2>::v;
+    auto k = pick(k_expand<R, 2, T, 256>, k_expand<R, 2, T, 128>, k_expand<R, 2, T, 64>, k_expand<R, 2>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
                                   raw);
@@ -1488,14 +1530,18 @@ void Ops<R>::helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const int tx = axis_tx<R>(lc, si.N, g.d);
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
-  const bool reg = si.N == 256;
+  auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
+    return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
+  };
   if (g.d == 3) {
-    auto k = reg ? k_contract<R, 3, RegTx<R, 3>::v> : k_contract<R, 3>;
+    constexpr int T = RegTx<R, 3>::v;
+    auto k = pick(k_contract<R, 3, T, 256>, k_contract<R, 3, T, 128>, k_contract<R, 3, T, 64>, k_contract<R, 3>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
                                   lc.max_blocks, ctl);
   } else {
-    auto k = reg ? k_contract<R, 2, RegTx<R, 2>::v> : k_contract<R, 2>;
+    constexpr int T = RegTx<R, 2>::v;
+    auto k = pick(k_contract<R, 2, T, 256>, k_contract<R, 2, T, 128>, k_contract<R, 2, T, 64>, k_contract<R, 2>);
     set_smem(k, sm);
     k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
                                   lc.max_blocks, ctl);

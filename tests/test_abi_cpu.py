@@ -88,3 +88,21 @@ def test_create_without_device_reports_status(pkg):
     with pytest.raises(pkg.RVEError) as ei:
         pkg.rve_create(2, (16, 16), (16.0, 16.0), pkg.RVE_FP64, 1)
     assert ei.value.status in (pkg.RVE_ERR_CUDA, pkg.RVE_ERR_OOM)
+
+
+def test_batch_adjoint_and_field_calls_reject_bad_arguments(pkg):
+    """The batch, autotuning, graph, stiffness-field and adjoint entry
+    points validate their arguments before any device work."""
+    lib = pkg.lib()
+    b = ctypes.c_void_p()
+    assert lib.rve_batch_create(ctypes.byref(b), 0, None, 0) == pkg.RVE_ERR_ARG
+    assert lib.rve_batch_create(None, 1, None, 0) == pkg.RVE_ERR_ARG
+    assert lib.rve_batch_step(None, None) == pkg.RVE_ERR_ARG
+    assert lib.rve_batch_size(None) == 0
+    lib.rve_batch_free(None)
+    assert lib.rve_set_graphs(None, 1) == pkg.RVE_ERR_ARG
+    assert lib.rve_autotune(None, 1, None, None, None) == pkg.RVE_ERR_ARG
+    assert lib.rve_set_stiffness_field(None, None) == pkg.RVE_ERR_ARG
+    J = ctypes.c_double()
+    assert lib.rve_adjoint_forward(None, 5, ctypes.byref(J)) == pkg.RVE_ERR_ARG
+    assert lib.rve_adjoint_backward(None, 1.0, None, None, None, None) == pkg.RVE_ERR_ARG

@@ -170,7 +170,9 @@ GAMMA_GRIDS = [(32, 30), (40, 16), (2, 2), (6, 5), (16, 12, 10), (12, 15, 8), (8
                # several q1 tiles per line and two-stage radix-8 axes
                (96, 20), (128, 64), (80, 12, 10), (64, 64, 16), (64, 24, 64),
                # compile-time FFT paths: N1 = 256 rows, 256-point y and last axes
-               (256, 256), (256, 8, 8), (16, 256, 8), (16, 8, 256), (40, 6, 256)]
+               (256, 256), (256, 8, 8), (16, 256, 8), (16, 8, 256), (40, 6, 256),
+               # register passes on 64- and 128-point axes; N1 = 96 and 64 compile-time rows
+               (16, 64, 128), (12, 128, 64), (24, 128), (20, 64), (96, 6, 8), (64, 10, 6)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -196,7 +198,7 @@ def test_apply_gamma(n, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [(24, 20), (40, 15), (8, 6, 10), (12, 15, 8), (96, 20), (64, 16, 24),
-                               (256, 8, 8), (16, 8, 256)])
+                               (256, 8, 8), (16, 8, 256), (16, 64, 128), (128, 8, 10)])
 def test_matvec_and_cg(n, prec):
     g = O.Grid(n)
     d = g.d
@@ -248,7 +250,8 @@ def test_matvec_and_cg(n, prec):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [(32, 30), (40, 16), (16, 12, 10), (12, 15, 8), (6, 5),
                                # compile-time paths: 256-point rows and last axis
-                               (256, 24), (24, 256), (256, 8, 16), (16, 8, 256)])
+                               (256, 24), (24, 256), (256, 8, 16), (16, 8, 256),
+                               (16, 8, 128), (24, 64), (12, 128, 8), (96, 8, 6)])
 def test_helmholtz(n, prec):
     g = O.Grid(n)
     rng = np.random.default_rng(6)
