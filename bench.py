@@ -80,6 +80,8 @@ def workload_config(cfg, precision):
 
 # ------------------------------------------------------------------ ranks
 def dist_init():
+    """One process per GPU (replicas: a single RVE does not shard).  NCCL on
+    GPUs; gloo when the host has none (the CPU tests of this path)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, None
@@ -87,25 +89,41 @@ def dist_init():
     import torch.distributed as dist
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist.init_process_group("gloo")
     return rank, ws, dist
+
+
+def _on_gpu(dist):
+    return dist is not None and dist.get_backend() == "nccl"
 
 
 def barrier(dist):
     if dist is not None:
         import torch
         dist.barrier()
-        torch.cuda.synchronize()
+        if _on_gpu(dist):
+            torch.cuda.synchronize()
 
 
 def allreduce(dist, x, op="max"):
+    """max or sum of a per-rank scalar over all ranks (identity on one rank)"""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+    t = torch.tensor([float(x)], device="cuda" if _on_gpu(dist) else "cpu", dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def aggregate(dist, ms, work):
+    """Whole-job rate of independent replicas: the ranks' work summed over
+    the slowest rank's time.  Returns (rate per second, max ms)."""
+    ms_max = allreduce(dist, ms, "max")
+    return allreduce(dist, work, "sum") / (ms_max * 1e-3), ms_max
 
 
 # ------------------------------------------------------------------ clocks
@@ -193,8 +211,7 @@ def run_ours(args, rank, ws, dist):
     prof = pkg.rve_profile_read(r.h)
     pkg.rve_profile(r.h, False)
     vi = sum(i["voxel_iterations"] for i in infos)
-    ms_max = allreduce(dist, ms, "max")
-    vi_sum = allreduce(dist, vi, "sum")
+    rate, ms_max = aggregate(dist, ms, vi)
     r.close()
 
     # -------- roofline of the dominant kernel class (live CUDA events)
@@ -217,7 +234,7 @@ def run_ours(args, rank, ws, dist):
                             for k, v in prof.items() if v[1] > 0}}
     gpu_launches = int(sum(v[1] for v in prof.values()))
 
-    out = {"metric": METRIC, "value": vi_sum / (ms_max * 1e-3), "unit": UNIT, "n_gpus": ws,
+    out = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if prec == pkg.RVE_MIXED else "f64", "data": "synthetic",
@@ -517,6 +534,8 @@ def main():
         out, _ = run_reference(args, rank, ws, dist)
         if rank == 0:
             print(json.dumps(out))
+        if dist is not None:
+            dist.destroy_process_group()
         return
     out, cfg = run_ours(args, rank, ws, dist)
     if rank == 0:
