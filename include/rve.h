@@ -234,6 +234,29 @@ int rve_op_helmholtz_apply(rve_t* h, int j, const double* a, double* out);
 int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, double rtol,
                            int maxit, int* iters);
 
+/* ------------------------------------------------ checkpoint / resume
+ * The converged state after the last increment (strain, plastic strain,
+ * local history variable, non-local variables and the homogenised values)
+ * as a self-describing byte image, so a long load path can be saved and
+ * resumed (also on another handle of the same grid, form and variable
+ * count; the phases, options and load path are not part of the image and
+ * must be set on the target handle).  FP64 in both forms. */
+
+/* Bytes of the image of this handle (header + (nc + 7 + J) V doubles). */
+long long rve_state_bytes(const rve_t* h);
+
+/* Write the image into the caller's host buffer `buf` of `bytes` bytes.
+ * Errors: RVE_ERR_ARG (NULL, buffer too small), RVE_ERR_STATE (phases not
+ * set), RVE_ERR_CUDA. */
+int rve_save_state(const rve_t* h, void* buf, long long bytes);
+
+/* Restore an image written by rve_save_state: the next rve_step_increment
+ * solves increment (saved count + 1) of the handle's load path.  The image's
+ * grid, form and variable count must match the handle.
+ * Errors: RVE_ERR_ARG (NULL, size or header mismatch), RVE_ERR_STATE
+ * (phases not set), RVE_ERR_CUDA. */
+int rve_load_state(rve_t* h, const void* buf, long long bytes);
+
 /* ------------------------------------------------ graphs, autotuning, batches
  * The paper solves one RVE at a time; these calls serve many RVEs of
  * different grids advanced together on one GPU. */

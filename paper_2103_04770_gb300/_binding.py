@@ -100,6 +100,9 @@ _SIGNATURES = {
     "rve_op_helmholtz_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(_I)]),
     "rve_op_apply_gamma_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D),
                                         ctypes.POINTER(ctypes.c_uint8), _P, _P, _P]),
+    "rve_state_bytes": (ctypes.c_longlong, [_P]),
+    "rve_save_state": (_I, [_P, _P, ctypes.c_longlong]),
+    "rve_load_state": (_I, [_P, _P, ctypes.c_longlong]),
     "rve_set_stiffness_field": (_I, [_P, _P]),
     "rve_adjoint_forward": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "rve_adjoint_backward": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(AdjointInfo)]),
@@ -304,6 +307,24 @@ def rve_op_apply_gamma_noalloc(dim, n, L, strain_ctrl, tau, out, stream=None):
     c = (ctypes.c_uint8 * 6)(*[int(x) for x in strain_ctrl])
     _check(lib().rve_op_apply_gamma_noalloc(int(dim), n3, L3, c, _ptr(tau), _ptr(out),
                                             _stream_handle(stream)), "rve_op_apply_gamma_noalloc")
+
+
+# ---------------------------------------------------- checkpoint / resume
+def rve_state_bytes(h):
+    return int(lib().rve_state_bytes(h))
+
+
+def rve_save_state(h):
+    """The converged state as bytes (see rve_save_state in rve.h)."""
+    n = lib().rve_state_bytes(h)
+    buf = ctypes.create_string_buffer(int(n))
+    _check(lib().rve_save_state(h, ctypes.cast(buf, ctypes.c_void_p), n), "rve_save_state")
+    return buf.raw
+
+
+def rve_load_state(h, data):
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(lib().rve_load_state(h, ctypes.cast(buf, ctypes.c_void_p), len(data)), "rve_load_state")
 
 
 # ------------------------------------------------------------- adjoint

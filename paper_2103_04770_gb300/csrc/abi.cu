@@ -1927,3 +1927,88 @@ int rve_adjoint_backward(rve_t* h, double dJ, double* grad_params, double* grad_
     return RVE_ERR_OOM;
   }
 }
+
+// ============================================================ checkpoint / resume
+namespace {
+struct StateHeader {
+  char magic[8];
+  int version, dim, prec, J;
+  int n[3], nc;
+  long long V;
+  int n_done, pad;
+  double E_prev[6], sig_mean[6], eps_mean[6], D_mean, D_max;
+};
+const char kStateMagic[8] = {'R', 'V', 'E', 'S', 'T', 'A', 'T', '1'};
+}  // namespace
+
+long long rve_state_bytes(const rve_t* h) {
+  if (!h) return 0;
+  const long long V = h->g.V;
+  return (long long)sizeof(StateHeader) + (long long)(h->g.nc + 7 + h->J) * V * 8;
+}
+
+int rve_save_state(const rve_t* h, void* buf, long long bytes) {
+  if (!h || !buf || bytes < rve_state_bytes(h)) return RVE_ERR_ARG;
+  if (!h->phases_set) return RVE_ERR_STATE;
+  StateHeader hd{};
+  std::memcpy(hd.magic, kStateMagic, 8);
+  hd.version = 1;
+  hd.dim = h->dim;
+  hd.prec = h->prec;
+  hd.J = h->J;
+  for (int j = 0; j < 3; j++) hd.n[j] = h->n[j];
+  hd.nc = h->g.nc;
+  hd.V = h->g.V;
+  hd.n_done = h->n_done;
+  for (int c = 0; c < 6; c++) {
+    hd.E_prev[c] = h->E_prev[c];
+    hd.sig_mean[c] = h->sig_mean[c];
+    hd.eps_mean[c] = h->eps_mean[c];
+  }
+  hd.D_mean = h->D_mean;
+  hd.D_max = h->D_max;
+  unsigned char* p = (unsigned char*)buf;
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  const size_t V = (size_t)h->g.V;
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpy(p, h->eps_conv, h->g.nc * V * 8, cudaMemcpyDeviceToHost));
+  p += h->g.nc * V * 8;
+  CK(cudaMemcpy(p, h->epsp_n, 6 * V * 8, cudaMemcpyDeviceToHost));
+  p += 6 * V * 8;
+  CK(cudaMemcpy(p, h->ep_n, V * 8, cudaMemcpyDeviceToHost));
+  p += V * 8;
+  if (h->J > 0) CK(cudaMemcpy(p, h->abar_n, (size_t)h->J * V * 8, cudaMemcpyDeviceToHost));
+  return RVE_OK;
+}
+
+int rve_load_state(rve_t* h, const void* buf, long long bytes) {
+  if (!h || !buf || bytes < (long long)sizeof(StateHeader)) return RVE_ERR_ARG;
+  if (!h->phases_set) return RVE_ERR_STATE;
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != 1 || hd.dim != h->dim || hd.prec != h->prec ||
+      hd.J != h->J || hd.nc != h->g.nc || hd.V != h->g.V || hd.n[0] != h->n[0] || hd.n[1] != h->n[1] ||
+      hd.n[2] != h->n[2] || bytes < rve_state_bytes(h) || hd.n_done < 0)
+    return RVE_ERR_ARG;
+  const unsigned char* p = (const unsigned char*)buf + sizeof(hd);
+  const size_t V = (size_t)h->g.V;
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpy(h->eps_conv, p, h->g.nc * V * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->eps, p, h->g.nc * V * 8, cudaMemcpyHostToDevice));
+  p += h->g.nc * V * 8;
+  CK(cudaMemcpy(h->epsp_n, p, 6 * V * 8, cudaMemcpyHostToDevice));
+  p += 6 * V * 8;
+  CK(cudaMemcpy(h->ep_n, p, V * 8, cudaMemcpyHostToDevice));
+  p += V * 8;
+  if (h->J > 0) CK(cudaMemcpy(h->abar_n, p, (size_t)h->J * V * 8, cudaMemcpyHostToDevice));
+  h->n_done = hd.n_done;
+  for (int c = 0; c < 6; c++) {
+    h->E_prev[c] = hd.E_prev[c];
+    h->sig_mean[c] = hd.sig_mean[c];
+    h->eps_mean[c] = hd.eps_mean[c];
+  }
+  h->D_mean = hd.D_mean;
+  h->D_max = hd.D_max;
+  return RVE_OK;
+}

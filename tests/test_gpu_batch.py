@@ -172,3 +172,26 @@ def test_batch_member_grids_mixed_vs_fp64(N):
             out[prec] = r.stress().copy()
     assert abs(out[1][0] - out[0][0]) <= 1e-4 * abs(out[0][0])
     assert np.abs(out[1] - out[0]).max() <= 1e-4 * abs(out[0][0])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_save_and_resume_state(prec):
+    """Saving after two increments and resuming on a fresh handle gives the
+    same next increments, bit for bit, as continuing."""
+    cfg = _member((12, 12, 12), 0.2, 2, 7, n_incr=4, prec=prec)
+    with pkg.RVE(cfg, precision=prec) as r:
+        r.step()
+        r.step()
+        img = pkg.rve_save_state(r.h)
+        cont = [(r.step()["cg_iters"], r.stress().copy()) for _ in range(2)]
+    with pkg.RVE(cfg, precision=prec) as r2:
+        pkg.rve_load_state(r2.h, img)
+        res = [(r2.step(), r2.stress().copy()) for _ in range(2)]
+    for (c0, s0), (info, s1) in zip(cont, res):
+        assert info["cg_iters"] == c0
+        np.testing.assert_array_equal(s0, s1)
+    assert res[0][0]["increment"] == 3
+    with pkg.RVE(cfg, precision=1 - prec) as r3:     # form mismatch is rejected
+        with pytest.raises(pkg.RVEError) as e:
+            pkg.rve_load_state(r3.h, img)
+        assert e.value.status == pkg.RVE_ERR_ARG
