@@ -580,12 +580,8 @@ static StrideInfo<R> stride_of(const Geo& g, int axis) {
 // Tile widths of the 256-point register-pass kernels (columns per CTA) for
 // NCOMP components per tile: NCOMP * TX * 16 tasks per pass, about three per
 // thread or fewer, and at most ~100 KB of shared memory.
-#ifndef RVK_TX6F
-#define RVK_TX6F 8
-#endif
 template <typename R, int NCOMP> struct RegTx {
-  static constexpr int v = sizeof(R) == 4 ? (NCOMP >= 6 ? RVK_TX6F : NCOMP >= 3 ? 8 : 16)
-                                          : (NCOMP >= 6 ? 4 : NCOMP >= 2 ? 8 : 16);
+  static constexpr int v = sizeof(R) == 4 ? (NCOMP >= 3 ? 8 : 16) : (NCOMP >= 6 ? 4 : NCOMP >= 2 ? 8 : 16);
 };
 // Point stride of the interleaved tile: six-component tiles (four rows of a
 // 32-lane warp per projection step) get 32 bytes of padding per point so
