@@ -39,6 +39,7 @@ enum {
   OFF_ERRMEAN = 16,   // 6
   OFF_ERRMAX = 22,
   OFF_ABAR = 24,      // 2 per variable
+  OFF_SIGREF = 40,    // 6: mean stress of the residual reference (mixed form)
 };
 
 // kernel classes of the launch accounting
@@ -151,6 +152,11 @@ struct rve {
   double g_pcg_b[kMaxVars][KC_COUNT] = {};
   bool stepped = false;  // an increment has been attempted (autotuning closed)
   double* stiff = nullptr;  // per-voxel modulus factor (nullptr: 1 everywhere)
+  // mixed form: stress and FP64-swept residual of the last FP64 sweep of the
+  // current increment (reference of the FP32 difference sweeps)
+  double* sig_ref = nullptr;
+  void* r_ref = nullptr;
+  bool ref_ok = false;
   AdjointStore* adj = nullptr;
 };
 
@@ -440,6 +446,38 @@ struct Alg {
                                             h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
   }
 
+  // Keep the stress and the residual of the FP64 sweep just made as the
+  // reference of later difference sweeps in this increment.
+  static int save_ref(rve* h) {
+    const Geo& g = h->g;
+    CK(cudaMemcpyAsync(h->sig_ref, h->sigma, 6 * (size_t)g.V * 8, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->r_ref, h->r, (size_t)g.nc * g.V * sizeof(R), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->dscal + OFF_SIGREF, h->dscal + OFF_SIGMEAN, 6 * sizeof(double),
+                       cudaMemcpyDeviceToDevice, h->st));
+    h->ref_ok = true;
+    return RVE_OK;
+  }
+
+  // Near Newton convergence (mixed form): G* is linear, so the residual at
+  // sigma is the FP64-swept reference residual minus the FP32 sweep of the
+  // small difference sigma - sigma_ref (Sigma_bar cancels); FP32 rounding is
+  // then about 1e-7 of |sigma - sigma_ref|, not of |sigma|.
+  static void residual_delta(rve* h, const Tables<R>& t, double rtol, int maxit) {
+    const Geo& g = h->g;
+    const double nc = g.nc;
+    const double zero[6] = {0, 0, 0, 0, 0, 0};
+    C2<R>* S = (C2<R>*)h->S;
+    LAUNCHB(h, KC_X_FWD_FIELD, nc * (16.0 * VV(h) + VS(h) * CS),
+            Op::xfwd_field64(g, t, h->lc, h->st, h->sigma, g.nc, g.cmap, h->dscal + OFF_SIGMEAN, S, h->sig_ref,
+                             h->dscal + OFF_SIGREF));
+    gamma_sweep(h, t, 1, nullptr);
+    LAUNCHB(h, KC_X_INV_RESIDUAL, nc * (VS(h) * CS + 2.0 * VV(h) * RS),
+            Op::template xinv_residual<R>(g, t, h->lc, h->st, S, (R*)h->r, h->dscal + OFF_SIGMEAN, h->smask_d,
+                                          zero, h->part, (const R*)h->r_ref, h->dscal + OFF_SIGREF));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
+                                            h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
+  }
+
   // FP32 Krylov solves stop when (r, r) has not fallen below a quarter of its
   // best value for this many iterations (attainable accuracy reached).
   static int stall_window() { return sizeof(R) == sizeof(float) ? 150 : 0; }
@@ -483,10 +521,22 @@ struct Alg {
     const double res_lo = std::max(100.0 * h->opt.tol_newton, 1e-4);
     for (;;) {
       return_map(h, abar_use);
-      bool lo = sizeof(R) == sizeof(float) && (last_res < 0.0 || last_res > res_lo);
+      const bool mixed = sizeof(R) == sizeof(float);
+      bool lo = mixed && (last_res < 0.0 || last_res > res_lo);
+      int s = RVE_OK;
+      // near convergence: a difference sweep against this increment's FP64
+      // reference, else a full FP64 sweep that becomes the reference
+      auto near = [&]() -> int {
+        if (mixed && h->ref_ok) {
+          residual_delta(h, t, h->opt.cg_rtol, h->opt.max_cg);
+          return RVE_OK;
+        }
+        residual(h, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
+        return mixed ? save_ref(h) : RVE_OK;
+      };
       if (lo) residual_lo(h, t, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
-      else residual(h, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
-      int s = sync_read(h);
+      else if ((s = near())) return s;
+      s = sync_read(h);
       if (s) return s;
       double sm = 0.0;
       for (int c = 0; c < g.nc; c++) sm += h->hscal[OFF_SIGMEAN + g.cmap[c]] * h->hscal[OFF_SIGMEAN + g.cmap[c]];
@@ -495,7 +545,7 @@ struct Alg {
       if (!(b2 == b2)) { h->fail_stage = 5; return RVE_ERR_NUMERIC; }
       double res_rel = std::sqrt(b2) / (std::sqrt((double)g.V) * std::max(sm, 1e-300));
       if (lo && res_rel <= res_lo) {
-        residual(h, sbar_c, h->opt.cg_rtol, h->opt.max_cg);
+        if ((s = near())) return s;
         if ((s = sync_read(h))) return s;
         b2 = h->hctl->b2;
         if (!(b2 == b2)) { h->fail_stage = 5; return RVE_ERR_NUMERIC; }
@@ -617,6 +667,7 @@ struct Alg {
       sbar[c] = h->ctrl[m] ? 0.0 : tm;
     }
     // initial guess (eps_n + dE on strain-controlled components; abar_n)
+    h->ref_ok = false;
     LAUNCHB(h, KC_MISC, 16.0 * g.nc * VV(h), k_copy_add(h->st, g.V, g.nc, h->eps_conv, h->eps, dE));
     CK(cudaMemcpyAsync(h->abar_k, h->abar_n, sizeof(double) * h->J * g.V, cudaMemcpyDeviceToDevice, h->st));
     int stag = 0, newton = 0;
@@ -973,6 +1024,8 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   if (precision == RVE_MIXED) {
     AL(build_tables<float>(h, h->tw, h->ts, h->tc));
     AL(dalloc(h, &h->S64, (size_t)nc * g.sstride * 16));
+    AL(dalloc_t(h, &h->sig_ref, 6 * V));
+    AL(dalloc(h, &h->r_ref, (size_t)nc * V * sizeof(float)));
   } else {
     for (int j = 0; j < 3; j++) { h->tw[j] = h->tw64[j]; h->ts[j] = h->ts64[j]; h->tc[j] = h->tc64[j]; }
     h->S64 = h->S;
@@ -1709,7 +1762,10 @@ void grad_field(rve* h, const Tables<double>& t, const double* a, double* out) {
   A::forward1(h, t, a, hr);
   LAUNCHB(h, KC_MISC, 0.0, Ops<double>::helm_expand(g, t, h->lc, h->st, W, (C2<double>*)h->hp, hr, 0.0, nullptr, 1));
   if (g.d == 3) LAUNCHB(h, KC_MISC, 0.0, Ops<double>::strided_plain(g, t, h->lc, h->st, W, g.d, 1, +1, nullptr));
-  LAUNCHB(h, KC_MISC, 0.0, Ops<double>::xinv_store64(g, t, h->lc, h->st, W, g.d, out));
+  // one component per store (the x1 store kernels exist for 1, 3 and 6)
+  for (int k = 0; k < g.d; k++)
+    LAUNCHB(h, KC_MISC, 0.0, Ops<double>::xinv_store64(g, t, h->lc, h->st, W + (size_t)k * g.sstride, 1,
+                                                       out + (size_t)k * g.V));
 }
 
 // read `n` finalised scalars from the adjoint reduction area

@@ -405,6 +405,8 @@ template <typename R, int NC>
 struct ProField64 {
   const double* f;
   const double* mean;   // device, may be null
+  const double* f2;     // subtracted field (same layout as f), may be null
+  const double* mean2;  // its mean, may be null
   long long V;
   int map[NC];
   __device__ void begin(const KrylovCtl*) {}
@@ -412,7 +414,9 @@ struct ProField64 {
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       double x = f[map[c] * V + v];
+      if (f2) x -= f2[map[c] * V + v];
       if (mean) x -= mean[map[c]];
+      if (mean2) x += mean2[map[c]];
       out[c] = (R)x;
     }
   }
@@ -459,11 +463,15 @@ struct EpiMatvec {       // Ap = val; acc0 += p . Ap   (p rows prefetched)
 };
 
 template <typename R, typename RO, int NC>
-struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
+// b = bref - (val + mask (mean_sigma - mean_ref - sbar)); acc0 += b . b
+// (bref, mean_ref null for a plain residual)
+struct EpiResidual {
   static constexpr bool kPrefetch = false;
   __device__ void prefetch(R*, long long, int, int) const {}
   RO* b;
   const double* mean_sig;   // full Mandel (6)
+  const double* mean_ref;   // full Mandel (6), may be null
+  const RO* bref;           // [NC][V], may be null
   double mask[NC];
   double sbar[NC];
   int map[NC];
@@ -471,13 +479,14 @@ struct EpiResidual {     // b = -(val + mask (mean_sigma - sbar)); acc0 += b . b
   double dc[NC];
   __device__ void begin(const KrylovCtl*) {
 #pragma unroll
-    for (int c = 0; c < NC; c++) dc[c] = mask[c] * (mean_sig[map[c]] - sbar[c]);
+    for (int c = 0; c < NC; c++)
+      dc[c] = mask[c] * (mean_sig[map[c]] - (mean_ref ? mean_ref[map[c]] : 0.0) - sbar[c]);
   }
   __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc) const {
     RO part = RO(0);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
-      const double bv = -((double)val[c] + dc[c]);
+      const double bv = (bref ? (double)bref[c * V + v] : 0.0) - ((double)val[c] + dc[c]);
       const RO br = (RO)bv;
       b[c * V + v] = br;
       part += br * br;
@@ -1334,9 +1343,10 @@ void Ops<R>::xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc,
 
 template <typename R, int NC>
 static void xfwd_field64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
-                            const double* f, const int* fmap, const double* mean_dev, C2<R>* S) {
+                            const double* f, const int* fmap, const double* mean_dev, C2<R>* S,
+                            const double* f2, const double* mean2) {
   ProField64<R, NC> pro;
-  pro.f = f; pro.mean = mean_dev; pro.V = g.V;
+  pro.f = f; pro.mean = mean_dev; pro.f2 = f2; pro.mean2 = mean2; pro.V = g.V;
   for (int c = 0; c < NC; c++) pro.map[c] = fmap[c];
 #define KCT_(M) (k_xfwd<R, NC, 4, ProField64<R, NC>, M>)
   XLAUNCH(KCT_, (k_xfwd<R, NC, 4, ProField64<R, NC>>),
@@ -1347,10 +1357,14 @@ static void xfwd_field64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
 
 template <typename R>
 void Ops<R>::xfwd_field64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
-                          const double* f, int ncomp, const int* fmap, const double* mean_dev, C2<R>* S) {
-  if (ncomp == 6) xfwd_field64_nc<R, 6>(g, t, lc, st, f, fmap, mean_dev, S);
-  else if (ncomp == 3) xfwd_field64_nc<R, 3>(g, t, lc, st, f, fmap, mean_dev, S);
-  else xfwd_field64_nc<R, 1>(g, t, lc, st, f, fmap, mean_dev, S);
+                          const double* f, int ncomp, const int* fmap, const double* mean_dev, C2<R>* S,
+                          const double* f2, const double* mean2) {
+  // component counts other than 6, 3 and 1 are transformed one by one
+  if (ncomp == 6) xfwd_field64_nc<R, 6>(g, t, lc, st, f, fmap, mean_dev, S, f2, mean2);
+  else if (ncomp == 3) xfwd_field64_nc<R, 3>(g, t, lc, st, f, fmap, mean_dev, S, f2, mean2);
+  else
+    for (int c = 0; c < ncomp; c++)
+      xfwd_field64_nc<R, 1>(g, t, lc, st, f, fmap + c, mean_dev, S + (size_t)c * g.sstride, f2, mean2);
 }
 
 template <typename R, int NC>
@@ -1375,9 +1389,9 @@ void Ops<R>::xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
 template <typename R, typename RO, int NC>
 static void xinv_residual_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                              const C2<R>* S, RO* b, const double* mean_sig_dev, const double* mask,
-                             const double* sbar, double* part) {
+                             const double* sbar, double* part, const RO* bref, const double* mean_ref) {
   EpiResidual<R, RO, NC> epi;
-  epi.b = b; epi.mean_sig = mean_sig_dev; epi.V = g.V;
+  epi.b = b; epi.mean_sig = mean_sig_dev; epi.mean_ref = mean_ref; epi.bref = bref; epi.V = g.V;
   for (int c = 0; c < NC; c++) {
     epi.mask[c] = mask[c];
     epi.sbar[c] = sbar[c];
@@ -1394,9 +1408,9 @@ template <typename R>
 template <typename RO>
 void Ops<R>::xinv_residual(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                            const C2<R>* S, RO* b, const double* mean_sig_dev, const double* mask,
-                           const double* sbar, double* part) {
-  if (g.nc == 6) xinv_residual_nc<R, RO, 6>(g, t, lc, st, S, b, mean_sig_dev, mask, sbar, part);
-  else xinv_residual_nc<R, RO, 3>(g, t, lc, st, S, b, mean_sig_dev, mask, sbar, part);
+                           const double* sbar, double* part, const RO* bref, const double* mean_ref) {
+  if (g.nc == 6) xinv_residual_nc<R, RO, 6>(g, t, lc, st, S, b, mean_sig_dev, mask, sbar, part, bref, mean_ref);
+  else xinv_residual_nc<R, RO, 3>(g, t, lc, st, S, b, mean_sig_dev, mask, sbar, part, bref, mean_ref);
 }
 
 template <typename R, int NC>
@@ -1414,9 +1428,11 @@ static void xinv_store64_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
 template <typename R>
 void Ops<R>::xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                           const C2<R>* S, int ncomp, double* out) {
+  // component counts other than 6, 3 and 1 are stored one by one
   if (ncomp == 6) xinv_store64_nc<R, 6>(g, t, lc, st, S, out);
   else if (ncomp == 3) xinv_store64_nc<R, 3>(g, t, lc, st, S, out);
-  else xinv_store64_nc<R, 1>(g, t, lc, st, S, out);
+  else
+    for (int c = 0; c < ncomp; c++) xinv_store64_nc<R, 1>(g, t, lc, st, S + (size_t)c * g.sstride, out + (size_t)c * g.V);
 }
 
 template <typename R>

@@ -52,19 +52,21 @@ struct Ops {
   // forward: tau = C_T : p  (with p <- r + beta p when ctl != null and iter > 0)
   static void xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                            R* p, const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl);
-  // forward: tau_c = f64[cmap?][v] - mean[c]  (ncomp components, comp stride V)
+  // forward: tau_c = f[map c][v] - mean[c] (ncomp components, comp stride V),
+  // minus f2[map c][v] - mean2[c] when f2 / mean2 are given
   static void xfwd_field64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                            const double* f, int ncomp, const int* fmap, const double* mean_dev,
-                           C2<R>* S);
+                           C2<R>* S, const double* f2 = nullptr, const double* mean2 = nullptr);
   // inverse: Ap = scale * C2R(S); partial (p, Ap)
   static void xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                           const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl);
-  // inverse: b = -(C2R + mask (mean_sigma - sbar)) stored in precision RO;
-  // partial (b, b) of the stored values
+  // inverse: b = bref - (C2R + mask (mean_sigma - mean_ref - sbar)) stored in
+  // precision RO (bref, mean_ref may be null); partial (b, b) of the stored values
   template <typename RO>
   static void xinv_residual(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                             const C2<R>* S, RO* b, const double* mean_sig_dev, const double* dcterm_mask,
-                            const double* sbar, double* part);
+                            const double* sbar, double* part, const RO* bref = nullptr,
+                            const double* mean_ref = nullptr);
   // inverse: out64[c][v] = scale * C2R(S)
   static void xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                            const C2<R>* S, int ncomp, double* out);

@@ -5,8 +5,10 @@ namespace rvk {
 template struct Ops<double>;
 template void Ops<double>::xinv_residual<double>(const Geo&, const Tables<double>&, const LaunchCfg&,
                                                  cudaStream_t, const C2<double>*, double*, const double*,
-                                                 const double*, const double*, double*);
+                                                 const double*, const double*, double*, const double*,
+                                                 const double*);
 template void Ops<double>::xinv_residual<float>(const Geo&, const Tables<double>&, const LaunchCfg&,
                                                 cudaStream_t, const C2<double>*, float*, const double*,
-                                                const double*, const double*, double*);
+                                                const double*, const double*, double*, const float*,
+                                                const double*);
 }  // namespace rvk
