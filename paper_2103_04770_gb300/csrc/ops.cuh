@@ -870,7 +870,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
 // Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
 // partial Hermitian-weighted (p, y).
 template <typename R, int D, int TXR = 0, int NAX = 256>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
 k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C2<R>* __restrict__ W,
            const C2<R>* __restrict__ p, C2<R>* __restrict__ y, int tx, long long astride,
            long long ostride, double* __restrict__ part, int pstride,
