@@ -158,6 +158,9 @@ struct rve {
   void* r_ref = nullptr;
   bool ref_ok = false;
   AdjointStore* adj = nullptr;
+  // CG step fused into the inverse x1 pass (its prefetch of p, x and r fits
+  // the shared memory of one CTA)
+  bool cg_fused = false;
 };
 
 namespace {
@@ -482,14 +485,30 @@ struct Alg {
   // best value for this many iterations (attainable accuracy reached).
   static int stall_window() { return sizeof(R) == sizeof(float) ? 150 : 0; }
 
-  // CG on G*(C_T : x) = b (r holds b, ctl initialised, x zeroed by caller).
+  // CG on G*(C_T : x) = b (r holds b in the range of G*, ctl initialised, x
+  // zeroed by caller).  Fused form: G* is an orthogonal projection and the
+  // directions p stay in its range, so the curvature (p, G*(C_T : p)) equals
+  // (p, C_T : p), summed in the forward x1 pass; alpha is then known before
+  // the inverse pass, which applies x += alpha p, r -= alpha A p at once and
+  // never stores A p.
   static int cg_loop(rve* h, const Tables<R>& t, int* iters) {
     const Geo& g = h->g;
     const int chunk = std::max(1, h->opt.check_every);
     const int nbx = xblocks(h, g.nc);
     for (;;) {
       int s = run_chunk(h, &h->g_cg, h->g_cg_n, h->g_cg_b, [&]() {
-        for (int i = 0; i < chunk; i++) {
+        for (int i = 0; i < chunk && h->cg_fused; i++) {
+          LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS,
+                  Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc,
+                                   (C2<R>*)h->S, h->ctl, h->part));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+          gamma_sweep(h, t, 0, h->ctl);
+          LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 5.0 * VV(h) * RS),
+                  Op::xinv_cg(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->x, (R*)h->r, (const R*)h->p,
+                              h->part, h->ctl));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
+        }
+        for (int i = 0; i < chunk && !h->cg_fused; i++) {
           LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S,
                            h->ctl));
           gamma_sweep(h, t, 0, h->ctl);
@@ -979,6 +998,16 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   lc.max_blocks = (int)mb;
   h->lc64 = lc;
   h->lc64.tx = tx64;
+  {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      optin = 0;
+    }
+    const size_t need = precision == RVE_MIXED ? Ops<float>::xinv_cg_smem(g, lc) : Ops<double>::xinv_cg_smem(g, lc);
+    h->cg_fused = need + 1024 <= (size_t)optin;
+  }
 
   int s = RVE_OK;
   const size_t V = (size_t)g.V;

@@ -181,14 +181,19 @@ k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, 
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
   pro.begin(ctl);
+  double acc[1] = {0.0};
   const int nvox = rows * n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
     const int r = e / n1, x = e - r * n1;
     const long long v = (row0 + r) * n1 + x;
     R val[NC];
-    pro(v, val);
+    if constexpr (PRO::kDot) pro(v, val, acc[0]);
+    else pro(v, val);
 #pragma unroll
     for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * n1 + x) = val[c];
+  }
+  if constexpr (PRO::kDot) {
+    if (pro.part) block_sum_store<1>(acc, pro.part, pro.pstride);
   }
   __syncthreads();
   if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, -1, true, 2, PS>(cbuf, tws);
@@ -275,7 +280,8 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
   // rows of the epilogue's input field, fetched together with the spectrum
   R* pre = reinterpret_cast<R*>(xs + (size_t)nrows * NC * g.ps);
-  if constexpr (EPI::kPrefetch) epi.prefetch(pre, row0, rows, n1);
+  const int fs = nrows * NC * n1;   // stride between prefetched fields
+  if constexpr (EPI::kPrefetch > 0) epi.prefetch(pre, row0, rows, n1, fs);
   xinv_pre_staged<R, NC, PS, MCT>(g, S, row0, rows, nrows, tws, cbuf, xs);
   __syncthreads();
   if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, +1, true, 2, PS>(cbuf, tws);
@@ -292,7 +298,7 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
     R val[NC];
 #pragma unroll
     for (int c = 0; c < NC; c++) val[c] = rpad<R, PS>(rbuf, (r * NC + c) * n1 + x) * scale;
-    if constexpr (EPI::kPrefetch) epi(v, val, acc, pre + (r * NC) * n1 + x, n1);
+    if constexpr (EPI::kPrefetch > 0) epi(v, val, acc, pre + (r * NC) * n1 + x, n1, fs);
     else epi(v, val, acc);
   }
   if (NS > 0) block_sum_store<NSA>(acc, part, pstride);
@@ -351,6 +357,9 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
 // Inside CG the direction is refreshed first: p <- r (iter 0) or r + beta p.
 template <typename R, int NC>
 struct ProTangent {
+  // (p, C_T : p) per CTA into part (when part is set): for p in the range of
+  // the projection this equals (p, G*(C_T : p)), the CG curvature
+  static constexpr bool kDot = true;
   R* p;
   const R* r;
   const R* desc;
@@ -358,10 +367,12 @@ struct ProTangent {
   int update;
   R beta;
   bool first;
+  double* part;
+  int pstride;
   __device__ void begin(const KrylovCtl* ctl) {
     if (ctl) { first = ctl->iter == 0; beta = (R)ctl->beta; }
   }
-  __device__ __forceinline__ void operator()(long long v, R (&out)[NC]) const {
+  __device__ __forceinline__ void operator()(long long v, R (&out)[NC], double& acc) const {
     constexpr int NN = NC == 6 ? 3 : 2;
     // every load first (r, p, descriptor), then the store of the new p:
     // the store could alias the loads, so it would otherwise serialise them
@@ -391,18 +402,24 @@ struct ProTangent {
 #pragma unroll
     for (int c = 0; c < NC; c++) mp += m[c] * pv[c];
     const R third = tr * R(1.0 / 3.0);
+    // the voxel's NC products summed in the working precision, the sum over
+    // voxels in FP64
+    R dot = R(0);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       R o = c2 * pv[c] - m[c] * mp;
       if (c < NN) o += c1 * tr - c2 * third;
       out[c] = o;
+      dot += pv[c] * o;
     }
+    acc += (double)dot;
   }
 };
 
 // tau_c = f[map[c]][v] - mean[map[c]]  (FP64 source fields)
 template <typename R, int NC>
 struct ProField64 {
+  static constexpr bool kDot = false;
   const double* f;
   const double* mean;   // device, may be null
   const double* f2;     // subtracted field (same layout as f), may be null
@@ -422,34 +439,40 @@ struct ProField64 {
   }
 };
 
+// cp.async of the CTA's rows of a [NC][V] field: pre[(r * NC + c) * n1 + x]
+template <typename R, int NC>
+__device__ __forceinline__ void prefetch_rows(R* pre, const R* f, long long V, long long row0, int rows,
+                                              int n1) {
+  constexpr int PER = 16 / (int)sizeof(R);
+  const int cpr = n1 / PER;
+  const int total = rows * NC * cpr;
+  if (n1 % PER == 0) {
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int l = e / cpr, ch = e - l * cpr;
+      const int r = l / NC, c = l - r * NC;
+      cp_async16(pre + (size_t)l * n1 + ch * PER, f + c * V + (row0 + r) * n1 + ch * PER);
+    }
+  } else {
+    for (int e = threadIdx.x; e < rows * NC * n1; e += kThreads) {
+      const int l = e / n1, x = e - l * n1;
+      const int r = l / NC, c = l - r * NC;
+      pre[e] = f[c * V + (row0 + r) * n1 + x];
+    }
+  }
+}
+
 template <typename R, int NC>
 struct EpiMatvec {       // Ap = val; acc0 += p . Ap   (p rows prefetched)
-  static constexpr bool kPrefetch = true;
+  static constexpr int kPrefetch = 1;
   R* Ap;
   const R* p;
   long long V;
   __device__ void begin(const KrylovCtl*) {}
-  // cp.async of the CTA's rows of p: pre[(r * NC + c) * n1 + x]
-  __device__ __forceinline__ void prefetch(R* pre, long long row0, int rows, int n1) const {
-    constexpr int PER = 16 / (int)sizeof(R);
-    const int cpr = n1 / PER;
-    const int total = rows * NC * cpr;
-    if (n1 % PER == 0) {
-      for (int e = threadIdx.x; e < total; e += kThreads) {
-        const int l = e / cpr, ch = e - l * cpr;
-        const int r = l / NC, c = l - r * NC;
-        cp_async16(pre + (size_t)l * n1 + ch * PER, p + c * V + (row0 + r) * n1 + ch * PER);
-      }
-    } else {
-      for (int e = threadIdx.x; e < rows * NC * n1; e += kThreads) {
-        const int l = e / n1, x = e - l * n1;
-        const int r = l / NC, c = l - r * NC;
-        pre[e] = p[c * V + (row0 + r) * n1 + x];
-      }
-    }
+  __device__ __forceinline__ void prefetch(R* pre, long long row0, int rows, int n1, int) const {
+    prefetch_rows<R, NC>(pre, p, V, row0, rows, n1);
   }
   __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc, const R* pv,
-                                             int n1) const {
+                                             int n1, int) const {
     // the voxel's NC products are summed in the working precision, the sum
     // over voxels in FP64
     R part = R(0);
@@ -462,12 +485,43 @@ struct EpiMatvec {       // Ap = val; acc0 += p . Ap   (p rows prefetched)
   }
 };
 
+// CG step fused into the inverse x1 pass: with val = G*(C_T : p) at the
+// voxel (never stored), x += alpha p, r -= alpha val, acc0 += r . r.  The
+// rows of p, x and r are prefetched with the spectrum.
+template <typename R, int NC>
+struct EpiCG {
+  static constexpr int kPrefetch = 3;
+  R* x;
+  R* r;
+  const R* p;
+  long long V;
+  R alpha;
+  __device__ void begin(const KrylovCtl* ctl) { alpha = (R)ctl->alpha; }
+  __device__ __forceinline__ void prefetch(R* pre, long long row0, int rows, int n1, int fs) const {
+    prefetch_rows<R, NC>(pre, p, V, row0, rows, n1);
+    prefetch_rows<R, NC>(pre + fs, x, V, row0, rows, n1);
+    prefetch_rows<R, NC>(pre + 2 * fs, r, V, row0, rows, n1);
+  }
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc, const R* pv,
+                                             int n1, int fs) const {
+    R part = R(0);
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      const R pc = pv[c * n1], xc = pv[fs + c * n1], rc = pv[2 * fs + c * n1];
+      x[c * V + v] = xc + alpha * pc;
+      const R rn = rc - alpha * val[c];
+      r[c * V + v] = rn;
+      part += rn * rn;
+    }
+    acc[0] += (double)part;
+  }
+};
+
 template <typename R, typename RO, int NC>
 // b = bref - (val + mask (mean_sigma - mean_ref - sbar)); acc0 += b . b
 // (bref, mean_ref null for a plain residual)
 struct EpiResidual {
-  static constexpr bool kPrefetch = false;
-  __device__ void prefetch(R*, long long, int, int) const {}
+  static constexpr int kPrefetch = 0;
   RO* b;
   const double* mean_sig;   // full Mandel (6)
   const double* mean_ref;   // full Mandel (6), may be null
@@ -497,8 +551,7 @@ struct EpiResidual {
 
 template <typename R, int NC>
 struct EpiStore64 {
-  static constexpr bool kPrefetch = false;
-  __device__ void prefetch(R*, long long, int, int) const {}
+  static constexpr int kPrefetch = 0;
   double* out;
   long long V;
   __device__ void begin(const KrylovCtl*) {}
@@ -1270,16 +1323,22 @@ static size_t xsmem(const Geo& g, int nrows, int nc) {
 }
 static inline int xgrid(const Geo& g, int nrows) { return (int)((g.nlines + nrows - 1) / nrows); }
 
+// shared memory of an x1 kernel: STAGE 0 plain, 1 staged spectrum rows,
+// 1 + k staged rows plus k prefetched real fields
+template <typename R>
+static size_t xinv_stage_smem(const Geo& g, int nr, int nc, int stage) {
+  if (!stage) return xsmem<R>(g, nr, nc);
+  return xstage_off<R>(g.n1, nr, nc) + (size_t)nr * nc * g.ps * sizeof(C2<R>) +
+         (size_t)(stage - 1) * nr * nc * g.n1 * sizeof(R);
+}
+
 // launch an x1 kernel K<E> with E = 4 or 16 as chosen in the launch config
-// (STAGE: 0 plain, 1 staged spectrum rows, 2 staged rows plus prefetched p)
 // x1 launch: compile-time variant KCT for rows of 128 complex points (N1 =
 // 256) at one row per CTA, else KT4 / KT16 by the staged-element count
 #define XLAUNCH(KCT, KT4, KT16, NCC, STAGE, ...)                                                        \
   do {                                                                                                  \
     const int nr = lc.nrows_c[NCC];                                                                     \
-    const size_t sm = STAGE ? xstage_off<R>(g.n1, nr, NCC) + (size_t)nr * NCC * g.ps * sizeof(C2<R>)   \
-                                  + (STAGE == 2 ? (size_t)nr * NCC * g.n1 * sizeof(R) : 0)              \
-                            : xsmem<R>(g, nr, NCC);                                                     \
+    const size_t sm = xinv_stage_smem<R>(g, nr, NCC, STAGE);                                           \
     if (lc.xe_c[NCC] == 4 && g.M == 128 && nr == XRows<128, NCC>::v) {                                  \
       auto k = KCT(128);                                                                                \
       set_smem(k, sm);                                                                                  \
@@ -1323,10 +1382,11 @@ static int axis_tx(const LaunchCfg& lc, int N, int ncomp) {
 
 template <typename R, int NC>
 static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
-                            const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl) {
+                            const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl, double* part) {
   ProTangent<R, NC> pro;
   pro.p = p; pro.r = r; pro.desc = desc; pro.V = g.V;
   pro.update = ctl != nullptr; pro.beta = R(0); pro.first = true;
+  pro.part = part; pro.pstride = lc.max_blocks;
 #define KCT_(M) (k_xfwd<R, NC, 4, ProTangent<R, NC>, M>)
   XLAUNCH(KCT_, (k_xfwd<R, NC, 4, ProTangent<R, NC>>),
           (k_xfwd<R, NC, 16, ProTangent<R, NC>>), NC, false,
@@ -1336,9 +1396,9 @@ static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& l
 
 template <typename R>
 void Ops<R>::xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
-                          const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl) {
-  if (g.nc == 6) xfwd_tangent_nc<R, 6>(g, t, lc, st, p, r, desc, S, ctl);
-  else xfwd_tangent_nc<R, 3>(g, t, lc, st, p, r, desc, S, ctl);
+                          const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl, double* part) {
+  if (g.nc == 6) xfwd_tangent_nc<R, 6>(g, t, lc, st, p, r, desc, S, ctl, part);
+  else xfwd_tangent_nc<R, 3>(g, t, lc, st, p, r, desc, S, ctl, part);
 }
 
 template <typename R, int NC>
@@ -1384,6 +1444,30 @@ void Ops<R>::xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
                          const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl) {
   if (g.nc == 6) xinv_matvec_nc<R, 6>(g, t, lc, st, S, Ap, p, part, ctl);
   else xinv_matvec_nc<R, 3>(g, t, lc, st, S, Ap, p, part, ctl);
+}
+
+template <typename R, int NC>
+static void xinv_cg_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                       const C2<R>* S, R* x, R* r, const R* p, double* part, const KrylovCtl* ctl) {
+  EpiCG<R, NC> epi;
+  epi.x = x; epi.r = r; epi.p = p; epi.V = g.V; epi.alpha = R(0);
+#define KCT_(M) (k_xinv<R, NC, 4, EpiCG<R, NC>, 1, M>)
+  XLAUNCH(KCT_, (k_xinv<R, NC, 4, EpiCG<R, NC>, 1>),
+          (k_xinv<R, NC, 16, EpiCG<R, NC>, 1>), NC, 4,
+          g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, part, lc.max_blocks, ctl);
+#undef KCT_
+}
+
+template <typename R>
+void Ops<R>::xinv_cg(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                     const C2<R>* S, R* x, R* r, const R* p, double* part, const KrylovCtl* ctl) {
+  if (g.nc == 6) xinv_cg_nc<R, 6>(g, t, lc, st, S, x, r, p, part, ctl);
+  else xinv_cg_nc<R, 3>(g, t, lc, st, S, x, r, p, part, ctl);
+}
+
+template <typename R>
+size_t Ops<R>::xinv_cg_smem(const Geo& g, const LaunchCfg& lc) {
+  return xinv_stage_smem<R>(g, lc.nrows_c[g.nc], g.nc, 4);
 }
 
 template <typename R, typename RO, int NC>

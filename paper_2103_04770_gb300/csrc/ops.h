@@ -49,9 +49,11 @@ struct LaunchCfg {
 template <typename R>
 struct Ops {
   // ---------------------------------------------------------------- x1 passes
-  // forward: tau = C_T : p  (with p <- r + beta p when ctl != null and iter > 0)
+  // forward: tau = C_T : p  (with p <- r + beta p when ctl != null and iter > 0);
+  // partial (p, tau) into part when part != null
   static void xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
-                           R* p, const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl);
+                           R* p, const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl,
+                           double* part = nullptr);
   // forward: tau_c = f[map c][v] - mean[c] (ncomp components, comp stride V),
   // minus f2[map c][v] - mean2[c] when f2 / mean2 are given
   static void xfwd_field64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
@@ -60,6 +62,12 @@ struct Ops {
   // inverse: Ap = scale * C2R(S); partial (p, Ap)
   static void xinv_matvec(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                           const C2<R>* S, R* Ap, const R* p, double* part, const KrylovCtl* ctl);
+  // inverse with the CG step fused: Ap = scale * C2R(S) (not stored),
+  // x += alpha p, r -= alpha Ap (alpha from ctl); partial (r, r)
+  static void xinv_cg(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                      const C2<R>* S, R* x, R* r, const R* p, double* part, const KrylovCtl* ctl);
+  // shared memory that xinv_cg asks for (it must fit the device's opt-in limit)
+  static size_t xinv_cg_smem(const Geo& g, const LaunchCfg& lc);
   // inverse: b = bref - (C2R + mask (mean_sigma - mean_ref - sbar)) stored in
   // precision RO (bref, mean_ref may be null); partial (b, b) of the stored values
   template <typename RO>
