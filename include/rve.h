@@ -222,7 +222,10 @@ int rve_op_apply_gamma(rve_t* h, const double* tau, double* out);
 int rve_op_matvec(rve_t* h, const double* p, double* Ap);
 
 /* Solves G*(C_T : x) = b by conjugate gradients from x = 0, stopping when
- * ||r|| <= rtol ||b|| or after maxit iterations; *iters receives the count. */
+ * ||r|| <= rtol ||b|| or after maxit iterations; *iters receives the count.
+ * b must lie in the range of G* (for instance b = G*(t) for some t): the
+ * curvature (p, G*(C_T : p)) is evaluated as (p, C_T : p), equal for
+ * directions in that range. */
 int rve_op_cg(rve_t* h, const double* b, double* x, double rtol, int maxit, int* iters);
 
 /* out = L(a) = a - div(l_j^2 grad a) evaluated spectrally (Eq.
