@@ -315,6 +315,7 @@ int sync_read(rve* h) {
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   if (h->prof) prof_resolve(h);
+  if (h->hctl->wait_err) return RVE_ERR_TIMEOUT;
   return RVE_OK;
 }
 
@@ -394,7 +395,8 @@ struct Alg {
   static void gamma_sweep(rve* h, const Tables<R>& t, int dc_mode, const KrylovCtl* ctl) {
     C2<R>* S = (C2<R>*)h->S;
     if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)h->g.nc * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, S, h->g.nc, 1, -1, ctl));
-    LAUNCHB(h, KC_GAMMA, 2.0 * (double)h->g.nc * VS(h) * CS, Op::gamma(h->g, t, h->lc, h->st, S, h->smask_f, dc_mode, ctl));
+    LAUNCHB(h, KC_GAMMA, 2.0 * (double)h->g.nc * VS(h) * CS,
+            Op::gamma(h->g, t, h->lc, h->st, S, h->smask_f, dc_mode, ctl, &h->ctl->wait_err));
     if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)h->g.nc * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, S, h->g.nc, 1, +1, ctl));
   }
 
@@ -421,7 +423,7 @@ struct Alg {
       LAUNCHB(h, KC_RES_Y_PASS, 2.0 * nc * VS(h) * cs64,
               Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, -1, nullptr));
     LAUNCHB(h, KC_RES_GAMMA, 2.0 * nc * VS(h) * cs64,
-            Ops<double>::gamma(g, t64, h->lc64, h->st, S64, h->smask_f, 1, nullptr));
+            Ops<double>::gamma(g, t64, h->lc64, h->st, S64, h->smask_f, 1, nullptr, &h->ctl->wait_err));
     if (g.d == 3)
       LAUNCHB(h, KC_RES_Y_PASS, 2.0 * nc * VS(h) * cs64,
               Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, +1, nullptr));
@@ -1048,6 +1050,12 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   AL(dalloc_t(h, &h->pt_dev, 1));
   AL(dalloc_t(h, &h->part, (size_t)kSlots * lc.max_blocks));
   AL(dalloc_t(h, &h->ctl, 1));
+  if (cudaMemset(h->ctl, 0, sizeof(KrylovCtl)) != cudaSuccess) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return RVE_ERR_CUDA;
+  }
   AL(dalloc_t(h, &h->dscal, kScal));
   AL(build_tables<double>(h, h->tw64, h->ts64, h->tc64));
   if (precision == RVE_MIXED) {
@@ -1248,6 +1256,7 @@ int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase
     d.eps_C = P.eps_C;
     d.eps_R = P.eps_R;
     d.D_max = P.D_max;
+    d.inv_dCR = P.eps_R > P.eps_C ? 1.0 / (P.eps_R - P.eps_C) : 0.0;
     d.law = P.damage_law;
     d.var = P.damage_law != 0 ? P.nonlocal_var : -1;
   }

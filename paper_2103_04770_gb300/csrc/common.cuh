@@ -53,6 +53,7 @@ __host__ __device__ constexpr bool reg_axis(int N) { return N == 64 || N == 128 
 struct PhaseDev {
   double K, mu, sigma_y, H;
   double eps_C, eps_R, D_max;
+  double inv_dCR;   // 1 / (eps_R - eps_C)
   int law;    // 0 elastic, 1 J2 + Lemaitre damage
   int var;    // non-local variable fed / read, -1 none
 };
@@ -80,6 +81,9 @@ struct KrylovCtl {
   // status: 0 running, 1 converged, 2 budget, 3 non-finite, 4 stopped at
   // the round-off floor ((p, Ap) <= 0)
   int iter, maxit, done, status;
+  // set by a kernel whose tile copy did not complete within its wait budget
+  // (never reset: the device is then not trustworthy)
+  int wait_err;
 };
 
 __host__ __device__ inline int grid_linear_block() {
@@ -107,6 +111,30 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NS], double* part, i
     double acc = 0.0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; w++) acc += red[w][threadIdx.x];
+    part[threadIdx.x * nblk_stride + grid_linear_block()] = acc;
+  }
+}
+
+// Deterministic block sum of per-thread FP32 partials: the warp tree runs in
+// FP32 (each thread's partial covers a few voxels, a warp 32 of those), the
+// warps' sums are added in FP64 in a fixed order.  Keeps the FP64 pipe,
+// which is narrow, out of the per-voxel work.
+template <int NS>
+__device__ __forceinline__ void block_sum_store(float (&v)[NS], double* part, int nblk_stride) {
+  __shared__ double redf[kThreads / 32][NS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    float x = v[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) redf[warp][s] = (double)x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) acc += redf[w][threadIdx.x];
     part[threadIdx.x * nblk_stride + grid_linear_block()] = acc;
   }
 }

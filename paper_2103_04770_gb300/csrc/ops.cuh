@@ -20,6 +20,7 @@
 #include "fft256.cuh"
 #include "fft_ct.cuh"
 #include "ops.h"
+#include "tma.cuh"
 
 namespace rvk {
 
@@ -181,7 +182,7 @@ k_xfwd(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ S, 
   const int rows = (int)lmin_(nrows, g.nlines - row0);
   for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
   pro.begin(ctl);
-  double acc[1] = {0.0};
+  R acc[1] = {R(0)};
   const int nvox = rows * n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
     const int r = e / n1, x = e - r * n1;
@@ -287,9 +288,9 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
   if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, +1, true, 2, PS>(cbuf, tws);
   else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
   constexpr int NSA = NS > 0 ? NS : 1;
-  double acc[NSA];
+  R acc[NSA];
 #pragma unroll
-  for (int s = 0; s < NSA; s++) acc[s] = 0.0;
+  for (int s = 0; s < NSA; s++) acc[s] = R(0);
   epi.begin(ctl);
   const int nvox = rows * n1;
   for (int e = threadIdx.x; e < nvox; e += kThreads) {
@@ -372,7 +373,7 @@ struct ProTangent {
   __device__ void begin(const KrylovCtl* ctl) {
     if (ctl) { first = ctl->iter == 0; beta = (R)ctl->beta; }
   }
-  __device__ __forceinline__ void operator()(long long v, R (&out)[NC], double& acc) const {
+  __device__ __forceinline__ void operator()(long long v, R (&out)[NC], R& acc) const {
     constexpr int NN = NC == 6 ? 3 : 2;
     // every load first (r, p, descriptor), then the store of the new p:
     // the store could alias the loads, so it would otherwise serialise them
@@ -402,17 +403,14 @@ struct ProTangent {
 #pragma unroll
     for (int c = 0; c < NC; c++) mp += m[c] * pv[c];
     const R third = tr * R(1.0 / 3.0);
-    // the voxel's NC products summed in the working precision, the sum over
-    // voxels in FP64
-    R dot = R(0);
+    // summed in the working precision per thread and warp, in FP64 above
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       R o = c2 * pv[c] - m[c] * mp;
       if (c < NN) o += c1 * tr - c2 * third;
       out[c] = o;
-      dot += pv[c] * o;
+      acc += pv[c] * o;
     }
-    acc += (double)dot;
   }
 };
 
@@ -426,15 +424,17 @@ struct ProField64 {
   const double* mean2;  // its mean, may be null
   long long V;
   int map[NC];
-  __device__ void begin(const KrylovCtl*) {}
+  double dm[NC];   // mean2 - mean per component
+  __device__ void begin(const KrylovCtl*) {
+#pragma unroll
+    for (int c = 0; c < NC; c++) dm[c] = (mean2 ? mean2[map[c]] : 0.0) - (mean ? mean[map[c]] : 0.0);
+  }
   __device__ __forceinline__ void operator()(long long v, R (&out)[NC]) const {
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       double x = f[map[c] * V + v];
       if (f2) x -= f2[map[c] * V + v];
-      if (mean) x -= mean[map[c]];
-      if (mean2) x += mean2[map[c]];
-      out[c] = (R)x;
+      out[c] = (R)(x + dm[c]);
     }
   }
 };
@@ -471,17 +471,14 @@ struct EpiMatvec {       // Ap = val; acc0 += p . Ap   (p rows prefetched)
   __device__ __forceinline__ void prefetch(R* pre, long long row0, int rows, int n1, int) const {
     prefetch_rows<R, NC>(pre, p, V, row0, rows, n1);
   }
-  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc, const R* pv,
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], R* acc, const R* pv,
                                              int n1, int) const {
-    // the voxel's NC products are summed in the working precision, the sum
-    // over voxels in FP64
-    R part = R(0);
+    // summed in the working precision per thread and warp, in FP64 above
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       Ap[c * V + v] = val[c];
-      part += pv[c * n1] * val[c];
+      acc[0] += pv[c * n1] * val[c];
     }
-    acc[0] += (double)part;
   }
 };
 
@@ -502,18 +499,16 @@ struct EpiCG {
     prefetch_rows<R, NC>(pre + fs, x, V, row0, rows, n1);
     prefetch_rows<R, NC>(pre + 2 * fs, r, V, row0, rows, n1);
   }
-  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc, const R* pv,
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], R* acc, const R* pv,
                                              int n1, int fs) const {
-    R part = R(0);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       const R pc = pv[c * n1], xc = pv[fs + c * n1], rc = pv[2 * fs + c * n1];
       x[c * V + v] = xc + alpha * pc;
       const R rn = rc - alpha * val[c];
       r[c * V + v] = rn;
-      part += rn * rn;
+      acc[0] += rn * rn;
     }
-    acc[0] += (double)part;
   }
 };
 
@@ -536,16 +531,22 @@ struct EpiResidual {
     for (int c = 0; c < NC; c++)
       dc[c] = mask[c] * (mean_sig[map[c]] - (mean_ref ? mean_ref[map[c]] : 0.0) - sbar[c]);
   }
-  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double* acc) const {
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], R* acc) const {
     RO part = RO(0);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
-      const double bv = (bref ? (double)bref[c * V + v] : 0.0) - ((double)val[c] + dc[c]);
-      const RO br = (RO)bv;
+      RO br;
+      if constexpr (sizeof(R) == 4) {
+        // FP32 sweep: operands already FP32, the result stored in FP32
+        br = (bref ? (R)bref[c * V + v] : R(0)) - (val[c] + (R)dc[c]);
+      } else {
+        const double bv = (bref ? (double)bref[c * V + v] : 0.0) - ((double)val[c] + dc[c]);
+        br = (RO)bv;
+      }
       b[c * V + v] = br;
       part += br * br;
     }
-    acc[0] += (double)part;
+    acc[0] += (R)part;
   }
 };
 
@@ -555,7 +556,7 @@ struct EpiStore64 {
   double* out;
   long long V;
   __device__ void begin(const KrylovCtl*) {}
-  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], double*) const {
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[NC], R*) const {
 #pragma unroll
     for (int c = 0; c < NC; c++) out[c * V + v] = (double)val[c];
   }
@@ -831,6 +832,67 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   tile_store<R, IL>(buf, base, nc, g.sstride, N, astride, tx, IL ? TXR : cols, RS);
 }
 
+// The same last-axis pass in 3D with the tile moved by the tensor memory
+// accelerator: one box {TXR columns, NC components, one y plane, NAX z
+// points} lands as [z][c][col] (point stride NC TXR, no padding), and goes
+// back the same way.  A CTA that waits longer than kWaitNs for its tile
+// records it in *wait_err and skips the tile.
+template <typename R, int NC, int TXR, int NAX>
+__global__ void __launch_bounds__(kThreads, 2)
+k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const C2<R>* __restrict__ tw,
+            Mask6 mask, int dc_mode, const KrylovCtl* __restrict__ ctl, int* __restrict__ wait_err) {
+  if (ctl && ctl->done) return;
+  constexpr int RS = NC * TXR;
+  constexpr int U8 = (int)sizeof(C2<R>) / 8;    // 8-byte elements per complex entry
+  constexpr uint32_t kBytes = (uint32_t)(NAX * RS * sizeof(C2<R>));
+  extern __shared__ __align__(128) unsigned char smtma[];
+  __shared__ __align__(8) uint64_t bar;
+  C2<R>* tws = reinterpret_cast<C2<R>*>(smtma);
+  C2<R>* buf = reinterpret_cast<C2<R>*>(smtma + ((tw_bytes<R>(NAX) + 127) & ~(size_t)127));
+  const int q0 = blockIdx.x * TXR;
+  const int cols = min(TXR, g.P1 - q0);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, kBytes);
+    tma_load_4d(buf, &tmap, q0 * U8, 0, blockIdx.y, 0, &bar);
+  }
+  for (int i = threadIdx.x; i < NAX; i += kThreads) tws[i] = tw[i];
+  __syncthreads();
+  if (!mbar_wait(&bar, 0, kWaitNs)) {
+    if (threadIdx.x == 0 && wait_err) atomicExch(wait_err, 1);
+    mbar_wait(&bar, 0, kWaitNs);   // the copy in flight, once more bounded
+    return;
+  }
+  fftreg_forward<R, NAX, NC * TXR, RS>(buf, tws);
+  {
+    // the register passes leave frequency reg_freq(n) at tile row n
+    constexpr int RPT = kThreads / TXR;
+    const int col = threadIdx.x % TXR;
+    if (col < cols) {
+      LastSym<R> sy;
+      sy.init(g, t, q0 + col);
+#pragma unroll 2
+      for (int n = threadIdx.x / TXR; n < NAX; n += RPT) {
+        R a[3];
+        C2<R> ph;
+        bool dc;
+        sy.at(g, t, reg_freq<NAX>(n), a, ph, dc);
+        C2<R> tv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) tv[c] = buf[n * RS + c * TXR + col];
+        gamma_apply<R, NC>(a, dc, mask, dc_mode, tv);
+#pragma unroll
+        for (int c = 0; c < NC; c++) buf[n * RS + c * TXR + col] = tv[c];
+      }
+    }
+  }
+  __syncthreads();
+  fftreg_inverse<R, NAX, NC * TXR, RS>(buf, tws);
+  tma_fence_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) tma_store_4d_and_wait(&tmap, buf, q0 * U8, 0, blockIdx.y, 0);
+}
+
 template <typename R>
 __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
   return (q1 == 0 || 2 * q1 == g.n1) ? R(1) : R(2);
@@ -961,7 +1023,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   } else {
     for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
-  double acc[1] = {0.0};
+  R acc[1] = {R(0)};
   if constexpr (IL) {
     const int col = threadIdx.x % TXR;
     if (col < cols) {
@@ -983,7 +1045,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
         const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
         const C2<R> yv = pv[k] + ks;
         y[off + n * astride + col] = yv;
-        acc[0] += (double)w1 * ((double)pv[k].x * (double)yv.x + (double)pv[k].y * (double)yv.y);
+        acc[0] += w1 * (pv[k].x * yv.x + pv[k].y * yv.y);
       }
     }
   } else {
@@ -1003,7 +1065,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
       const C2<R> pn = p[idx];
       const C2<R> yv = pn + ks;
       y[idx] = yv;
-      acc[0] += (double)q1_weight<R>(g, m0) * ((double)pn.x * (double)yv.x + (double)pn.y * (double)yv.y);
+      acc[0] += q1_weight<R>(g, m0) * (pn.x * yv.x + pn.y * yv.y);
     }
   }
   block_sum_store<1>(acc, part, pstride);
@@ -1044,8 +1106,8 @@ template <> __device__ __forceinline__ void vaxpy<double>(double2& y, double a, 
   y.x += a * x.x; y.y += a * x.y;
 }
 
-// x += alpha p, r -= alpha Ap, partial (r, r): 16-byte vectors, the vector's
-// terms summed in the working precision and accumulated in FP64
+// x += alpha p, r -= alpha Ap, partial (r, r): 16-byte vectors; the terms
+// summed in the working precision per thread and warp, in FP64 above
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_cg_update(long long n, R* __restrict__ x, R* __restrict__ r, const R* __restrict__ p,
@@ -1055,7 +1117,7 @@ k_cg_update(long long n, R* __restrict__ x, R* __restrict__ r, const R* __restri
   using VT = typename Vec16<R>::T;
   constexpr int VN = Vec16<R>::n;
   const R alpha = (R)ctl->alpha;
-  double acc[1] = {0.0};
+  R acc[1] = {R(0)};
   const long long nv = n / VN;
   VT* xv = reinterpret_cast<VT*>(x);
   VT* rv = reinterpret_cast<VT*>(r);
@@ -1068,14 +1130,14 @@ k_cg_update(long long n, R* __restrict__ x, R* __restrict__ r, const R* __restri
     vaxpy<R>(ri, -alpha, ai);
     xv[i] = xi;
     rv[i] = ri;
-    acc[0] += (double)vdot_self<R>(ri);
+    acc[0] += vdot_self<R>(ri);
   }
   for (long long i = nv * VN + blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
        i += (long long)gridDim.x * kThreads) {
     x[i] += alpha * p[i];
     const R rn = r[i] - alpha * Ap[i];
     r[i] = rn;
-    acc[0] += (double)rn * (double)rn;
+    acc[0] += rn * rn;
   }
   block_sum_store<1>(acc, part, pstride);
 }
@@ -1112,26 +1174,72 @@ k_pcg_init(Geo g, Tables<R> t, C2<R>* __restrict__ x, const C2<R>* __restrict__ 
   block_sum_store<2>(acc, part, pstride);
 }
 
+// Element e of the flat half spectrum (line e / P1, column e % P1), split
+// without a 64-bit division: a float estimate of the quotient (off by at
+// most one below about 5 M lines, by a few beyond) is corrected exactly.
+__device__ __forceinline__ void split_flat(long long e, int P1, float invP1, long long& line, int& q1) {
+  long long l = (long long)((float)e * invP1);
+  long long r = e - l * P1;
+  while (r < 0) { l -= 1; r += P1; }
+  while (r >= P1) { l += 1; r -= P1; }
+  line = l;
+  q1 = (int)r;
+}
+
+// M = 1 / (1 + <l^2> |k|^2) at column q1 of the line with modes (m1, m2)
+template <typename R>
+__device__ __forceinline__ R precond_mode(const Geo& g, const Tables<R>& t, int q1, int m1, int m2, R ell2m) {
+  R a[3];
+  C2<R> ph;
+  symbol(g, t, q1, m1, m2, a, ph);
+  return R(1) / (R(1) + ell2m * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+}
+
+// x += alpha p, r -= alpha y over the half spectrum; partial (r, r) and
+// (r, M r) with the Hermitian weights.  One 16-byte vector of complex
+// entries per thread and step over the padded rows (entries past P1 are
+// updated too, their values are never used); the terms are summed in the
+// working precision per thread and warp, in FP64 above.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_pcg_update(Geo g, Tables<R> t, C2<R>* __restrict__ x, C2<R>* __restrict__ r,
              const C2<R>* __restrict__ p, const C2<R>* __restrict__ y, R ell2m,
              double* __restrict__ part, int pstride, const KrylovCtl* __restrict__ ctl) {
   if (ctl->done) return;
+  using VT = typename Vec16<R>::T;
+  constexpr int U = 16 / (int)sizeof(C2<R>);   // complex entries per vector
   const R alpha = (R)ctl->alpha;
-  double acc[2] = {0.0, 0.0};
-  const long long n = (long long)g.P1 * g.nlines;
-  for (long long e = blockIdx.x * (long long)kThreads + threadIdx.x; e < n; e += (long long)gridDim.x * kThreads) {
-    int q1;
-    const R Mk = precond_at(g, t, e, ell2m, q1);
-    const long long idx = (e / g.P1) * g.ps + q1;
-    x[idx] = x[idx] + cscale(p[idx], alpha);
-    const C2<R> rn = r[idx] - cscale(y[idx], alpha);
-    r[idx] = rn;
-    const double w = q1_weight<R>(g, q1);
-    const double rr = (double)rn.x * rn.x + (double)rn.y * rn.y;
-    acc[0] += w * rr;
-    acc[1] += w * (double)Mk * rr;
+  R acc[2] = {R(0), R(0)};
+  const int upl = g.ps / U;                    // vectors per padded row
+  const long long nu = (long long)upl * g.nlines;
+  const float inv_upl = 1.0f / (float)upl;
+  for (long long u = blockIdx.x * (long long)kThreads + threadIdx.x; u < nu;
+       u += (long long)gridDim.x * kThreads) {
+    long long line;
+    int jv;
+    split_flat(u, upl, inv_upl, line, jv);
+    // line = m1 + n2 m2 (32-bit: fewer than 2^31 lines)
+    const int m2 = (int)((unsigned)line / (unsigned)g.n2), m1 = (int)line - m2 * g.n2;
+    const long long base = line * g.ps + (long long)jv * U;
+    alignas(16) C2<R> xe[U], re[U], pe[U], ye[U];
+    *reinterpret_cast<VT*>(xe) = *reinterpret_cast<const VT*>(x + base);
+    *reinterpret_cast<VT*>(re) = *reinterpret_cast<const VT*>(r + base);
+    *reinterpret_cast<VT*>(pe) = *reinterpret_cast<const VT*>(p + base);
+    *reinterpret_cast<VT*>(ye) = *reinterpret_cast<const VT*>(y + base);
+#pragma unroll
+    for (int i = 0; i < U; i++) {
+      const int q1 = jv * U + i;
+      xe[i] = xe[i] + cscale(pe[i], alpha);
+      re[i] = re[i] - cscale(ye[i], alpha);
+      if (q1 < g.P1) {
+        const R Mk = precond_mode(g, t, q1, m1, m2, ell2m);
+        const R wrr = q1_weight<R>(g, q1) * (re[i].x * re[i].x + re[i].y * re[i].y);
+        acc[0] += wrr;
+        acc[1] += Mk * wrr;
+      }
+    }
+    *reinterpret_cast<VT*>(x + base) = *reinterpret_cast<const VT*>(xe);
+    *reinterpret_cast<VT*>(r + base) = *reinterpret_cast<const VT*>(re);
   }
   block_sum_store<2>(acc, part, pstride);
 }
@@ -1202,8 +1310,9 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
     double pn[6];
     for (int c = 0; c < 6; c++) { pn[c] = epsp_n[c * V + v]; e[c] -= pn[c]; }
     const double tr = e[0] + e[1] + e[2];
+    const double tr3 = tr * (1.0 / 3.0);
     double dev[6];
-    for (int c = 0; c < 6; c++) dev[c] = e[c] - (c < 3 ? tr / 3.0 : 0.0);
+    for (int c = 0; c < 6; c++) dev[c] = e[c] - (c < 3 ? tr3 : 0.0);
     // per-voxel modulus factor (1 without a stiffness field)
     const double sc = stiff ? stiff[v] : 1.0;
     const double K = P.K * sc, mu = P.mu * sc;
@@ -1216,17 +1325,19 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
     if (P.law == 1) {
       const double f = q - s23 * (P.sigma_y + P.H * epn);
       if (f > 0.0) {
-        // three FP64 divisions per plastic voxel (division is slow on the
-        // FP64 pipe): 1/q is shared by the flow direction and theta
-        dl = f / (2.0 * mu + 2.0 * P.H / 3.0);
+        // two FP64 divisions per plastic voxel (division is slow on the FP64
+        // pipe): 2 mu + 2H/3 = (2/3)(3 mu + H), so 1/(3 mu + H) serves the
+        // multiplier and thetabar, 1/q the flow direction and theta
+        const double ih = 1.0 / (3.0 * mu + P.H);
+        dl = 1.5 * f * ih;
         const double iq = 1.0 / q;
         for (int c = 0; c < 6; c++) nh[c] = 2.0 * mu * dev[c] * iq;
         theta = 1.0 - 2.0 * mu * dl * iq;
-        thetab = (3.0 * mu) / (3.0 * mu + P.H) - (1.0 - theta);
+        thetab = 3.0 * mu * ih - (1.0 - theta);
       }
       if (P.var >= 0) {
         const double ab = abar[P.var * V + v];
-        D = (ab - P.eps_C) / (P.eps_R - P.eps_C);
+        D = (ab - P.eps_C) * P.inv_dCR;
         D = D < 0.0 ? 0.0 : (D > P.D_max ? P.D_max : D);
       }
     }
@@ -1237,7 +1348,7 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
       kap = fmax(epn, positive_principal_norm(e));
       if (P.var >= 0) {
         const double ab = abar[P.var * V + v];
-        D = (ab - P.eps_C) / (P.eps_R - P.eps_C);
+        D = (ab - P.eps_C) * P.inv_dCR;
         D = D < 0.0 ? 0.0 : (D > P.D_max ? P.D_max : D);
       }
     }
@@ -1258,8 +1369,10 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
     dmx[0] = fmax(dmx[0], D);
     desc[v] = (R)(om * K);
     desc[V + v] = (R)(om * 2.0 * mu * theta);
-    const double ms = sqrt(om * 2.0 * mu * thetab);
-    for (int c = 0; c < nc; c++) desc[(2 + c) * V + v] = (R)(ms * nh[g.cmap[c]]);
+    // the descriptor is stored in the working precision: its square root in
+    // that precision too
+    const R ms = sqrt((R)(om * 2.0 * mu * thetab));
+    for (int c = 0; c < nc; c++) desc[(2 + c) * V + v] = ms * (R)nh[g.cmap[c]];
   }
   block_sum_store<7>(acc, part, pstride);
   __syncthreads();
@@ -1561,7 +1674,7 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
 
 template <typename R>
 void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* S,
-                   const float* stress_mask, int dc_mode, const KrylovCtl* ctl) {
+                   const float* stress_mask, int dc_mode, const KrylovCtl* ctl, int* wait_err) {
   const int axis = g.d - 1;
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
@@ -1572,6 +1685,32 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   Mask6 m;
   for (int c = 0; c < 6; c++) m.m[c] = c < g.nc ? stress_mask[c] : 0.f;
+  if (g.d == 3 && g.nc == 6 && reg) {
+    // TMA path: the box {TX6 columns, 6 components, 1, N} of the half
+    // spectrum seen as 8-byte elements [z][y][c][x]
+    constexpr int TX6 = RegTx<R, 6>::v;
+    constexpr int U8 = (int)sizeof(C2<R>) / 8;
+    const unsigned long long cb = sizeof(C2<R>);
+    const unsigned long long dims[4] = {(unsigned long long)g.ps * U8, 6ULL, (unsigned long long)g.n2,
+                                        (unsigned long long)g.n3};
+    const unsigned long long strides[3] = {(unsigned long long)g.sstride * cb, (unsigned long long)g.ps * cb,
+                                           (unsigned long long)g.ps * g.n2 * cb};
+    const unsigned box[4] = {(unsigned)(TX6 * U8), 6u, 1u, (unsigned)si.N};
+    const CUtensorMap* map = tensor_map_8b(S, 4, dims, strides, box);
+    if (map) {
+      // column tiles up to P1 (inside the padded row: ps is a multiple of 16)
+      const size_t smt = ((tw_bytes<R>(si.N) + 127) & ~(size_t)127) + (size_t)si.N * 6 * TX6 * sizeof(C2<R>);
+      dim3 gt((g.P1 + TX6 - 1) / TX6, g.n2, 1);
+      auto launch = [&](auto k) {
+        set_smem(k, smt);
+        k<<<gt, kThreads, smt, st>>>(g, t, *map, t.tw[axis], m, dc_mode, ctl, wait_err);
+      };
+      if (si.N == 256) launch(k_gamma_tma<R, 6, TX6, 256>);
+      else if (si.N == 128) launch(k_gamma_tma<R, 6, TX6, 128>);
+      else launch(k_gamma_tma<R, 6, TX6, 64>);
+      return;
+    }
+  }
   auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
     return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
   };

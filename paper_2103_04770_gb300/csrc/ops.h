@@ -87,9 +87,11 @@ struct Ops {
   static void strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                             C2<R>* S, int ncomp, int axis, int sign, const KrylovCtl* ctl);
   // last axis: forward, modified projection (dc_mode 0: stress-mask at xi=0,
-  // 1: zero at xi=0), inverse
+  // 1: zero at xi=0), inverse.  In 3D the tiles move by TMA; a CTA whose
+  // tile did not arrive within its wait budget sets *wait_err (if given).
   static void gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
-                    C2<R>* S, const float* stress_mask, int dc_mode, const KrylovCtl* ctl);
+                    C2<R>* S, const float* stress_mask, int dc_mode, const KrylovCtl* ctl,
+                    int* wait_err = nullptr);
   // last axis inverse with p <- M r + beta p, W_j = k_j p
   // raw = 1: W_j = k_j r without touching p (operator application only)
   static void helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,

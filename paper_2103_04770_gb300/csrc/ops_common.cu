@@ -5,33 +5,37 @@
 
 namespace rvk {
 
-// One CTA: slot s is reduced in a fixed order (thread t sums blocks
-// t, t + 256, ...; then a fixed tree), so results are reproducible.
-__global__ void __launch_bounds__(kThreads)
+// One CTA of kFinThreads: slot s is reduced in a fixed order (thread t sums
+// blocks t, t + kFinThreads, ... in eight interleaved accumulators; then a
+// fixed tree), so results are reproducible.  Eight loads in flight per
+// thread over 1024 threads keep the 32 K partials of the x1 passes at
+// 256^3 to a few round trips.
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads)
 k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int nslots, int mode,
                 KrylovCtl* ctl, double* out, double scale, int imax, int stall) {
-  __shared__ double red[kThreads];
+  __shared__ double red[kFinThreads];
   __shared__ double vals[16];
   const bool is_max = mode == FIN_MAXS;
   for (int s = 0; s < nslots; s++) {
-    // four independent partial accumulators per thread (loads in flight
-    // together), combined in a fixed order: deterministic
     const double* ps = part + (long long)s * stride;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int b = threadIdx.x;
-    for (; b + 3 * kThreads < nblocks; b += 4 * kThreads) {
-      const double x0 = ps[b], x1 = ps[b + kThreads], x2 = ps[b + 2 * kThreads], x3 = ps[b + 3 * kThreads];
-      if (is_max) {
-        a0 = fmax(a0, x0); a1 = fmax(a1, x1); a2 = fmax(a2, x2); a3 = fmax(a3, x3);
-      } else {
-        a0 += x0; a1 += x1; a2 += x2; a3 += x3;
-      }
+    for (; b + 7 * kFinThreads < nblocks; b += 8 * kFinThreads) {
+      double x[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) x[k] = ps[b + k * kFinThreads];
+#pragma unroll
+      for (int k = 0; k < 8; k++) a[k] = is_max ? fmax(a[k], x[k]) : a[k] + x[k];
     }
-    for (; b < nblocks; b += kThreads) a0 = is_max ? fmax(a0, ps[b]) : a0 + ps[b];
-    const double acc = is_max ? fmax(fmax(a0, a1), fmax(a2, a3)) : (a0 + a1) + (a2 + a3);
+    for (; b < nblocks; b += kFinThreads) a[0] = is_max ? fmax(a[0], ps[b]) : a[0] + ps[b];
+    double acc;
+    if (is_max) acc = fmax(fmax(fmax(a[0], a[1]), fmax(a[2], a[3])), fmax(fmax(a[4], a[5]), fmax(a[6], a[7])));
+    else acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int o = kThreads / 2; o > 0; o >>= 1) {
+    for (int o = kFinThreads / 2; o > 0; o >>= 1) {
       if (threadIdx.x < o) {
         red[threadIdx.x] = is_max ? fmax(red[threadIdx.x], red[threadIdx.x + o])
                                   : red[threadIdx.x] + red[threadIdx.x + o];
@@ -122,8 +126,8 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
 
 void k_finalize(cudaStream_t st, const double* part, int nblocks, int nblk_stride, int nslots, int mode,
                 KrylovCtl* ctl, double* out, double scale, int imax, int stall) {
-  k_finalize_impl<<<1, kThreads, 0, st>>>(part, nblocks, nblk_stride, nslots, mode, ctl, out, scale, imax,
-                                          stall);
+  k_finalize_impl<<<1, kFinThreads, 0, st>>>(part, nblocks, nblk_stride, nslots, mode, ctl, out, scale, imax,
+                                             stall);
 }
 
 struct Add6 { double a[6]; };
