@@ -712,6 +712,14 @@ struct LastSym {
     s1 = t.s[1][m1];
     c1 = t.c[1][m1];
   }
+  // 3D, last-axis factors s2 = sin, c2 = cos of mode f given (staged by the
+  // caller): the same products as at()
+  __device__ __forceinline__ void at3(const Tables<R>& t, int f, R s2, R c2, R a[3], bool& dc) const {
+    a[0] = t.two_over_h[0] * s0 * c1 * c2;
+    a[1] = t.two_over_h[1] * s1 * c0 * c2;
+    a[2] = t.two_over_h[2] * s2 * c0 * c1;
+    dc = m0 == 0 && m1 == 0 && f == 0;
+  }
   // modes (m0, m1, f) in 3D, (m0, f) in 2D
   __device__ __forceinline__ void at(const Geo& g, const Tables<R>& t, int f, R a[3], C2<R>& ph,
                                      bool& dc) const {
@@ -832,6 +840,13 @@ k_gamma(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __r
   tile_store<R, IL>(buf, base, nc, g.sstride, N, astride, tx, IL ? TXR : cols, RS);
 }
 
+// bytes ahead of the tile in the TMA last-axis pass: twiddles, the sin and
+// cos tables of the last axis, rounded up to 128 bytes
+template <typename R>
+__host__ __device__ __forceinline__ size_t gamma_tma_head(int N) {
+  return (tw_bytes<R>(N) + 2 * (size_t)N * sizeof(R) + 127) & ~(size_t)127;
+}
+
 // The same last-axis pass in 3D with the tile moved by the tensor memory
 // accelerator: one box {TXR columns, NC components, one y plane, NAX z
 // points} lands as [z][c][col] (point stride NC TXR, no padding), and goes
@@ -848,7 +863,9 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
   extern __shared__ __align__(128) unsigned char smtma[];
   __shared__ __align__(8) uint64_t bar;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smtma);
-  C2<R>* buf = reinterpret_cast<C2<R>*>(smtma + ((tw_bytes<R>(NAX) + 127) & ~(size_t)127));
+  R* zs = reinterpret_cast<R*>(smtma + tw_bytes<R>(NAX));   // sin, cos of the last-axis modes
+  R* zc = zs + NAX;
+  C2<R>* buf = reinterpret_cast<C2<R>*>(smtma + gamma_tma_head<R>(NAX));
   const int q0 = blockIdx.x * TXR;
   const int cols = min(TXR, g.P1 - q0);
   if (threadIdx.x == 0) {
@@ -856,7 +873,11 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
     mbar_expect_tx(&bar, kBytes);
     tma_load_4d(buf, &tmap, q0 * U8, 0, blockIdx.y, 0, &bar);
   }
-  for (int i = threadIdx.x; i < NAX; i += kThreads) tws[i] = tw[i];
+  for (int i = threadIdx.x; i < NAX; i += kThreads) {
+    tws[i] = tw[i];
+    zs[i] = t.s[2][i];
+    zc[i] = t.c[2][i];
+  }
   __syncthreads();
   if (!mbar_wait(&bar, 0, kWaitNs)) {
     if (threadIdx.x == 0 && wait_err) atomicExch(wait_err, 1);
@@ -874,9 +895,9 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
 #pragma unroll 2
       for (int n = threadIdx.x / TXR; n < NAX; n += RPT) {
         R a[3];
-        C2<R> ph;
         bool dc;
-        sy.at(g, t, reg_freq<NAX>(n), a, ph, dc);
+        const int f = reg_freq<NAX>(n);
+        sy.at3(t, f, zs[f], zc[f], a, dc);
         C2<R> tv[NC];
 #pragma unroll
         for (int c = 0; c < NC; c++) tv[c] = buf[n * RS + c * TXR + col];
@@ -1405,16 +1426,17 @@ k_eps_update(Geo g, double* __restrict__ eps, const R* __restrict__ x, double* _
   const long long V = g.V;
   const int nc = g.nc;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  double mx[1] = {0.0};
+  R mxr = R(0);   // max |x| in the correction's own precision
   for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
     for (int c = 0; c < nc; c++) {
-      const double xv = x[c * V + v];
-      const double en = eps[c * V + v] + xv;
+      const R xr = x[c * V + v];
+      const double en = eps[c * V + v] + (double)xr;
       eps[c * V + v] = en;
       acc[c] += en;
-      mx[0] = fmax(mx[0], fabs(xv));
+      mxr = fmax(mxr, fabs(xr));
     }
   }
+  double mx[1] = {(double)mxr};
   block_sum_store<6>(acc, part, pstride);
   __syncthreads();
   block_max_store<1>(mx, part + 6 * (long long)pstride, pstride);
@@ -1699,7 +1721,7 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
     const CUtensorMap* map = tensor_map_8b(S, 4, dims, strides, box);
     if (map) {
       // column tiles up to P1 (inside the padded row: ps is a multiple of 16)
-      const size_t smt = ((tw_bytes<R>(si.N) + 127) & ~(size_t)127) + (size_t)si.N * 6 * TX6 * sizeof(C2<R>);
+      const size_t smt = gamma_tma_head<R>(si.N) + (size_t)si.N * 6 * TX6 * sizeof(C2<R>);
       dim3 gt((g.P1 + TX6 - 1) / TX6, g.n2, 1);
       auto launch = [&](auto k) {
         set_smem(k, smt);
