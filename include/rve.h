@@ -163,6 +163,22 @@ int rve_set_load_path(rve_t* h, int n_incr, const uint8_t strain_ctrl[6], const 
  * RVE_ERR_NUMERIC the state stays at the last converged increment. */
 int rve_step_increment(rve_t* h, rve_step_info* info);
 
+/* The next load increment with automatic cut-back of the strain increment
+ * (Section 4: a variable increment, reduced where the solution needs it,
+ * down to a minimum admissible size).  The path from the last converged
+ * (sub-)step to the increment's target is tried whole; on
+ * RVE_ERR_NOT_CONVERGED the state stays at the last converged sub-step and
+ * the sub-step is halved; after each converged sub-step it doubles again
+ * (capped by what is left).  Targets of both control kinds are interpolated
+ * linearly along the remaining path.  The sub-step never falls below
+ * 2^-max_cuts (0..60) of the path left at the call: then the call returns
+ * RVE_ERR_NOT_CONVERGED with the state at the last converged sub-step, and
+ * a later call (or rve_step_increment) continues from there.  info (may be
+ * NULL): the last sub-step's result with the iteration counts summed over
+ * every attempt; info->reserved receives the number of converged
+ * sub-steps.  Other errors are returned as they occur. */
+int rve_step_increment_adaptive(rve_t* h, int max_cuts, rve_step_info* info);
+
 /* Homogenised stress / strain (volume averages, Section 3.1) of the last
  * converged increment, tensor shears, host output. */
 int rve_homogenized_stress(const rve_t* h, double sigma[6]);

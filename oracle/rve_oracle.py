@@ -45,6 +45,13 @@ R1..R26 of the design notes):
       0.01 TOL_N sqrt(V) ||<sigma>||: the linear solve is not pushed below the
       accuracy the Newton test (R4) can use, where the right-hand side is
       dominated by the round-off of -G*(sigma - Sigma_bar).
+  R27 Increment cut-back (Section 4 applies a variable strain increment,
+      reduced where the solution needs it, down to a minimum admissible
+      size, without printing the rule): the remaining path of an increment
+      is tried whole; a solve that runs out of its Newton or staggered
+      budget halves the sub-step, a converged one doubles it again (capped
+      by what is left), targets are linear along the path, and the sub-step
+      never falls below 2^-max_cuts of the path.
   R20 Particle cracking (law 2; not in the paper, an extension of Section
       3.1's multi-variable framework): the local variable is the history
       kappa = max(kappa_n, ||<eps>_+||), the Euclidean norm of the positive
@@ -641,6 +648,38 @@ def homogenized_stress(st):
 def homogenized_strain(st):
     e = embed(st.eps, st.grid.d).mean(axis=0)
     return e / MANDEL_W
+
+
+def step_increment_adaptive(st, strain_ctrl, target_last, target, opt, max_cuts=7):
+    """One increment with cut-back (R27).  target_last: the targets of the
+    last converged (sub-)step; target: the increment's.  A failed sub-step
+    leaves the state untouched (step_increment commits only on success).
+    Returns (record of the last sub-step, converged sub-steps, targets
+    reached); raises RuntimeError when the sub-step would fall below
+    2^-max_cuts of the path, with the state at the last converged sub-step."""
+    T0 = np.asarray(target_last, dtype=np.float64)
+    T1 = np.asarray(target, dtype=np.float64)
+    n0 = st.n_done
+    frac, sub, subs = 0.0, 1.0, 0
+    last = T0.copy()
+    rec = None
+    while frac < 1.0:
+        fn = min(1.0, frac + sub)
+        T = T1.copy() if fn >= 1.0 else T0 + fn * (T1 - T0)
+        try:
+            rec = step_increment(st, strain_ctrl, last, T, opt)
+        except RuntimeError:
+            st.n_done = n0
+            if sub * 0.5 < 2.0 ** -max_cuts:
+                raise
+            sub *= 0.5
+            continue
+        frac = fn
+        subs += 1
+        sub *= 2.0
+        last = T
+    st.n_done = n0 + 1
+    return rec, subs, last
 
 
 def run_load_path(grid, phase_map, phase_dicts, ell, strain_ctrl, target, opt, n_incr=None,

@@ -87,6 +87,7 @@ _SIGNATURES = {
     "rve_set_phases": (_I, [_P, _P, _I, ctypes.POINTER(PhaseParams), ctypes.POINTER(_D)]),
     "rve_set_load_path": (_I, [_P, _I, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(_D)]),
     "rve_step_increment": (_I, [_P, ctypes.POINTER(StepInfo)]),
+    "rve_step_increment_adaptive": (_I, [_P, _I, ctypes.POINTER(StepInfo)]),
     "rve_homogenized_stress": (_I, [_P, ctypes.POINTER(_D)]),
     "rve_homogenized_strain": (_I, [_P, ctypes.POINTER(_D)]),
     "rve_get_field": (_I, [_P, _I, _P, ctypes.c_size_t]),
@@ -236,6 +237,19 @@ def rve_step_increment(h, raise_on_error=True):
         _check(s, "rve_step_increment")
     d = info.as_dict()
     d["status"] = s
+    return d
+
+
+def rve_step_increment_adaptive(h, max_cuts=7, raise_on_error=True):
+    """Next increment with cut-back; the result's "substeps" is the number of
+    converged sub-steps (info.reserved)."""
+    info = StepInfo()
+    s = lib().rve_step_increment_adaptive(h, int(max_cuts), ctypes.byref(info))
+    if raise_on_error:
+        _check(s, "rve_step_increment_adaptive")
+    d = info.as_dict()
+    d["status"] = s
+    d["substeps"] = d.pop("reserved")
     return d
 
 
@@ -445,6 +459,9 @@ class RVE:
 
     def step(self, raise_on_error=True):
         return rve_step_increment(self.h, raise_on_error)
+
+    def step_adaptive(self, max_cuts=7, raise_on_error=True):
+        return rve_step_increment_adaptive(self.h, max_cuts, raise_on_error)
 
     def stress(self):
         return rve_homogenized_stress(self.h)

@@ -98,6 +98,9 @@ struct rve {
   uint8_t ctrl[6] = {1, 1, 1, 1, 1, 1};
   std::vector<double> target;    // tensor shears
   double E_prev[6] = {0, 0, 0, 0, 0, 0};
+  // stress targets of the stress-controlled components at the last
+  // converged (sub-)step (interpolation origin of cut-back sub-steps)
+  double S_prev[6] = {0, 0, 0, 0, 0, 0};
   double smask_d[6] = {0, 0, 0, 0, 0, 0};
   float smask_f[6] = {0, 0, 0, 0, 0, 0};
   // FP64 state
@@ -673,13 +676,14 @@ struct Alg {
     return RVE_OK;
   }
 
-  // One load increment (Algorithm 1).
-  static int step(rve* h, rve_step_info* info) {
+  // One load increment (Algorithm 1) to target tg (null: the next target of
+  // the load path); advance: count it as the load path's next increment.
+  static int step(rve* h, rve_step_info* info, const double* tg_in = nullptr, bool advance = true) {
     const Geo& g = h->g;
     const Tables<R> t = tables<R>(h);
     const double sq2 = std::sqrt(2.0);
     const double W6[6] = {1, 1, 1, sq2, sq2, sq2};
-    const double* tg = &h->target[(size_t)h->n_done * 6];
+    const double* tg = tg_in ? tg_in : &h->target[(size_t)h->n_done * 6];
     double dE[6] = {0, 0, 0, 0, 0, 0}, sbar[6] = {0, 0, 0, 0, 0, 0};
     for (int c = 0; c < g.nc; c++) {
       const int m = g.cmap[c];
@@ -762,11 +766,13 @@ struct Alg {
     for (int c = 0; c < 6; c++) h->sig_mean[c] = h->hscal[OFF_SIGMEAN + c] / W6[c];
     for (int c = 0; c < 6; c++) h->eps_mean[c] = 0.0;
     for (int c = 0; c < g.nc; c++) h->eps_mean[g.cmap[c]] = h->hscal[OFF_ERRMEAN + c] / W6[g.cmap[c]];
-    for (int c = 0; c < 6; c++)
+    for (int c = 0; c < 6; c++) {
       if (h->ctrl[c]) h->E_prev[c] = tg[c];
+      else h->S_prev[c] = tg[c];
+    }
     h->D_mean = h->hscal[OFF_DMEAN];
     h->D_max = h->hscal[OFF_DMAX];
-    h->n_done++;
+    if (advance) h->n_done++;
     if (info) {
       info->status = RVE_OK;
       info->increment = h->n_done;
@@ -910,7 +916,7 @@ int reset_state(rve* h) {
   CK(cudaMemsetAsync(h->abar_new, 0, JV, h->st));
   CK(cudaStreamSynchronize(h->st));
   h->n_done = 0;
-  for (int c = 0; c < 6; c++) { h->E_prev[c] = 0; h->sig_mean[c] = 0; h->eps_mean[c] = 0; }
+  for (int c = 0; c < 6; c++) { h->E_prev[c] = 0; h->S_prev[c] = 0; h->sig_mean[c] = 0; h->eps_mean[c] = 0; }
   h->D_mean = h->D_max = 0;
   return RVE_OK;
 }
@@ -1158,6 +1164,7 @@ const char* rve_status_string(int s) {
     case RVE_ERR_NOT_CONVERGED: return "iteration budget exhausted";
     case RVE_ERR_NUMERIC: return "non-finite value or Krylov breakdown";
     case RVE_ERR_LOAD_PATH_END: return "load path finished";
+    case RVE_ERR_TIMEOUT: return "device wait for a tile copy timed out";
     default: return "unknown status";
   }
 }
@@ -1323,6 +1330,68 @@ int rve_step_increment(rve_t* h, rve_step_info* info) {
   } catch (...) {
     return RVE_ERR_OOM;
   }
+}
+
+int rve_step_increment_adaptive(rve_t* h, int max_cuts, rve_step_info* info) {
+  if (!h || max_cuts < 0 || max_cuts > 60) return RVE_ERR_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!h->phases_set || !h->path_set) return RVE_ERR_STATE;
+  if (h->n_done >= h->n_incr) return RVE_ERR_LOAD_PATH_END;
+  h->stepped = true;
+  // the remaining path of this increment: from the last converged
+  // (sub-)step's targets T0 to the increment's target T1
+  const double* T1 = &h->target[(size_t)h->n_done * 6];
+  double T0[6];
+  for (int c = 0; c < 6; c++) T0[c] = h->ctrl[c] ? h->E_prev[c] : h->S_prev[c];
+  const double min_step = std::ldexp(1.0, -max_cuts);
+  double f = 0.0, step = 1.0;
+  int subs = 0;
+  rve_step_info acc{}, sub{};
+  int s = RVE_OK;
+  try {
+    while (f < 1.0) {
+      const double fn = std::min(1.0, f + step);
+      double T[6];
+      for (int c = 0; c < 6; c++) T[c] = fn >= 1.0 ? T1[c] : T0[c] + fn * (T1[c] - T0[c]);
+      s = h->prec == RVE_MIXED ? Alg<float>::step(h, &sub, T, fn >= 1.0) : Alg<double>::step(h, &sub, T, fn >= 1.0);
+      acc.staggered_iters += sub.staggered_iters;
+      acc.newton_iters += sub.newton_iters;
+      acc.cg_iters += sub.cg_iters;
+      acc.pcg_iters += sub.pcg_iters;
+      acc.voxel_iterations += (double)h->g.V * (double)(sub.cg_iters + sub.pcg_iters);
+      if (s == RVE_OK) {
+        f = fn;
+        subs++;
+        step *= 2.0;   // grow back after a success (the next try is capped at the rest)
+      } else if (s == RVE_ERR_NOT_CONVERGED && step * 0.5 >= min_step) {
+        step *= 0.5;   // the state is at the last converged sub-step
+      } else {
+        break;
+      }
+    }
+  } catch (...) {
+    s = RVE_ERR_OOM;
+  }
+  if (info) {
+    *info = sub;   // the last sub-step (on failure: the attempt that failed)
+    if (s != RVE_OK) {
+      for (int c = 0; c < 6; c++) {
+        info->sigma[c] = h->sig_mean[c];
+        info->eps[c] = h->eps_mean[c];
+      }
+      info->D_mean = h->D_mean;
+      info->D_max = h->D_max;
+    }
+    info->status = s;
+    info->increment = s == RVE_OK ? h->n_done : h->n_done + 1;
+    info->staggered_iters = acc.staggered_iters;
+    info->newton_iters = acc.newton_iters;
+    info->cg_iters = acc.cg_iters;
+    info->pcg_iters = acc.pcg_iters;
+    info->voxel_iterations = acc.voxel_iterations;
+    info->reserved = subs;
+  }
+  return s;
 }
 
 int rve_homogenized_stress(const rve_t* h, double sigma[6]) {
@@ -1663,7 +1732,7 @@ void rve_batch_free(rve_batch_t* b) {
 // Saved converged state after n_done increments (restart point).
 struct AdjCkpt {
   int n_done = 0;
-  double E_prev[6], sig_mean[6], eps_mean[6], D_mean = 0, D_max = 0;
+  double E_prev[6], S_prev[6], sig_mean[6], eps_mean[6], D_mean = 0, D_max = 0;
   double *eps_conv = nullptr, *epsp_n = nullptr, *ep_n = nullptr, *abar_n = nullptr;
 };
 
@@ -1722,6 +1791,7 @@ int ckpt_save(rve* h, AdjCkpt& c) {
   c.n_done = h->n_done;
   for (int k = 0; k < 6; k++) {
     c.E_prev[k] = h->E_prev[k];
+    c.S_prev[k] = h->S_prev[k];
     c.sig_mean[k] = h->sig_mean[k];
     c.eps_mean[k] = h->eps_mean[k];
   }
@@ -1741,6 +1811,7 @@ int ckpt_load(rve* h, const AdjCkpt& c) {
   h->n_done = c.n_done;
   for (int k = 0; k < 6; k++) {
     h->E_prev[k] = c.E_prev[k];
+    h->S_prev[k] = c.S_prev[k];
     h->sig_mean[k] = c.sig_mean[k];
     h->eps_mean[k] = c.eps_mean[k];
   }
@@ -2030,9 +2101,10 @@ struct StateHeader {
   int n[3], nc;
   long long V;
   int n_done, pad;
-  double E_prev[6], sig_mean[6], eps_mean[6], D_mean, D_max;
+  double E_prev[6], S_prev[6], sig_mean[6], eps_mean[6], D_mean, D_max;
 };
 const char kStateMagic[8] = {'R', 'V', 'E', 'S', 'T', 'A', 'T', '1'};
+constexpr int kStateVersion = 2;
 }  // namespace
 
 long long rve_state_bytes(const rve_t* h) {
@@ -2046,7 +2118,7 @@ int rve_save_state(const rve_t* h, void* buf, long long bytes) {
   if (!h->phases_set) return RVE_ERR_STATE;
   StateHeader hd{};
   std::memcpy(hd.magic, kStateMagic, 8);
-  hd.version = 1;
+  hd.version = kStateVersion;
   hd.dim = h->dim;
   hd.prec = h->prec;
   hd.J = h->J;
@@ -2056,6 +2128,7 @@ int rve_save_state(const rve_t* h, void* buf, long long bytes) {
   hd.n_done = h->n_done;
   for (int c = 0; c < 6; c++) {
     hd.E_prev[c] = h->E_prev[c];
+    hd.S_prev[c] = h->S_prev[c];
     hd.sig_mean[c] = h->sig_mean[c];
     hd.eps_mean[c] = h->eps_mean[c];
   }
@@ -2081,7 +2154,7 @@ int rve_load_state(rve_t* h, const void* buf, long long bytes) {
   if (!h->phases_set) return RVE_ERR_STATE;
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != 1 || hd.dim != h->dim || hd.prec != h->prec ||
+  if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != kStateVersion || hd.dim != h->dim || hd.prec != h->prec ||
       hd.J != h->J || hd.nc != h->g.nc || hd.V != h->g.V || hd.n[0] != h->n[0] || hd.n[1] != h->n[1] ||
       hd.n[2] != h->n[2] || bytes < rve_state_bytes(h) || hd.n_done < 0)
     return RVE_ERR_ARG;
@@ -2099,6 +2172,7 @@ int rve_load_state(rve_t* h, const void* buf, long long bytes) {
   h->n_done = hd.n_done;
   for (int c = 0; c < 6; c++) {
     h->E_prev[c] = hd.E_prev[c];
+    h->S_prev[c] = hd.S_prev[c];
     h->sig_mean[c] = hd.sig_mean[c];
     h->eps_mean[c] = hd.eps_mean[c];
   }

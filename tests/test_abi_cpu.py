@@ -76,6 +76,8 @@ def test_argument_errors_without_device(pkg):
     assert lib.rve_create(ctypes.byref(h), 2, n, L, 0, 1, None) == pkg.RVE_ERR_ARG
     assert lib.rve_create(ctypes.byref(h), 4, n, L, 0, 1, None) == pkg.RVE_ERR_ARG
     assert lib.rve_step_increment(None, None) == pkg.RVE_ERR_ARG
+    assert lib.rve_step_increment_adaptive(None, 7, None) == pkg.RVE_ERR_ARG
+    assert pkg.rve_status_string(pkg.RVE_ERR_TIMEOUT) == "device wait for a tile copy timed out"
     lib.rve_free(None)
 
 
