@@ -176,6 +176,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the mixed-form kernel class, from one ncu full capture on the 256x128x256
+# sphere RVE (profiles/x1_cg_and_gamma_tma_passes_3d_spheres_256x128x256_mixed.md),
+# per voxel of that grid: the traffic grows in proportion to the voxels, so a
+# launch on V voxels moves V times this.  Valid for the kernels as captured.
+DRAM_BYTES_PER_VOXEL = {
+    "x1_inv_matvec": (830.541824e6 + 360.079360e6) / (256 * 128 * 256),   # k_xinv<EpiCG>
+    "x1_fwd_tangent": (475.303936e6 + 364.743680e6) / (256 * 128 * 256),  # k_xfwd<ProTangent>
+    "gamma_last_axis": (226.528512e6 + 161.263360e6) / (256 * 128 * 256),  # k_gamma_tma
+}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, rank, ws, dist):
     import torch
@@ -225,9 +237,14 @@ def run_ours(args, rank, ws, dist):
         except Exception:
             pass
     achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
+    # DRAM bytes per launch scaled from the smaller capture (3D, mixed form
+    # and the six-component kernels only)
+    traffic = None
+    if dom in DRAM_BYTES_PER_VOXEL and prec == pkg.RVE_MIXED and len(cfg.n) == 3:
+        traffic = round(DRAM_BYTES_PER_VOXEL[dom] * V)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                "traffic": None, "bytes_per_launch": dbytes / max(dlaunch, 1),
+                "traffic": traffic, "bytes_per_launch": dbytes / max(dlaunch, 1),
                 "avg_launch_ms": dms / max(dlaunch, 1), "launches": dlaunch,
                 "classes": {k: {"ms": round(v[0], 3), "launches": v[1],
                                 "GBps": round(v[2] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None}
