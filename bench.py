@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--curve", action="store_true",
+                    help="time the whole load path (cut-back steps) instead of the headline rate")
     ap.add_argument("--cpu-iters", type=int, default=1)
     ap.add_argument("--workload", default="spheres256", choices=["spheres256", "batch", "adjoint"],
                     help="batch: the 32-RVE {64,96,128}^3 two-variable workload; adjoint: gradients of "
@@ -533,9 +535,55 @@ def run_adjoint(args):
            "gradients": grads, "finite_differences": fd}
 
 
+def run_curve(args):
+    """Time to curve: the whole load path of the 256^3 workload (40 increments
+    of 1e-3) in the mixed form, each increment through the cut-back step
+    (halving on a Newton or staggered budget failure), timed on the device
+    from the first increment to the last."""
+    import torch
+    import paper_2103_04770_gb300 as pkg
+
+    torch.cuda.init()
+    stream = torch.cuda.current_stream()
+    cfg = workload(args.n, args.grid)
+    V = int(np.prod(cfg.n))
+    prec = pkg.RVE_MIXED if args.precision == "mixed" else pkg.RVE_FP64
+    r = pkg.RVE(cfg, precision=prec, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    curve, vi, status = [], 0.0, "ok"
+    for _ in range(cfg.target.shape[0]):
+        info = r.step_adaptive(max_cuts=7, raise_on_error=False)
+        if info["status"] != pkg.RVE_OK:
+            status = pkg.rve_status_string(info["status"])
+            break
+        vi += info["voxel_iterations"]
+        curve.append([round(info["eps"][0], 6), round(info["sigma"][0], 4), round(info["D_max"], 4),
+                      info["substeps"], int(info["cg_iters"]), int(info["pcg_iters"])])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    s = e0.elapsed_time(e1) * 1e-3
+    r.close()
+    peak = max(c[1] for c in curve) if curve else None
+    return {"metric": "time to curve, 256^3 sphere RVE, 40 increments to E11 = 4 %", "value": s, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64" if prec == pkg.RVE_MIXED else "f64",
+            "data": "synthetic", "config": workload_config(cfg, args.precision), "status": status,
+            "increments_done": len(curve), "wall_s": wall, "voxel_iterations": vi,
+            "voxel_iterations_per_s": vi / s if s > 0 else None, "peak_S11": peak,
+            "curve_columns": ["E11", "S11", "D_max", "substeps", "cg", "pcg"], "curve": curve}
+
+
 def main():
     args = parse()
     rank, ws, dist = dist_init()
+    if args.curve and args.impl == "ours":
+        if rank == 0:
+            print(json.dumps(run_curve(args)))
+        return
     if args.workload == "adjoint" and args.impl == "ours":
         if rank == 0:
             print(json.dumps(run_adjoint(args)))
