@@ -62,7 +62,12 @@ R1..R26 of the design notes):
 
 Parity: every function below is pinned by the CPU tests (closed forms,
 invariants, dense brute-force solves built from real-space stencils, finite
-differences); none is "parity unpinned".
+differences); none is "parity unpinned".  The staggered loop of Algorithm 1
+(step_increment: ERR, stopping rule and commit) is pinned on heterogeneous
+damaging cells by checking each committed increment against the monolithic
+system it must solve (equilibrium at D(abar), the Helmholtz equations, the
+macroscopic targets), with operators assembled from real-space stencils, by
+recomputing ERR from the iterates, and by mirror symmetry of centred cells.
 """
 from __future__ import annotations
 
@@ -240,14 +245,37 @@ def gamma_hat_apply(tau_hat, grid, stress_mask):
     return out
 
 
+# Threads of the FFT library step: None uses numpy's FFT (one thread); an
+# integer uses scipy.fft with that many worker threads.  Both are the same
+# discrete Fourier transform; only the library call differs.
+_FFT_WORKERS = None
+
+
+def set_fft_workers(n):
+    """Run the oracle's FFTs on ``n`` threads (scipy.fft), or on numpy's
+    single-threaded FFT when ``n`` is None.  Returns the previous value."""
+    global _FFT_WORKERS
+    old = _FFT_WORKERS
+    if n is not None:
+        import scipy.fft  # noqa: F401  (fail here, not inside a solve)
+    _FFT_WORKERS = None if n is None else int(n)
+    return old
+
+
 def fft_fields(f, grid):
     axes = tuple(range(grid.d))
-    return np.fft.fftn(f, axes=axes)
+    if _FFT_WORKERS is None:
+        return np.fft.fftn(f, axes=axes)
+    import scipy.fft
+    return scipy.fft.fftn(f, axes=axes, workers=_FFT_WORKERS)
 
 
 def ifft_fields(fh, grid):
     axes = tuple(range(grid.d))
-    return np.fft.ifftn(fh, axes=axes)
+    if _FFT_WORKERS is None:
+        return np.fft.ifftn(fh, axes=axes)
+    import scipy.fft
+    return scipy.fft.ifftn(fh, axes=axes, workers=_FFT_WORKERS)
 
 
 def G_apply(tau, grid, stress_mask):
@@ -572,11 +600,15 @@ def ell2_field(st, j):
     return (st.ell[j][st.phase] ** 2).reshape(st.grid.shape)
 
 
-def step_increment(st, strain_ctrl, target_prev, target, opt):
+def step_increment(st, strain_ctrl, target_prev, target, opt, trace=None):
     """One load increment n -> n+1 of Algorithm 1 (iterated staggered scheme).
 
     strain_ctrl: 6-vector, 1 where E_hk is prescribed, 0 where Sigma_HK is;
-    target_prev / target: tensor-shear 6-vectors of increment n and n+1."""
+    target_prev / target: tensor-shear 6-vectors of increment n and n+1.
+    trace: optional callable, given after every staggered iteration a dict
+    with the iteration count k, the strain and non-local iterates before and
+    after it (eps_prev, eps_new, abar_prev, abar_new) and the ERR it computed
+    (a read-only view for tests; nothing it returns is used)."""
     g = st.grid
     d = g.d
     comps = carried(d)
@@ -616,6 +648,9 @@ def step_increment(st, strain_ctrl, target_prev, target, opt):
             an = np.linalg.norm(abar_new[j])
             if an >= 1e-30:
                 err = max(err, float(np.linalg.norm(abar_new[j] - abar_k[j]) / an))
+        if trace is not None:
+            trace(dict(k=stag + 1, eps_prev=eps_k.copy(), eps_new=eps_new.copy(),
+                       abar_prev=abar_k.copy(), abar_new=abar_new.copy(), err=err))
         eps_k = eps_new
         abar_k = abar_new
         stag += 1
