@@ -44,14 +44,16 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--grid", default=None, help="N1,N2,N3 instead of the n^3 cube (profiling shapes)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="increments of the instrumented replay that gives the per-class times")
     ap.add_argument("--curve", action="store_true",
                     help="time the whole load path (cut-back steps) instead of the headline rate")
     ap.add_argument("--curve-incr", type=int, default=0, help="--curve: first K increments only (0: all)")
-    ap.add_argument("--cpu-iters", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--workload", default="spheres256", choices=["spheres256", "batch", "adjoint"],
                     help="batch: the 32-RVE {64,96,128}^3 two-variable workload; adjoint: gradients of "
                          "the final stress of the 96^3 two-variable RVE (each its own JSON line)")
@@ -179,19 +181,109 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the mixed-form kernel class, from one ncu full capture on the 256x128x256
-# sphere RVE (profiles/x1_cg_and_gamma_tma_passes_3d_spheres_256x128x256_mixed.md),
-# per voxel of that grid: the traffic grows in proportion to the voxels, so a
-# launch on V voxels moves V times this.  Valid for the kernels as captured.
-DRAM_BYTES_PER_VOXEL = {
-    "x1_inv_matvec": (830.541824e6 + 360.079360e6) / (256 * 128 * 256),   # k_xinv<EpiCG>
-    "x1_fwd_tangent": (475.303936e6 + 364.743680e6) / (256 * 128 * 256),  # k_xfwd<ProTangent>
-    "gamma_last_axis": (226.528512e6 + 161.263360e6) / (256 * 128 * 256),  # k_gamma_tma
-}
+# ------------------------------------------------------------------ traffic
+DEVICE_SOURCES = ["common.cuh", "fft.cuh", "fft256.cuh", "fft_ct.cuh", "ops.cuh", "tma.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_bytes_per_voxel.txt")
+
+
+def device_sources_sha16():
+    """Hash of the device sources whose kernels the DRAM counters describe."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_04770_gb300", "csrc")
+    for f in DEVICE_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_bytes_per_voxel():
+    """{class: DRAM bytes per voxel of one launch} from the committed record
+    of an ncu capture, or ({}, reason) when the kernels changed since."""
+    try:
+        lines = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
+        return {}, "no traffic record"
+    sha, grid, out = None, None, {}
+    for ln in lines:
+        t = ln.split()
+        if not t or t[0].startswith("#"):
+            continue
+        if t[0] == "kernel_sources_sha16":
+            sha = t[1]
+        elif t[0] == "capture_grid":
+            grid = [int(x) for x in t[1].split("x")]
+        elif len(t) == 4:
+            out[t[0]] = (float(t[2]) + float(t[3]))
+    if sha != device_sources_sha16() or not grid:
+        return {}, "kernels changed since the traffic record was captured"
+    V = float(np.prod(grid))
+    return {k: v / V for k, v in out.items()}, "ncu capture on %s, scaled by voxels" % "x".join(map(str, grid))
 
 
 # ------------------------------------------------------------------ ours
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def _pinned(nbytes):
+    import torch
+    try:
+        return torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
+    except RuntimeError:
+        return torch.empty(int(nbytes), dtype=torch.uint8)
+
+
+def cufft_comparison(cfg, stream, reps=10):
+    """cuFFT (torch.fft, timed comparison only): the six-component FP32 R2C
+    and C2R transforms of the 256^3 field, no operator between them, CUDA
+    events on the launching stream."""
+    import torch
+    n1, n2, n3 = cfg.n
+    x = torch.randn(6, n3, n2, n1, device="cuda", dtype=torch.float32)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=(n3, n2, n1), dim=(1, 2, 3))
+        a, b = _events(2)
+        a.record(stream)
+        for _ in range(reps):
+            X = torch.fft.rfftn(x, dim=(1, 2, 3))
+            y = torch.fft.irfftn(X, s=(n3, n2, n1), dim=(1, 2, 3))
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    err = float((y - x).abs().max())
+    del x, y, X
+    torch.cuda.empty_cache()
+    return ms, err
+
+
+def cg_iteration_ms(pkg, h, V, nc, iters=24):
+    """Device time of one fused mechanical CG iteration of the library
+    (x1 R2C with C_T : p and the curvature, y, z with G*, y, x1 C2R with the
+    CG step and (r, r)) through rve_op_cg on the handle's current tangent,
+    with b = G*(t) for a random t (so b lies in the range of G*)."""
+    import torch
+    t = torch.randn(nc, V, device="cuda", dtype=torch.float64)
+    b = torch.empty_like(t)
+    pkg.rve_op_apply_gamma(h, t, b)
+    x = torch.empty_like(t)
+    pkg.rve_op_cg(h, b, x, 1e-30, 2)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = _events(2)
+    e0.record(s)
+    it = pkg.rve_op_cg(h, b, x, 1e-30, iters)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    del t, b, x
+    torch.cuda.empty_cache()
+    return ms / max(it, 1), it
+
+
 def run_ours(args, rank, ws, dist):
     import torch
     import paper_2103_04770_gb300 as pkg
@@ -201,35 +293,62 @@ def run_ours(args, rank, ws, dist):
     stream = torch.cuda.current_stream()
     cfg = workload(args.n, args.grid)
     V = int(np.prod(cfg.n))
+    nc = 6 if len(cfg.n) == 3 else 3
     prec = pkg.RVE_MIXED if args.precision == "mixed" else pkg.RVE_FP64
+    K = args.steps
 
-    # -------- device-resident timing
+    # -------- device-resident timing: graph replay of the Krylov chunks on,
+    # no per-launch events in the timed region
     r = pkg.RVE(cfg, precision=prec, stream=stream)
+    pkg.rve_set_graphs(r.h, True)
     for _ in range(args.warmup):
         r.step()
+    nbytes = pkg.rve_state_bytes(r.h)
+    start_state = pkg.rve_save_state(r.h, _pinned(nbytes))        # before the timed increments
+    # like-for-like FP64 samples: the first, middle and last timed increment
+    samples = sorted({0, K // 2, K - 1}) if (not args.no_fp64 and prec == pkg.RVE_MIXED) else []
+    snaps = {i: _pinned(nbytes) for i in samples if i > 0}
     pkg.rve_profile_reset(r.h)
-    pkg.rve_profile(r.h, True)
     clocks = ClockSampler()
     if rank == 0:
         clocks.start(dev)
     barrier(dist)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev_a, ev_b = _events(K), _events(K)
+    e0, e1 = _events(2)
     e0.record(stream)
-    infos = [r.step() for _ in range(args.steps)]
+    infos = []
+    for i in range(K):
+        if i in snaps:
+            pkg.rve_save_state(r.h, snaps[i])                         # state before increment i
+        ev_a[i].record(stream)
+        infos.append(r.step())
+        ev_b[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(dist)
     ck = clocks.stop() if rank == 0 else None
     ms = e0.elapsed_time(e1)
-    prof = pkg.rve_profile_read(r.h)
-    pkg.rve_profile(r.h, False)
+    incr_ms = [a.elapsed_time(b) for a, b in zip(ev_a, ev_b)]
+    launches = pkg.rve_profile_read(r.h)
+    gpu_launches = int(sum(v[1] for v in launches.values()))
     vi = sum(i["voxel_iterations"] for i in infos)
     rate, ms_max = aggregate(dist, ms, vi)
-    r.close()
 
-    # -------- roofline of the dominant kernel class (live CUDA events)
+    # -------- per-class device time: an instrumented replay (CUDA events
+    # around every launch, direct launches) of the first timed increments
+    # from the saved state
+    pkg.rve_load_state(r.h, start_state)
+    pkg.rve_profile_reset(r.h)
+    pkg.rve_profile(r.h, True)
+    n_rep = min(args.profile_steps, K)
+    rep_infos = [r.step() for _ in range(n_rep)]
+    prof = pkg.rve_profile_read(r.h)
+    pkg.rve_profile(r.h, False)
+    replay_same = all(a["cg_iters"] == b["cg_iters"] and a["pcg_iters"] == b["pcg_iters"]
+                      for a, b in zip(rep_infos, infos))
+
+    # roofline of the dominant kernel class (its CUDA-event time in the replay)
     dom = max((k for k in prof if k not in ("finalize",)), key=lambda k: prof[k][0])
     dms, dlaunch, dbytes = prof[dom]
     peak, peak_src = HBM_FALLBACK_GBS, "fallback"
@@ -240,107 +359,123 @@ def run_ours(args, rank, ws, dist):
         except Exception:
             pass
     achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
-    # DRAM bytes per launch scaled from the smaller capture (3D, mixed form
-    # and the six-component kernels only)
+    bpv, traffic_note = dram_bytes_per_voxel()
     traffic = None
-    if dom in DRAM_BYTES_PER_VOXEL and prec == pkg.RVE_MIXED and len(cfg.n) == 3:
-        traffic = round(DRAM_BYTES_PER_VOXEL[dom] * V)
+    if dom in bpv and prec == pkg.RVE_MIXED and len(cfg.n) == 3:
+        traffic = round(bpv[dom] * V)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                "traffic": traffic, "bytes_per_launch": dbytes / max(dlaunch, 1),
+                "traffic": traffic, "traffic_source": traffic_note if traffic is not None else traffic_note,
+                "bytes_per_launch": dbytes / max(dlaunch, 1),
                 "avg_launch_ms": dms / max(dlaunch, 1), "launches": dlaunch,
+                "timing": "CUDA events around every launch of an instrumented replay of the first %d timed "
+                          "increments from the saved state (same iteration counts: %s)" % (n_rep, replay_same),
                 "classes": {k: {"ms": round(v[0], 3), "launches": v[1],
                                 "GBps": round(v[2] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None}
                             for k, v in prof.items() if v[1] > 0}}
-    gpu_launches = int(sum(v[1] for v in prof.values()))
 
     out = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+           "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if prec == pkg.RVE_MIXED else "f64", "data": "synthetic",
            "config": workload_config(cfg, args.precision), "roofline": roofline,
            "gpu_launches": gpu_launches, "clocks": ck,
-           "increments": [{"incr": i["increment"], "stag": i["staggered_iters"], "newton": i["newton_iters"],
-                           "cg": i["cg_iters"], "pcg": i["pcg_iters"], "S11": i["sigma"][0],
-                           "D_max": i["D_max"]} for i in infos]}
+           "timed_region": "increments %d..%d, graph replay of the Krylov chunks, no per-launch events; "
+                           "includes %d state snapshot(s) to pinned host memory for the FP64 samples"
+                           % (args.warmup + 1, args.warmup + K, len(snaps)),
+           "increments": [{"incr": i["increment"], "ms": round(t, 2) if t else None, "stag": i["staggered_iters"],
+                           "newton": i["newton_iters"], "cg": i["cg_iters"], "pcg": i["pcg_iters"],
+                           "S11": i["sigma"][0], "D_max": i["D_max"]} for i, t in zip(infos, incr_ms)]}
 
-    # -------- end to end through the public API with host buffers
+    # -------- cuFFT timed comparison beside one fused CG iteration
+    if not args.no_cufft and len(cfg.n) == 3:
+        cg_ms, cg_it = cg_iteration_ms(pkg, r.h, V, nc)
+        cf_ms, cf_err = cufft_comparison(cfg, stream)
+        out["cufft_comparison"] = {
+            "cufft_r2c_c2r_6comp_fp32_ms": round(cf_ms, 4), "cufft_roundtrip_max_abs_err": cf_err,
+            "ours_cg_iteration_ms": round(cg_ms, 4), "ours_cg_iterations_timed": cg_it,
+            "ours_over_cufft": round(cg_ms / cf_ms, 3),
+            "what": "cuFFT: torch.fft rfftn + irfftn of a (6, N3, N2, N1) FP32 field, nothing between; "
+                    "ours: one whole mechanical CG iteration (R2C with C_T:p and the curvature, y, z with "
+                    "G*, y, C2R with the CG step and (r, r)) timed through rve_op_cg"}
+    r.close()
+
+    # -------- plain FP64 GPU form on the same increments, each from the mixed
+    # run's converged state before it
+    if samples:
+        r3 = pkg.RVE(cfg, precision=pkg.RVE_FP64, stream=stream)
+        pkg.rve_set_graphs(r3.h, True)
+        r3.step()                                                     # kernels loaded, graphs captured
+        t64, vi64, tm, vim, errs, rows = 0.0, 0.0, 0.0, 0.0, [], []
+        for i in samples:
+            pkg.rve_load_state(r3.h, start_state if i == 0 else snaps[i])
+            a, b = _events(2)
+            torch.cuda.synchronize()
+            a.record(stream)
+            inf = r3.step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            t64 += t
+            vi64 += inf["voxel_iterations"]
+            tm += incr_ms[i]
+            vim += infos[i]["voxel_iterations"]
+            errs.append(abs(infos[i]["sigma"][0] - inf["sigma"][0]) / abs(inf["sigma"][0]))
+            rows.append({"incr": inf["increment"], "fp64_ms": round(t, 1), "mixed_ms": round(incr_ms[i], 1),
+                         "fp64_cg": inf["cg_iters"], "mixed_cg": infos[i]["cg_iters"], "fp64_pcg": inf["pcg_iters"],
+                         "mixed_pcg": infos[i]["pcg_iters"], "S11_fp64": inf["sigma"][0],
+                         "S11_mixed": infos[i]["sigma"][0], "D_max": inf["D_max"]})
+        r3.close()
+        for s in snaps.values():
+            del s
+        v64 = vi64 / (t64 * 1e-3)
+        vmix = vim / (tm * 1e-3)
+        out["fp64_form"] = {"value": v64, "unit": UNIT, "increments": rows,
+                            "mixed_same_increments": vmix, "mixed_over_fp64": vmix / v64,
+                            "time_ratio_fp64_over_mixed": t64 / tm,
+                            "sigma11_rel_err_mixed_vs_fp64": max(errs),
+                            "how": "each sampled increment solved by both forms from the same converged state "
+                                   "(the mixed run's, FP64 image), CUDA events around the increment"}
+
+    # -------- end to end through the public API with host buffers, the same
+    # increments: microstructure, load path and the converged state before
+    # the timed increments go host -> device inside the timed region
     if not args.no_e2e:
         r2 = pkg.RVE(cfg, precision=prec, stream=stream)
-        for _ in range(args.warmup):
-            r2.step()
+        pkg.rve_set_graphs(r2.h, True)
+        r2.step()                                                     # kernels loaded
         phase_host = np.ascontiguousarray(cfg.phase)
         barrier(dist)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pkg.rve_set_phases(r2.h, phase_host, cfg.params, cfg.ell)          # H2D of the microstructure
+        pkg.rve_set_phases(r2.h, phase_host, cfg.params, cfg.ell)    # H2D of the microstructure
         pkg.rve_set_load_path(r2.h, cfg.strain_ctrl, cfg.target)
+        pkg.rve_load_state(r2.h, start_state)                         # H2D of the converged state
         vi2 = 0.0
-        for _ in range(args.steps):
-            inf = pkg.rve_step_increment(r2.h)                             # D2H step record
-            s = pkg.rve_homogenized_stress(r2.h)                           # D2H result
+        s11 = []
+        for _ in range(K):
+            inf = pkg.rve_step_increment(r2.h)                        # D2H step record
+            s11.append(pkg.rve_homogenized_stress(r2.h)[0])           # D2H result
             vi2 += inf["voxel_iterations"]
         torch.cuda.synchronize()
         t2 = time.perf_counter() - t0
         t2 = allreduce(dist, t2, "max")
         vi2 = allreduce(dist, vi2, "sum")
         r2.close()
-        h2d = V + 6 * 8 * cfg.target.shape[0] + 64 * len(cfg.params) + 8 * cfg.ell.size
+        h2d = V + 6 * 8 * cfg.target.shape[0] + 64 * len(cfg.params) + 8 * cfg.ell.size + nbytes
         d2h = 208 + 48
-        out["e2e"] = {"value": vi2 / t2, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-                      "d2h_bytes_per_step": d2h, "includes": "rve_set_phases(host map) + "
-                      "rve_set_load_path + steps + rve_homogenized_stress per step", "s": t2}
-
-    # -------- plain FP64 GPU form on the same workload
-    if not args.no_fp64 and prec == pkg.RVE_MIXED and args.fp64_steps > 0:
-        r3 = pkg.RVE(cfg, precision=pkg.RVE_FP64, stream=stream)
-        for _ in range(args.warmup):
-            r3.step()
-        barrier(dist)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        inf3 = [r3.step() for _ in range(args.fp64_steps)]
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms3 = allreduce(dist, f0.elapsed_time(f1), "max")
-        vi3 = allreduce(dist, sum(i["voxel_iterations"] for i in inf3), "sum")
-        s64 = [i["sigma"][0] for i in inf3]
-        r3.close()
-        # homogenised-stress error of the mixed form against the FP64 form on
-        # the same increments (the mixed run's increments warmup+1..)
-        s_mixed = [i["sigma"][0] for i in infos[:args.fp64_steps]]
-        err = max(abs(a - b) for a, b in zip(s_mixed, s64)) / max(abs(x) for x in s64)
-        out["fp64_form"] = {"value": vi3 / (ms3 * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
-                            "ms_per_step": ms3 / args.fp64_steps,
-                            "mixed_over_fp64": out["value"] / (vi3 / (ms3 * 1e-3)),
-                            "sigma11_rel_err_mixed_vs_fp64": err}
+        out["e2e"] = {"value": vi2 / t2, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+                      "d2h_bytes_per_step": d2h, "s": t2,
+                      "includes": "rve_set_phases(host map) + rve_set_load_path + rve_load_state(host image "
+                                  "of the state before increment %d) + the same %d increments + "
+                                  "rve_homogenized_stress per step" % (args.warmup + 1, K),
+                      "same_S11_as_device_timed": bool(np.allclose(s11, [i["sigma"][0] for i in infos],
+                                                                   rtol=1e-12, atol=0))}
+    del start_state
     return out, cfg
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(cfg, iters):
-    """Bounded sample of the same workload on the host with the FP64 oracle:
-    the first increment's return map and residual, then `iters` mechanical
-    CG iterations at full size.  Returns (voxel-iterations/s, seconds)."""
-    from oracle import rve_oracle as O
-    g = O.Grid(cfg.n, cfg.L)
-    st = O.make_state(g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
-    ctrl_c = cfg.strain_ctrl.astype(float)
-    mask = 1.0 - ctrl_c
-    tm = O.to_mandel_target(cfg.target[0])
-    eps = (st.eps + ctrl_c * tm).reshape(g.shape + (6,))
-    rm = O.return_map(eps.reshape(g.V, 6), st.epsp, st.ep, st.abar, st.phase, st.phases)
-    sig = rm["sigma"].reshape(g.shape + (6,))
-    C = rm["C"].reshape(g.shape + (6, 6))
-    res = -O.G_apply(sig - mask * tm, g, mask)
-    t0 = time.perf_counter()
-    O.cg(lambda x: O.G_apply(np.einsum("...ij,...j->...i", C, x), g, mask), res, 1e-30, iters)
-    t = time.perf_counter() - t0
-    return g.V * iters / t, t
-
-
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -348,37 +483,89 @@ def cpu_threads():
         return os.cpu_count()
 
 
+class OracleNewtonSample:
+    """A bounded sample of the workload on the host with the FP64 oracle as
+    it stands: the first Newton iteration of the first increment (the return
+    map of every voxel at the initial guess, the residual -G*(sigma -
+    Sigma_bar), then mechanical CG iterations of G*(C_T : d eps) = residual),
+    at full size.  The FFT library step runs on ``threads`` host threads
+    (scipy.fft); the oracle's other numpy steps run on one."""
+
+    def __init__(self, cfg, threads):
+        from oracle import rve_oracle as O
+        self.O = O
+        self.threads = threads
+        O.set_fft_workers(threads)
+        self.g = O.Grid(cfg.n, cfg.L)
+        self.st = O.make_state(self.g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
+        self.cfg = cfg
+
+    def newton_setup(self):
+        """Return map and residual; sets the CG operator and right-hand side."""
+        O, g, st, cfg = self.O, self.g, self.st, self.cfg
+        ctrl_c = cfg.strain_ctrl.astype(float)[O.carried(g.d)]
+        self.mask = 1.0 - ctrl_c
+        tm = O.to_mandel_target(cfg.target[0])[O.carried(g.d)]
+        eps = st.eps + ctrl_c * tm
+        rm = O.return_map(O.embed(eps, g.d), st.epsp, st.ep, st.abar, st.phase, st.phases)
+        comps = O.carried(g.d)
+        sig = rm["sigma"][:, comps].reshape(g.shape + (len(comps),))
+        self.C = rm["C"][:, comps][:, :, comps].reshape(g.shape + (len(comps), len(comps)))
+        self.res = -O.G_apply(sig - self.mask * tm, g, self.mask)
+
+    def cg(self, iters):
+        O, g = self.O, self.g
+        O.cg(lambda x: O.G_apply(np.einsum("...ij,...j->...i", self.C, x), g, self.mask), self.res, 1e-30,
+             iters)
+
+    def close(self):
+        self.O.set_fft_workers(None)
+
+
+def oracle_sample(cfg, iters, threads):
+    """Timed sample: return map + residual + `iters` CG iterations of the
+    first Newton iteration.  Returns (voxel-iterations/s, seconds)."""
+    smp = OracleNewtonSample(cfg, threads)
+    try:
+        t0 = time.perf_counter()
+        smp.newton_setup()
+        smp.cg(iters)
+        t = time.perf_counter() - t0
+    finally:
+        smp.close()
+    return smp.g.V * iters / t, t
+
+
 def run_reference(args, rank, ws, dist):
-    """The oracle, as it stands, on the host cores: each step is one
-    mechanical CG iteration of the oracle on the full workload."""
+    """The oracle, as it stands, on the host cores (FFTs on every host
+    thread): the timed run is the first Newton iteration of the first
+    increment on the full workload, its return map and residual once, then
+    one mechanical CG iteration per step."""
     cfg = workload(args.n, args.grid)
     if rank != 0:
         return None, cfg
-    from oracle import rve_oracle as O
-    g = O.Grid(cfg.n, cfg.L)
-    st = O.make_state(g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
-    ctrl_c = cfg.strain_ctrl.astype(float)
-    mask = 1.0 - ctrl_c
-    tm = O.to_mandel_target(cfg.target[0])
-    eps = (st.eps + ctrl_c * tm).reshape(g.shape + (6,))
-    rm = O.return_map(eps.reshape(g.V, 6), st.epsp, st.ep, st.abar, st.phase, st.phases)
-    sig = rm["sigma"].reshape(g.shape + (6,))
-    C = rm["C"].reshape(g.shape + (6, 6))
-    res = -O.G_apply(sig - mask * tm, g, mask)
-    A = lambda x: O.G_apply(np.einsum("...ij,...j->...i", C, x), g, mask)  # noqa: E731
-    for _ in range(args.warmup):
-        O.cg(A, res, 1e-30, 1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.cg(A, res, 1e-30, 1)
-    t = time.perf_counter() - t0
-    v = g.V * args.steps / t
-    sample = "one FP64 oracle CG iteration (G*(C_T:p) + update) per step on the full 256^3 workload"
+    th = cpu_threads()
+    smp = OracleNewtonSample(cfg, th)
+    try:
+        smp.newton_setup()
+        smp.cg(args.warmup)                      # warm-up (untimed)
+        t0 = time.perf_counter()
+        smp.newton_setup()
+        for _ in range(args.steps):
+            smp.cg(1)
+        t = time.perf_counter() - t0
+    finally:
+        smp.close()
+    V = smp.g.V
+    v = V * args.steps / t
+    sample = ("first Newton iteration of increment 1 on the full %s workload: return map + residual "
+              "-G*(sigma - Sigma_bar) once, then one FP64 oracle CG iteration per step; FFTs on %d threads "
+              "(scipy.fft), other numpy steps on one" % ("x".join(map(str, cfg.n)), th))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": workload_config(cfg, "fp64 (CPU oracle)"),
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+           "data": "synthetic", "config": workload_config(cfg, args.precision),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample,
                             "host_threads": cpu_threads()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return out, cfg
@@ -610,11 +797,13 @@ def main():
     out, cfg = run_ours(args, rank, ws, dist)
     if rank == 0:
         if not args.no_cpu and ws == 1:
-            v, t = oracle_sample(cfg, args.cpu_iters)
-            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": "%d FP64 oracle CG iteration(s) of the first increment on the "
-                                             "full 256^3 workload (%.1f s; numpy FFT, single thread)"
-                                             % (args.cpu_iters, t),
+            th = cpu_threads()
+            v, t = oracle_sample(cfg, args.cpu_iters, th)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+                                   "sample": "first Newton iteration of increment 1 on the full %s workload: "
+                                             "return map + residual + %d FP64 oracle CG iteration(s), all "
+                                             "timed (%.1f s); FFTs on %d threads (scipy.fft), other numpy "
+                                             "steps on one" % ("x".join(map(str, cfg.n)), args.cpu_iters, t, th),
                                    "host_threads": cpu_threads()}
         print(json.dumps(out))
     if dist is not None:

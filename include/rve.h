@@ -260,9 +260,11 @@ int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, d
  * The converged state after the last increment (strain, plastic strain,
  * local history variable, non-local variables and the homogenised values)
  * as a self-describing byte image, so a long load path can be saved and
- * resumed (also on another handle of the same grid, form and variable
- * count; the phases, options and load path are not part of the image and
- * must be set on the target handle).  FP64 in both forms. */
+ * resumed (also on another handle of the same grid and variable count; the
+ * phases, options and load path are not part of the image and must be set
+ * on the target handle).  The image is FP64 in both forms, so an image
+ * written by a mixed-precision handle loads into an FP64 handle and the
+ * other way round. */
 
 /* Bytes of the image of this handle (header + (nc + 7 + J) V doubles). */
 long long rve_state_bytes(const rve_t* h);
@@ -274,7 +276,7 @@ int rve_save_state(const rve_t* h, void* buf, long long bytes);
 
 /* Restore an image written by rve_save_state: the next rve_step_increment
  * solves increment (saved count + 1) of the handle's load path.  The image's
- * grid, form and variable count must match the handle.
+ * grid and variable count must match the handle.
  * Errors: RVE_ERR_ARG (NULL, size or header mismatch), RVE_ERR_STATE
  * (phases not set), RVE_ERR_CUDA. */
 int rve_load_state(rve_t* h, const void* buf, long long bytes);
@@ -397,7 +399,7 @@ int rve_adjoint_backward(rve_t* h, double dJ, double* grad_params, double* grad_
  * cudaMalloc calls, or a plug-in running inside a host framework that owns
  * the device's memory.  Such a caller cannot create a handle (rve_create
  * allocates), so this call computes the same out = G*(tau) as
- * rve_op_apply_gamma (Eq. eqdiscrete2, FP64) without one, and allocates
+ * rve_op_apply_gamma (FP64) without one, and allocates
  * nothing: its half-spectrum scratch (32 MiB) and its FFT tables sit in
  * static device arrays that every GPU which loads the library holds until
  * the process exits.
@@ -412,12 +414,17 @@ int rve_adjoint_backward(rve_t* h, double dJ, double* grad_params, double* grad_
  *    rounded up to 16) exceeds 32 MiB, e.g. beyond 64^3 in 3D, are rejected
  *    with RVE_ERR_ARG before any device work.
  *  - The first call on a device (with that device current) looks up the
- *    static arrays' device addresses; make that first call before any stream
- *    capture.
- *  - Every call shares the same static scratch and tables, which keep the
- *    last call's contents: calls that overlap on the GPU (other streams,
- *    other host threads) race and must be serialised by the caller.
- * Errors: RVE_ERR_ARG, RVE_ERR_CUDA. */
+ *    static arrays' device addresses.  Every call copies the grid's tables
+ *    from host memory and synchronises the stream, so the call must not be
+ *    made while its stream (or, in global capture mode, any stream) is being
+ *    captured into a CUDA graph.
+ *  - Every call shares the same static scratch, tables and wait flag, which
+ *    keep the last call's contents (the call clears the flag itself): calls
+ *    that overlap on the GPU (other streams, other host threads) race and
+ *    must be serialised by the caller.
+ * Errors: RVE_ERR_ARG, RVE_ERR_CUDA, RVE_ERR_TIMEOUT (a tile copy of the 3D
+ * projection pass did not arrive within its wait budget; out is then
+ * incomplete). */
 int rve_op_apply_gamma_noalloc(int dim, const int n[3], const double L[3], const uint8_t strain_ctrl[6],
                                const double* tau, double* out, void* cuda_stream);
 

@@ -329,17 +329,42 @@ def rve_state_bytes(h):
     return int(lib().rve_state_bytes(h))
 
 
-def rve_save_state(h):
-    """The converged state as bytes (see rve_save_state in rve.h)."""
+def _host_buffer(buf):
+    """(address, bytes) of a writable C-contiguous host buffer: a numpy
+    array or a CPU torch tensor (pinned or not)."""
+    if hasattr(buf, "data_ptr"):
+        if buf.is_cuda or not buf.is_contiguous():
+            raise ValueError("expected a contiguous host tensor")
+        return buf.data_ptr(), buf.numel() * buf.element_size()
+    a = np.asarray(buf)
+    if not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous host array")
+    return a.ctypes.data, a.nbytes
+
+
+def rve_save_state(h, out=None):
+    """The converged state (see rve_save_state in rve.h): as bytes, or
+    written into the host buffer ``out`` (numpy array or CPU tensor of at
+    least rve_state_bytes bytes), which is returned."""
     n = lib().rve_state_bytes(h)
-    buf = ctypes.create_string_buffer(int(n))
-    _check(lib().rve_save_state(h, ctypes.cast(buf, ctypes.c_void_p), n), "rve_save_state")
-    return buf.raw
+    if out is None:
+        buf = ctypes.create_string_buffer(int(n))
+        _check(lib().rve_save_state(h, ctypes.cast(buf, ctypes.c_void_p), n), "rve_save_state")
+        return buf.raw
+    addr, nb = _host_buffer(out)
+    _check(lib().rve_save_state(h, ctypes.c_void_p(addr), nb), "rve_save_state")
+    return out
 
 
 def rve_load_state(h, data):
-    buf = ctypes.create_string_buffer(bytes(data), len(data))
-    _check(lib().rve_load_state(h, ctypes.cast(buf, ctypes.c_void_p), len(data)), "rve_load_state")
+    """Restore a state image: bytes, or a host buffer (numpy array or CPU
+    tensor) read in place."""
+    if isinstance(data, (bytes, bytearray)):
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        _check(lib().rve_load_state(h, ctypes.cast(buf, ctypes.c_void_p), len(data)), "rve_load_state")
+        return
+    addr, nb = _host_buffer(data)
+    _check(lib().rve_load_state(h, ctypes.c_void_p(addr), nb), "rve_load_state")
 
 
 # ------------------------------------------------------------- adjoint

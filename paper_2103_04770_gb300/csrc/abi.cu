@@ -2154,7 +2154,7 @@ int rve_load_state(rve_t* h, const void* buf, long long bytes) {
   if (!h->phases_set) return RVE_ERR_STATE;
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != kStateVersion || hd.dim != h->dim || hd.prec != h->prec ||
+  if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != kStateVersion || hd.dim != h->dim ||
       hd.J != h->J || hd.nc != h->g.nc || hd.V != h->g.V || hd.n[0] != h->n[0] || hd.n[1] != h->n[1] ||
       hd.n[2] != h->n[2] || bytes < rve_state_bytes(h) || hd.n_done < 0)
     return RVE_ERR_ARG;

@@ -28,6 +28,9 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 static __device__ __align__(256) C2<double> g_tw[3][kMaxAxis];
 static __device__ __align__(256) double g_s[3][kMaxAxis];
 static __device__ __align__(256) double g_c[3][kMaxAxis];
+// set by a CTA of the 3D projection pass whose tile copy did not arrive
+// within its wait budget
+static __device__ __align__(256) int g_wait_flag;
 
 struct DevSymbols {
   bool ready = false;
@@ -35,6 +38,7 @@ struct DevSymbols {
   C2<double>* tw = nullptr;
   double* s = nullptr;
   double* c = nullptr;
+  int* wait_flag = nullptr;
 };
 
 std::mutex g_mutex;
@@ -52,7 +56,8 @@ int symbols_for_current_device(DevSymbols** out) {
     if (cudaGetSymbolAddress(&d.scratch, g_scratch) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.tw, g_tw) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.s, g_s) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&d.c, g_c) != cudaSuccess) {
+        cudaGetSymbolAddress((void**)&d.c, g_c) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&d.wait_flag, g_wait_flag) != cudaSuccess) {
       cudaGetLastError();
       return RVE_ERR_CUDA;
     }
@@ -179,12 +184,22 @@ extern "C" int rve_op_apply_gamma_noalloc(int dim, const int n[3], const double 
   for (int c = 0; c < 6; c++) mask[c] = c < nc ? (strain_ctrl[g.cmap[c]] ? 0.f : 1.f) : 0.f;
   int map[6] = {0, 1, 2, 3, 4, 5};
   C2<double>* S = (C2<double>*)sym->scratch;
+  // the flag keeps the last call's value: clear it before this call's sweep
+  if (cudaMemsetAsync(sym->wait_flag, 0, sizeof(int), st) != cudaSuccess) {
+    cudaGetLastError();
+    return RVE_ERR_CUDA;
+  }
   Ops<double>::xfwd_field64(g, t, lc, st, tau, nc, map, nullptr, S);
   if (dim == 3) Ops<double>::strided_plain(g, t, lc, st, S, nc, 1, -1, nullptr);
-  Ops<double>::gamma(g, t, lc, st, S, mask, 0, nullptr);
+  Ops<double>::gamma(g, t, lc, st, S, mask, 0, nullptr, sym->wait_flag);
   if (dim == 3) Ops<double>::strided_plain(g, t, lc, st, S, nc, 1, +1, nullptr);
   Ops<double>::xinv_store64(g, t, lc, st, S, nc, out);
+  int waited_out = 0;
   if (cudaGetLastError() != cudaSuccess) return RVE_ERR_CUDA;
+  if (cudaMemcpyAsync(&waited_out, sym->wait_flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    cudaGetLastError();
+    return RVE_ERR_CUDA;
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return RVE_ERR_CUDA;
-  return RVE_OK;
+  return waited_out ? RVE_ERR_TIMEOUT : RVE_OK;
 }

@@ -191,7 +191,16 @@ def test_save_and_resume_state(prec):
         assert info["cg_iters"] == c0
         np.testing.assert_array_equal(s0, s1)
     assert res[0][0]["increment"] == 3
-    with pkg.RVE(cfg, precision=1 - prec) as r3:     # form mismatch is rejected
+    # the image is FP64 in both forms: the other form resumes from it and
+    # agrees with this form's continuation to the mixed-form tolerance
+    with pkg.RVE(cfg, precision=1 - prec) as r3:
+        pkg.rve_load_state(r3.h, img)
+        info = r3.step()
+        assert info["increment"] == 3
+        s3 = r3.stress()
+        assert np.abs(s3 - cont[0][1]).max() <= 1e-4 * abs(cont[0][1][0])
+    other = _member((12, 12, 16), 0.2, 2, 7, n_incr=4, prec=prec)
+    with pkg.RVE(other, precision=prec) as r4:       # grid mismatch is rejected
         with pytest.raises(pkg.RVEError) as e:
-            pkg.rve_load_state(r3.h, img)
+            pkg.rve_load_state(r4.h, img)
         assert e.value.status == pkg.RVE_ERR_ARG
