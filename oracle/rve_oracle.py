@@ -297,6 +297,8 @@ class Phase:
     eps_R: float = 1.0
     D_max: float = 0.0
     var: int = -1           # non-local variable fed/read by this phase
+    hard: int = 0           # flow stress: 0 linear sigma_y + H e, 1 Aravas power law (Eq. aravas)
+    N: float = 0.1          # Aravas exponent
 
     @property
     def K(self):
@@ -307,9 +309,47 @@ class Phase:
         return self.E / (2.0 * (1.0 + self.nu))
 
 
+PHASE_KEYS = ("E", "nu", "sigma_y", "H", "law", "eps_C", "eps_R", "D_max", "var")
+PHASE_OPTIONAL = ("hard", "N")
+
+
 def phases_from_dicts(ds):
-    return [Phase(**{k: d[k] for k in ("E", "nu", "sigma_y", "H", "law", "eps_C",
-                                       "eps_R", "D_max", "var")}) for d in ds]
+    return [Phase(**{k: d[k] for k in PHASE_KEYS}, **{k: d[k] for k in PHASE_OPTIONAL if k in d})
+            for d in ds]
+
+
+def _bisect_increasing(g, lo, hi, iters=200):
+    """Root of the increasing function g on [lo, hi] (arrays, g(lo) <= 0 <=
+    g(hi)) by bisection, element-wise."""
+    lo = np.array(lo, dtype=np.float64, copy=True)
+    hi = np.array(hi, dtype=np.float64, copy=True)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        up = g(mid) > 0.0
+        hi = np.where(up, mid, hi)
+        lo = np.where(up, lo, mid)
+    return 0.5 * (lo + hi)
+
+
+def flow_stress(ph, e0):
+    """Matrix flow stress sigma_0 and its slope d sigma_0 / d e0 at the
+    equivalent plastic strain e0 (array).
+
+    hard 0: linear hardening sigma_0 = sigma_y + H e0 (Section 4).
+    hard 1: Aravas power law of Section 4.1 (Eq. aravas),
+        sigma_0 / sigma_y = (sigma_0 / sigma_y + 3 mu e0 / sigma_y)^N,
+    with mu the phase's shear modulus: y = sigma_0 / sigma_y solves
+    g(y) = y - (y + c)^N = 0, c = 3 mu e0 / sigma_y, which is increasing in
+    y (g' >= 1 - N) with g(1) <= 0 and g((1 + c)^(N/(1-N))) >= 0; the slope
+    follows from differentiating the implicit law."""
+    e0 = np.asarray(e0, dtype=np.float64)
+    if ph.hard == 0:
+        return ph.sigma_y + ph.H * e0, np.full(e0.shape, float(ph.H))
+    c = 3.0 * ph.mu * e0 / ph.sigma_y
+    N = ph.N
+    y = _bisect_increasing(lambda y: y - (y + c) ** N, np.ones(e0.shape), (1.0 + c) ** (N / (1.0 - N)))
+    w = N * (y + c) ** (N - 1.0)
+    return ph.sigma_y * y, 3.0 * ph.mu * w / (1.0 - w)
 
 
 def damage_of(abar, ph):
@@ -345,8 +385,11 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None):
       D = clamp((abar - eps_C) / (eps_R - eps_C), 0, D_max)
       sigma = (1 - D) sigma_eff
       C = (1 - D) [K I(x)I + 2 mu theta P_dev - 2 mu thetabar nhat(x)nhat]
-          theta = 1 - 2 mu dlambda / q, thetabar = 1/(1 + H/(3 mu)) - (1 - theta)
-    (the consistent tangent of radial return with linear isotropic hardening).
+          theta = 1 - 2 mu dlambda / q, thetabar = 1/(1 + H'/(3 mu)) - (1 - theta)
+    (the consistent tangent of radial return with isotropic hardening, H' the
+    slope of the flow stress at the end point).  With the Aravas flow stress
+    (hard 1) sigma_y + H ep_n above reads sigma_0(ep_n) and dlambda solves
+    q - 2 mu dlambda - sqrt(2/3) sigma_0(ep_n + sqrt(2/3) dlambda) = 0.
     Particle cracking (law 2, R20): kappa = max(kappa_n, ||<e>_+||) is kept
     in the ep slot, D from abar of the phase's variable, sigma = (1 - D) C e.
     stiff: optional (V,) field scaling the Young's modulus voxel by voxel
@@ -378,16 +421,26 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None):
         nhat = np.zeros_like(s_tr)
         sig_eff = sig_tr
         if ph.law == 1:
-            f = qn - math.sqrt(2.0 / 3.0) * (ph.sigma_y + ph.H * ep_n[sel])
+            s23 = math.sqrt(2.0 / 3.0)
+            f = qn - s23 * flow_stress(ph, ep_n[sel])[0]
             pl = f > 0.0
-            dl = np.where(pl, f / (2.0 * mu + 2.0 * ph.H / 3.0), 0.0)
+            if ph.hard == 0:
+                dl = np.where(pl, f / (2.0 * mu + 2.0 * ph.H / 3.0), 0.0)
+            else:
+                # nonlinear hardening: q - 2 mu dl - sqrt(2/3) sigma_0(ep_n +
+                # sqrt(2/3) dl) = 0 is decreasing in dl, positive at 0 and
+                # negative at q / (2 mu)
+                dl = np.where(pl, _bisect_increasing(
+                    lambda x: -(qn - 2.0 * mu * x - s23 * flow_stress(ph, ep_n[sel] + s23 * x)[0]),
+                    np.zeros(qn.shape), qn / (2.0 * mu)), 0.0)
+            Hp = flow_stress(ph, ep_n[sel] + s23 * dl)[1]      # slope at the end point
             safe_q = np.where(pl, qn, 1.0)
             nhat = np.where(pl[:, None], s_tr / safe_q[:, None], 0.0)
             epsp[sel] = epsp_n[sel] + dl[:, None] * nhat
-            ep[sel] = ep_n[sel] + math.sqrt(2.0 / 3.0) * dl
+            ep[sel] = ep_n[sel] + s23 * dl
             sig_eff = sig_tr - 2.0 * mu[:, None] * dl[:, None] * nhat
             theta = np.where(pl, 1.0 - 2.0 * mu * dl / safe_q, 1.0)
-            thetabar = np.where(pl, 1.0 / (1.0 + ph.H / (3.0 * mu)) - (1.0 - theta), 0.0)
+            thetabar = np.where(pl, 1.0 / (1.0 + Hp / (3.0 * mu)) - (1.0 - theta), 0.0)
             Dq = damage_of(abar[ph.var][sel], ph) if ph.var >= 0 else np.zeros(qn.shape)
             D[sel] = Dq
             if ph.var >= 0:
