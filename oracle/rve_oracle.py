@@ -299,6 +299,17 @@ class Phase:
     var: int = -1           # non-local variable fed/read by this phase
     hard: int = 0           # flow stress: 0 linear sigma_y + H e, 1 Aravas power law (Eq. aravas)
     N: float = 0.1          # Aravas exponent
+    # Gurson-Tvergaard-Needleman (law 3, Section 2.1.1; defaults of Section 4.1)
+    q1: float = 1.5
+    q2: float = 1.0
+    q3: float = 2.25
+    f_C: float = 0.15       # onset of coalescence
+    f_F: float = 0.25       # porosity at fracture
+    f_N: float = 0.04       # Chu-Needleman nucleation amplitude
+    eps_N: float = 0.3
+    s_N: float = 0.1
+    f0: float = 0.0         # initial porosity
+    fstar_max: float = 0.6  # cap on f* (Section 4: 0.9 f_V*)
 
     @property
     def K(self):
@@ -310,7 +321,7 @@ class Phase:
 
 
 PHASE_KEYS = ("E", "nu", "sigma_y", "H", "law", "eps_C", "eps_R", "D_max", "var")
-PHASE_OPTIONAL = ("hard", "N")
+PHASE_OPTIONAL = ("hard", "N", "q1", "q2", "q3", "f_C", "f_F", "f_N", "eps_N", "s_N", "f0", "fstar_max")
 
 
 def phases_from_dicts(ds):
@@ -352,6 +363,138 @@ def flow_stress(ph, e0):
     return ph.sigma_y * y, 3.0 * ph.mu * w / (1.0 - w)
 
 
+def _flow_value(ph, e0):
+    """sigma_0(e0) for real or complex-step arguments: a complex e0 = a + i b
+    (b the complex-step perturbation) maps to sigma_0(a) + i b sigma_0'(a),
+    the first-order expansion that complex-step differentiation evaluates."""
+    if np.iscomplexobj(e0):
+        s0, hp = flow_stress(ph, e0.real)
+        return s0 + 1j * e0.imag * hp
+    return flow_stress(ph, e0)[0]
+
+
+def gtn_fV(ph):
+    """Porosity at which the GTN surface shrinks to the origin (Section
+    2.1.1): f_V* = (q1 + sqrt(q1^2 - q3)) / q3."""
+    return (ph.q1 + math.sqrt(ph.q1 ** 2 - ph.q3)) / ph.q3
+
+
+def gtn_fstar(f, ph):
+    """Effective porosity f*(f) (Eq. effective_porosity), clamped to
+    [0, fstar_max] (Section 4 caps it at 0.9 f_V*)."""
+    fv = gtn_fV(ph)
+    fs = np.where(f < ph.f_C, f, np.where(f < ph.f_F, ph.f_C + (fv - ph.f_C) / (ph.f_F - ph.f_C) * (f - ph.f_C), fv))
+    return np.clip(fs, 0.0, ph.fstar_max)
+
+
+def gtn_nucleation(e0bar, ph):
+    """Chu-Needleman nucleation rate A_N (Eq. nucleation)."""
+    return ph.f_N / (ph.s_N * math.sqrt(2.0 * math.pi)) * np.exp(-0.5 * ((e0bar - ph.eps_N) / ph.s_N) ** 2)
+
+
+def gtn_porosity(f_n, a0, a0_n, at, at_n, ph):
+    """Backward-Euler porosity of the non-local GTN model (Eq.
+    non-local_porosity_gurson, Appendix A.1) with the non-local eps_0^p (a0)
+    and tr eps^p (at) held at the staggered iterate:
+        f - f_n = A_N(a0) (a0 - a0_n) + (1 - f) (at - at_n)."""
+    dat = at - at_n
+    return (f_n + gtn_nucleation(a0, ph) * (a0 - a0_n) + dat) / (1.0 + dat)
+
+
+def _gtn_residual(e, epsp_n, e0_n, fs, f, ph, K, mu, x):
+    """Residuals of the Backward-Euler GTN update (Appendix A.1) at x =
+    (d_v, d_q, e0): plastic strain increment d eps^p = d_v I/3 + d_q n with n
+    the trial flow direction (normality, Eq. flow_rule_gurson); pressure p =
+    p_tr + K d_v and Mises stress s = s_tr - 3 mu d_q;
+      R1 = phi(s, p, sigma_0(e0), f*)                       (Eq. yield_gurson)
+      R2 = sigma_0 (d_v dphi/ds + d_q dphi/dp)   (the normality ratio)
+      R3 = [(1 - f) sigma_0 (e0 - e0_n) - sigma : d eps^p] / sigma_0
+           (Eq. micro-macro, sigma : d eps^p = -p d_v + s d_q).
+    Complex arguments are carried through (complex-step differentiation)."""
+    ee = e - epsp_n
+    tr = ee[:, 0] + ee[:, 1] + ee[:, 2]
+    dev = ee - tr[:, None] * IVEC[None, :] / 3.0
+    p_tr = -K * tr
+    s_tr = np.sqrt(1.5 * np.sum((2.0 * mu[:, None] * dev) ** 2, axis=1))
+    dv, dq, e0 = x[:, 0], x[:, 1], x[:, 2]
+    s = s_tr - 3.0 * mu * dq
+    p = p_tr + K * dv
+    s0 = _flow_value(ph, e0)
+    arg = 1.5 * ph.q2 * p / s0
+    phi = (s / s0) ** 2 + 2.0 * fs * ph.q1 * np.cosh(arg) - (1.0 + ph.q3 * fs ** 2)
+    phi_s = 2.0 * s / s0 ** 2
+    phi_p = 3.0 * ph.q1 * ph.q2 * fs / s0 * np.sinh(arg)
+    r2 = s0 * (dv * phi_s + dq * phi_p)
+    r3 = ((1.0 - f) * s0 * (e0 - e0_n) - (-p * dv + s * dq)) / s0
+    return np.stack([phi, r2, r3], axis=1), s_tr, p_tr, dev
+
+
+def gtn_update(e, epsp_n, e0_n, fs, f, ph, K, mu):
+    """Backward-Euler GTN return map (Section 2.1.1, Appendix A.1) with f and
+    f* held fixed (they follow the frozen non-local variables).  e: (n, 6)
+    total Mandel strain, real or complex (complex step).  Elastic where the
+    trial stress satisfies phi <= 0; elsewhere Newton on (d_v, d_q, e0) from
+    the elastic predictor with a complex-step Jacobian of the residuals at the
+    real iterate and backtracking on the real residual.  Returns sigma,
+    epsp, e0."""
+    n = e.shape[0]
+    x = np.zeros((n, 3), dtype=e.dtype)
+    x[:, 2] = e0_n
+    R, s_tr, p_tr, dev = _gtn_residual(e, epsp_n, e0_n, fs, f, ph, K, mu, x)
+    pl = R[:, 0].real > 0.0
+    if np.any(pl):
+        sel = np.nonzero(pl)[0]
+        xs = x[sel]
+        args = (e[sel], epsp_n[sel], e0_n[sel], fs[sel], f[sel], ph, K[sel], mu[sel])
+        h = 1e-30
+        done = False
+        for it in range(100):
+            Rs = _gtn_residual(*args, xs)[0]
+            xr = xs.real.copy()
+            J = np.empty((len(sel), 3, 3))
+            for k in range(3):
+                xp = xr.astype(np.complex128)
+                xp[:, k] += 1j * h
+                J[:, :, k] = _gtn_residual(args[0].real, *args[1:], xp)[0].imag / h
+            step = np.linalg.solve(J, Rs[..., None])[..., 0]
+            lam = np.ones(len(sel))
+            r0 = np.linalg.norm(Rs.real, axis=1)
+            for _ in range(40):
+                xn = xs - lam[:, None] * step
+                rn = np.linalg.norm(_gtn_residual(*args, xn)[0].real, axis=1)
+                bad = ~(rn <= r0 * (1.0 - 1e-4 * lam)) & (r0 > 1e-15)
+                if not np.any(bad):
+                    break
+                lam = np.where(bad, 0.5 * lam, lam)
+            xs = xs - lam[:, None] * step
+            if done:
+                break
+            # quadratic convergence: a relative step of 1e-12 leaves the real
+            # part at round-off; one more iteration settles the complex-step
+            # part, which follows the real iterate
+            done = it >= 1 and bool(np.all(np.abs(step) <= 1e-12 * np.maximum(np.abs(xs), 1e-4)))
+        else:
+            raise RuntimeError("GTN return map did not converge")
+        if np.max(np.abs(_gtn_residual(*args, xs)[0].real)) > 1e-10:
+            raise RuntimeError("GTN return map did not converge")
+        x[sel] = xs
+    K2, mu2 = K[:, None], mu[:, None]
+    dv, dq, e0 = x[:, 0], x[:, 1], x[:, 2]
+    safe = np.where(s_tr.real > 0.0, s_tr, 1.0)
+    nflow = np.where((s_tr.real > 0.0)[:, None], 1.5 * 2.0 * mu2 * dev / safe[:, None], 0.0)
+    s = s_tr - 3.0 * mu * dq
+    p = p_tr + K * dv
+    sigma = -p[:, None] * IVEC[None, :] + (2.0 / 3.0) * s[:, None] * nflow
+    # elastic voxels: sigma = C (e - epsp_n) exactly
+    el = ~pl
+    if np.any(el):
+        ee = (e - epsp_n)[el]
+        trr = ee[:, 0] + ee[:, 1] + ee[:, 2]
+        sigma[el] = K2[el] * trr[:, None] * IVEC[None, :] + 2.0 * mu2[el] * (ee - trr[:, None] * IVEC[None, :] / 3.0)
+    epsp = epsp_n + dv[:, None] * IVEC[None, :] / 3.0 + dq[:, None] * nflow
+    return sigma, epsp, e0
+
+
 def damage_of(abar, ph):
     """Linear damage law driven by the non-local equivalent plastic strain
     (Eq. non-local_damage_lemaitre), capped at D_max (Section 4.1, R10); the
@@ -369,7 +512,7 @@ def positive_principal_norm(e):
     return np.sqrt(np.sum(np.maximum(lam, 0.0) ** 2, axis=-1))
 
 
-def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None):
+def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None, abar_n=None, f_n=None):
     """Backward-Euler update of the Lemaitre model (Appendix A.2 with R8-R11)
     at every voxel.
 
@@ -394,6 +537,14 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None):
     in the ep slot, D from abar of the phase's variable, sigma = (1 - D) C e.
     stiff: optional (V,) field scaling the Young's modulus voxel by voxel
     (K and mu of the voxel's phase times stiff; 1 where absent).
+    Gurson-Tvergaard-Needleman (law 3, Section 2.1.1 / 2.2.2, Appendix A.1):
+    the phase feeds variables var (alpha = eps_0^p, in the ep slot) and
+    var + 1 (alpha = tr eps^p); the porosity f follows the frozen non-local
+    variables from f_n (gtn_porosity, with abar_n the converged values of the
+    last increment), f* = gtn_fstar(f); gtn_update returns sigma, eps^p and
+    eps_0^p; the tangent is the complex-step derivative of that map (the
+    consistent tangent with f frozen, as D is for Lemaitre, R11); D reports
+    f*.  The dict also carries f (V,).
     """
     Vn = eps.shape[0]
     J = abar.shape[0]
@@ -404,12 +555,36 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None):
     D = np.zeros(Vn)
     alpha = np.zeros((J, Vn))
     Pdev = np.eye(6) - np.outer(IVEC, IVEC) / 3.0
+    if abar_n is None:
+        abar_n = np.zeros_like(abar)
+    fout = initial_porosity(phase, phases) if f_n is None else np.array(f_n, dtype=np.float64)
     for q, ph in enumerate(phases):
         sel = phase == q
         if not np.any(sel):
             continue
         sc = np.ones(int(sel.sum())) if stiff is None else np.asarray(stiff, dtype=np.float64)[sel]
         K, mu = ph.K * sc, ph.mu * sc
+        if ph.law == 3:
+            v0, v1 = ph.var, ph.var + 1
+            fq = gtn_porosity(fout[sel], abar[v0][sel], abar_n[v0][sel], abar[v1][sel], abar_n[v1][sel], ph)
+            fs = gtn_fstar(fq, ph)
+            e_q = eps[sel]
+            sig_q, epsp_q, e0_q = gtn_update(e_q, epsp_n[sel], ep_n[sel], fs, fq, ph, K, mu)
+            Cq = np.empty((e_q.shape[0], 6, 6))
+            hcs = 1e-30
+            for c in range(6):
+                ec = e_q.astype(np.complex128)
+                ec[:, c] += 1j * hcs
+                Cq[:, :, c] = gtn_update(ec, epsp_n[sel], ep_n[sel], fs, fq, ph, K, mu)[0].imag / hcs
+            sigma[sel] = sig_q
+            C[sel] = Cq
+            epsp[sel] = epsp_q
+            ep[sel] = e0_q
+            D[sel] = fs
+            fout[sel] = fq
+            alpha[v0, sel] = e0_q
+            alpha[v1, sel] = epsp_q[:, 0] + epsp_q[:, 1] + epsp_q[:, 2]
+            continue
         e = eps[sel] - epsp_n[sel]
         tr = e[:, 0] + e[:, 1] + e[:, 2]
         dev = e - tr[:, None] * IVEC[None, :] / 3.0
@@ -457,7 +632,16 @@ def return_map(eps, epsp_n, ep_n, abar, phase, phases, stiff=None):
               + 2.0 * (mu * theta)[:, None, None] * Pdev[None]
               - 2.0 * (mu * thetabar)[:, None, None] * np.einsum("vi,vj->vij", nhat, nhat))
         C[sel] = (1.0 - Dq)[:, None, None] * Cq
-    return dict(sigma=sigma, C=C, epsp=epsp, ep=ep, D=D, alpha=alpha)
+    return dict(sigma=sigma, C=C, epsp=epsp, ep=ep, D=D, alpha=alpha, f=fout)
+
+
+def initial_porosity(phase, phases):
+    """f0 of each GTN voxel, 0 elsewhere."""
+    f = np.zeros(len(phase))
+    for q, ph in enumerate(phases):
+        if ph.law == 3:
+            f[phase == q] = ph.f0
+    return f
 
 
 # ============================================================ Krylov solvers
@@ -578,7 +762,8 @@ class Options:
 PARITY_OPTIONS = Options(tol_stag=1e-11, tol_newton=1e-12, cg_rtol=1e-13, pcg_rtol=1e-13)
 
 
-def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_bar_c, opt, stiff=None):
+def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_bar_c, opt, stiff=None,
+               abar_n=None, f_n=None):
     """Newton-Raphson on the Galerkin residual at fixed abar (step (i) of
     Algorithm 1, Eq. lin_stress and the CG solve after it):
 
@@ -595,7 +780,7 @@ def mech_solve(grid, eps_c, epsp_n, ep_n, abar, phase, phases, stress_mask, sig_
     cg_total = 0
     de_rel = None
     while True:
-        rm = return_map(embed(eps_c, d).reshape(Vn, 6), epsp_n, ep_n, abar, phase, phases, stiff)
+        rm = return_map(embed(eps_c, d).reshape(Vn, 6), epsp_n, ep_n, abar, phase, phases, stiff, abar_n, f_n)
         sig_c = rm["sigma"][:, comps].reshape(sh + (len(comps),))
         Cc = rm["C"][:, comps][:, :, comps].reshape(sh + (len(comps), len(comps)))
         res = -G_apply(sig_c - sig_bar_c, grid, stress_mask)
@@ -630,6 +815,7 @@ class State:
     sigma: np.ndarray           # (V, 6)
     D: np.ndarray               # (V,)
     stiff: np.ndarray = None    # (V,) Young's modulus scaling, None = 1
+    f: np.ndarray = None        # (V,) porosity of GTN voxels (law 3)
     n_done: int = 0
     curve: list = field(default_factory=list)
 
@@ -639,9 +825,10 @@ def make_state(grid, phase_map, phases, ell, stiff=None):
     nc = len(carried(grid.d))
     J = np.asarray(ell).shape[0]
     sf = None if stiff is None else np.asarray(stiff, dtype=np.float64).reshape(Vn)
-    return State(grid, np.asarray(phase_map).reshape(Vn).astype(np.int64), phases,
-                 np.asarray(ell, dtype=np.float64), np.zeros((Vn, nc)), np.zeros((Vn, 6)),
-                 np.zeros(Vn), np.zeros((J, Vn)), np.zeros((Vn, 6)), np.zeros(Vn), sf)
+    ph = np.asarray(phase_map).reshape(Vn).astype(np.int64)
+    return State(grid, ph, phases, np.asarray(ell, dtype=np.float64), np.zeros((Vn, nc)), np.zeros((Vn, 6)),
+                 np.zeros(Vn), np.zeros((J, Vn)), np.zeros((Vn, 6)), np.zeros(Vn), sf,
+                 initial_porosity(ph, phases))
 
 
 def to_mandel_target(t6):
@@ -685,7 +872,7 @@ def step_increment(st, strain_ctrl, target_prev, target, opt, trace=None):
     while True:
         eps_new, rm, nn, nc_it = mech_solve(g, eps_k.reshape(sh + (nc,)), st.epsp, st.ep,
                                             abar_k, st.phase, st.phases, stress_mask,
-                                            sig_bar, opt, st.stiff)
+                                            sig_bar, opt, st.stiff, st.abar, st.f)
         eps_new = eps_new.reshape(Vn, nc)
         newton_tot += nn
         cg_tot += nc_it
@@ -719,6 +906,7 @@ def step_increment(st, strain_ctrl, target_prev, target, opt, trace=None):
     st.abar = abar_k
     st.sigma = rm["sigma"]
     st.D = rm["D"]
+    st.f = rm["f"]
     st.n_done += 1
     rec = dict(E=homogenized_strain(st), S=homogenized_stress(st),
                D_mean=float(st.D.mean()), D_max=float(st.D.max()), stag=stag,
