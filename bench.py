@@ -48,13 +48,22 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
-    ap.add_argument("--profile-steps", type=int, default=2,
-                    help="increments of the instrumented replay that gives the per-class times")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="increments of the instrumented replay that gives the per-class times (0: all)")
     ap.add_argument("--curve", action="store_true",
                     help="time the whole load path (cut-back steps) instead of the headline rate")
     ap.add_argument("--curve-incr", type=int, default=0, help="--curve: first K increments only (0: all)")
     ap.add_argument("--cpu-iters", type=int, default=2)
-    ap.add_argument("--workload", default="spheres256", choices=["spheres256", "batch", "adjoint"],
+    ap.add_argument("--obj-grids", type=lambda v: [int(x) for x in v.split(",")], default=[128, 256, 512])
+    ap.add_argument("--obj-incr", type=int, default=50)
+    ap.add_argument("--study-models", type=lambda v: v.split(","), default=["lemaitre", "gtn"])
+    ap.add_argument("--study-emax", type=float, default=0.1)
+    ap.add_argument("--study-de", type=float, default=2e-3)
+    ap.add_argument("--study-budget-s", type=float, default=120.0)
+    ap.add_argument("--study-profile-e", type=float, default=0.05)
+    ap.add_argument("--topology-model", default="lemaitre", choices=["lemaitre", "gtn"])
+    ap.add_argument("--workload", default="spheres256",
+                    choices=["spheres256", "batch", "adjoint", "objectivity", "studies2d", "topology3d"],
                     help="batch: the 32-RVE {64,96,128}^3 two-variable workload; adjoint: gradients of "
                          "the final stress of the 96^3 two-variable RVE (each its own JSON line)")
     ap.add_argument("--adj-incr", type=int, default=30)
@@ -270,12 +279,12 @@ def cg_iteration_ms(pkg, h, V, nc, iters=24):
     b = torch.empty_like(t)
     pkg.rve_op_apply_gamma(h, t, b)
     x = torch.empty_like(t)
-    pkg.rve_op_cg(h, b, x, 1e-30, 2)
+    pkg.rve_op_cg(h, b, x, 1e-30, 2, allow_budget=True)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     e0, e1 = _events(2)
     e0.record(s)
-    it = pkg.rve_op_cg(h, b, x, 1e-30, iters)
+    it = pkg.rve_op_cg(h, b, x, 1e-30, iters, allow_budget=True)
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -307,7 +316,7 @@ def run_ours(args, rank, ws, dist):
     start_state = pkg.rve_save_state(r.h, _pinned(nbytes))        # before the timed increments
     # like-for-like FP64 samples: the first, middle and last timed increment
     samples = sorted({0, K // 2, K - 1}) if (not args.no_fp64 and prec == pkg.RVE_MIXED) else []
-    snaps = {i: _pinned(nbytes) for i in samples if i > 0}
+    snaps = {}
     pkg.rve_profile_reset(r.h)
     clocks = ClockSampler()
     if rank == 0:
@@ -319,8 +328,6 @@ def run_ours(args, rank, ws, dist):
     e0.record(stream)
     infos = []
     for i in range(K):
-        if i in snaps:
-            pkg.rve_save_state(r.h, snaps[i])                         # state before increment i
         ev_a[i].record(stream)
         infos.append(r.step())
         ev_b[i].record(stream)
@@ -336,14 +343,26 @@ def run_ours(args, rank, ws, dist):
     rate, ms_max = aggregate(dist, ms, vi)
 
     # -------- per-class device time: an instrumented replay (CUDA events
-    # around every launch, direct launches) of the first timed increments
-    # from the saved state
+    # around every launch, direct launches) of the timed increments from the
+    # saved state; it also keeps the states before the FP64 samples
     pkg.rve_load_state(r.h, start_state)
     pkg.rve_profile_reset(r.h)
     pkg.rve_profile(r.h, True)
-    n_rep = min(args.profile_steps, K)
-    rep_infos = [r.step() for _ in range(n_rep)]
-    prof = pkg.rve_profile_read(r.h)
+    n_rep = K if args.profile_steps <= 0 else min(args.profile_steps, K)
+    last_sample = max(samples) if samples else 0
+    rep_infos = []
+    prof = None
+    for i in range(K):
+        if i == n_rep:                                                # replay of n_rep increments done
+            prof = pkg.rve_profile_read(r.h)
+            pkg.rve_profile(r.h, False)
+        if i in samples and i > 0:
+            snaps[i] = pkg.rve_save_state(r.h, _pinned(nbytes))       # state before increment i
+        if i >= n_rep and i >= last_sample:
+            break
+        rep_infos.append(r.step())
+    if prof is None:
+        prof = pkg.rve_profile_read(r.h)
     pkg.rve_profile(r.h, False)
     replay_same = all(a["cg_iters"] == b["cg_iters"] and a["pcg_iters"] == b["pcg_iters"]
                       for a, b in zip(rep_infos, infos))
@@ -368,8 +387,9 @@ def run_ours(args, rank, ws, dist):
                 "traffic": traffic, "traffic_source": traffic_note if traffic is not None else traffic_note,
                 "bytes_per_launch": dbytes / max(dlaunch, 1),
                 "avg_launch_ms": dms / max(dlaunch, 1), "launches": dlaunch,
-                "timing": "CUDA events around every launch of an instrumented replay of the first %d timed "
-                          "increments from the saved state (same iteration counts: %s)" % (n_rep, replay_same),
+                "timing": "CUDA events around every launch of an instrumented replay of the first %d of the "
+                          "%d timed increments from the saved state (same iteration counts: %s)"
+                          % (n_rep, K, replay_same),
                 "classes": {k: {"ms": round(v[0], 3), "launches": v[1],
                                 "GBps": round(v[2] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None}
                             for k, v in prof.items() if v[1] > 0}}
@@ -380,9 +400,8 @@ def run_ours(args, rank, ws, dist):
            "dtype": "f32+f64" if prec == pkg.RVE_MIXED else "f64", "data": "synthetic",
            "config": workload_config(cfg, args.precision), "roofline": roofline,
            "gpu_launches": gpu_launches, "clocks": ck,
-           "timed_region": "increments %d..%d, graph replay of the Krylov chunks, no per-launch events; "
-                           "includes %d state snapshot(s) to pinned host memory for the FP64 samples"
-                           % (args.warmup + 1, args.warmup + K, len(snaps)),
+           "timed_region": "increments %d..%d, graph replay of the Krylov chunks, no per-launch events"
+                           % (args.warmup + 1, args.warmup + K),
            "increments": [{"incr": i["increment"], "ms": round(t, 2) if t else None, "stag": i["staggered_iters"],
                            "newton": i["newton_iters"], "cg": i["cg_iters"], "pcg": i["pcg_iters"],
                            "S11": i["sigma"][0], "D_max": i["D_max"]} for i, t in zip(infos, incr_ms)]}
@@ -769,9 +788,227 @@ def run_curve(args):
             "curve_columns": ["E11", "S11", "D_max", "substeps", "cg", "pcg"], "curve": curve}
 
 
+def run_objectivity(args):
+    """Mesh objectivity of the 2D single-particle cell: the FP64 GPU form
+    runs the load path (uniaxial E11 in steps of 1e-3) at 128^2, 256^2 and
+    512^2 with the length fixed in physical units (l = L/16), each until the
+    end of the path or the first increment the staggered scheme cannot
+    converge.  Past the peak of the 512^2 curve, the softening branches of the
+    coarser grids are compared with it: the largest |Sigma11(E) - Sigma11_512(E)|
+    over the common increments, relative to the 512^2 peak."""
+    import torch
+    import rve_inputs as I
+    import paper_2103_04770_gb300 as pkg
+
+    torch.cuda.init()
+    curves = {}
+    for N in args.obj_grids:
+        cfg = I.config_mesh_objectivity(N, n_incr=args.obj_incr)
+        opt = pkg.rve_default_options(0)
+        opt.max_stag = 1000
+        t0 = time.perf_counter()
+        pts, status = [], "end of path"
+        with pkg.RVE(cfg, precision=0, options=opt) as r:
+            for i in range(cfg.target.shape[0]):
+                info = r.step(raise_on_error=False)
+                if info["status"] != pkg.RVE_OK:
+                    status = "increment %d: %s" % (i + 1, pkg.rve_status_string(info["status"]))
+                    break
+                pts.append([round(info["eps"][0], 6), info["sigma"][0], info["D_max"], info["staggered_iters"]])
+                print(json.dumps({"N": N, "increment": i + 1, "S11": info["sigma"][0], "D_max": info["D_max"],
+                                  "stag": info["staggered_iters"]}), file=sys.stderr, flush=True)
+        curves[N] = {"curve": pts, "status": status, "seconds": round(time.perf_counter() - t0, 1)}
+    ref_N = max(curves)
+    ref = np.array([p[1] for p in curves[ref_N]["curve"]])
+    ipk = int(np.argmax(ref))
+    out = {}
+    for N, c in curves.items():
+        if N == ref_N:
+            continue
+        s = np.array([p[1] for p in c["curve"]])
+        m = min(len(s), len(ref))
+        post = range(ipk, m)
+        dev = max((abs(s[i] - ref[i]) for i in post), default=None)
+        out[str(N)] = {"increments_compared_past_peak": len(post),
+                       "max_rel_dev_past_peak": None if dev is None else dev / ref[ipk],
+                       "within_3_percent": None if dev is None else bool(dev / ref[ipk] <= 0.03)}
+    return {"metric": "mesh objectivity of the softening branch, 2D single particle, l = L/16",
+            "value": max((v["max_rel_dev_past_peak"] for v in out.values()
+                          if v["max_rel_dev_past_peak"] is not None), default=None),
+            "unit": "max |Sigma11 - Sigma11_%d| / peak past the %d^2 peak" % (ref_N, ref_N),
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2d_disc_objectivity", "grids": list(curves), "ell": "L/16",
+                       "load": "uniaxial E11 steps of 1e-3, Sigma22 = Sigma12 = 0, plane strain",
+                       "options": "production FP64 (tol 1e-6), staggered budget 1000"},
+            "peak_increment_%d" % ref_N: ipk + 1, "comparison": out,
+            "curves": {str(N): c for N, c in curves.items()}}
+
+
+def _run_curve_cfg(pkg, cfg, precision, budget_s, max_cuts=6, tag=None):
+    """The load path of cfg through the cut-back step, until its end, the
+    first failure or the wall-clock budget; returns the curve and why it
+    stopped."""
+    opt = pkg.rve_default_options(precision)
+    opt.max_stag = 200
+    pts, status = [], "end of path"
+    t0 = time.perf_counter()
+    with pkg.RVE(cfg, precision=precision, options=opt) as r:
+        for i in range(cfg.target.shape[0]):
+            info = r.step_adaptive(max_cuts=max_cuts, raise_on_error=False)
+            if info["status"] != pkg.RVE_OK:
+                status = "increment %d: %s" % (i + 1, pkg.rve_status_string(info["status"]))
+                break
+            pts.append([round(info["eps"][0], 6), round(info["sigma"][0], 5), round(info["D_max"], 5),
+                        info["substeps"]])
+            print(json.dumps({"curve": tag or cfg.name, "increment": i + 1, "point": pts[-1]}), file=sys.stderr,
+                  flush=True)
+            if time.perf_counter() - t0 > budget_s:
+                status = "wall-clock budget of %d s after increment %d" % (budget_s, i + 1)
+                break
+    return {"curve": pts, "status": status, "seconds": round(time.perf_counter() - t0, 1)}
+
+
+def _curve_summary(c):
+    """Peak stress, strain at the peak, and the strain at which the stress
+    has fallen to 80 % of the peak (ductility; None if not reached)."""
+    if not c["curve"]:
+        return {}
+    E = [p[0] for p in c["curve"]]
+    S = [p[1] for p in c["curve"]]
+    ip = int(np.argmax(S))
+    e80 = next((E[i] for i in range(ip, len(S)) if S[i] <= 0.8 * S[ip]), None)
+    return {"peak_S11": S[ip], "E11_at_peak": E[ip], "E11_at_80pct_past_peak": e80, "last_E11": E[-1],
+            "max_D": max(p[2] for p in c["curve"])}
+
+
+def run_studies2d(args):
+    """The 2D studies of Section 4.1 with the paper's parameters: grid
+    sensitivity of the local and non-local Lemaitre and GTN models on
+    32^2 / 64^2 / 128^2 (Section 4.1.1), the matrix length l_M in {0.025, 0.05,
+    0.075} L on 128^2 (Section 4.1.2), and the non-local plastic strain across
+    the interface for l_M / l_I in {1, 5, 10, 20, 50} (one Helmholtz solve per
+    ratio on the plastic strain field of the non-local Lemaitre run).  The
+    paper's curves exist only as figures, so these runs report behaviour: the
+    spread between resolutions of the non-local curves against the local ones,
+    ductility against l_M, and how far abar reaches into the inclusion."""
+    import torch
+    import rve_inputs as I
+    import paper_2103_04770_gb300 as pkg
+
+    torch.cuda.init()
+    out = {"grid_sensitivity": {}, "length_effect": {}, "interface_profile": {}}
+    n_incr = int(round(args.study_emax / args.study_de))
+    for model in args.study_models:
+        for local in (False, True):
+            key = "%s_%s" % (model, "local" if local else "nonlocal")
+            curves = {}
+            for N in (32, 64, 128):
+                cfg = I.config_paper2d(N, model, local, n_incr=n_incr, dE=args.study_de)
+                curves[N] = _run_curve_cfg(pkg, cfg, 0, args.study_budget_s, tag=cfg.name)
+                curves[N]["summary"] = _curve_summary(curves[N])
+            # largest stress difference to the 128^2 curve over the common increments
+            ref = [p[1] for p in curves[128]["curve"]]
+            spread = {}
+            for N in (32, 64):
+                s = [p[1] for p in curves[N]["curve"]]
+                m = min(len(s), len(ref))
+                spread[str(N)] = max((abs(s[i] - ref[i]) for i in range(m)), default=None)
+            out["grid_sensitivity"][key] = {"curves": {str(N): c for N, c in curves.items()},
+                                            "max_abs_dS11_vs_128": spread}
+    for model in args.study_models:
+        for lM in (0.025, 0.05, 0.075):
+            cfg = I.config_paper2d(128, model, False, ell_M=lM, n_incr=n_incr, dE=args.study_de)
+            c = _run_curve_cfg(pkg, cfg, 0, args.study_budget_s, tag=cfg.name + "_lM%.3f" % lM)
+            c["summary"] = _curve_summary(c)
+            out["length_effect"]["%s_lM_%.3f" % (model, lM)] = c
+    # interface profiles: the plastic strain of the non-local Lemaitre run at
+    # its last increment, regularised with l_I = l_M / ratio
+    cfg = I.config_paper2d(128, "lemaitre", False, n_incr=n_incr, dE=args.study_de)
+    N = 128
+    V = N * N
+    opt = pkg.rve_default_options(0)
+    opt.max_stag = 200
+    with pkg.RVE(cfg, precision=0, options=opt) as r:
+        for i in range(cfg.target.shape[0]):
+            info = r.step_adaptive(max_cuts=6, raise_on_error=False)
+            if info["status"] != pkg.RVE_OK:
+                break
+            if info["eps"][0] >= args.study_profile_e:
+                break
+        ep = torch.empty(V, device="cuda", dtype=torch.float64)
+        pkg.rve_get_field(r.h, 4, ep)
+        E_at = info["eps"][0]
+    phase = torch.as_tensor(cfg.phase.reshape(-1), device="cuda")
+    alpha = ep * (phase == 0).to(torch.float64)
+    lM = 0.05 * N
+    line = N // 2
+    inside = (cfg.phase.reshape(N, N)[line] == 1)
+    for ratio in (1, 5, 10, 20, 50):
+        h = pkg.rve_create(2, cfg.n, cfg.L, 0, 1)
+        try:
+            pkg.rve_set_phases(h, cfg.phase, cfg.params, np.array([[lM, lM / ratio]]))
+            abar = torch.empty(V, device="cuda", dtype=torch.float64)
+            it = pkg.rve_op_helmholtz_solve(h, 0, alpha, abar, 1e-12, 5000)
+            prof = abar.cpu().numpy().reshape(N, N)[line]
+            a_in = prof[inside]
+            out["interface_profile"]["ratio_%d" % ratio] = {
+                "pcg_iterations": it, "profile_along_x1": [round(float(x), 7) for x in prof],
+                "max_abar_inside_over_max": float(a_in.max() / prof.max()) if prof.max() > 0 else None,
+                "mean_abar_inside_over_mean_matrix": float(a_in.mean() / prof[~inside].mean())}
+        finally:
+            pkg.rve_free(h)
+    out["interface_profile"]["E11"] = E_at
+    return {"metric": "2D parameter studies of Section 4.1 (grid sensitivity, l_M effect, interface profiles)",
+            "value": None, "unit": "curves", "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper2d_studies", "models": args.study_models, "E11_max": args.study_emax,
+                       "dE11": args.study_de, "steps": "cut-back steps, at most 6 halvings",
+                       "budget_s_per_curve": args.study_budget_s,
+                       "materials": "Section 4.1 parameters (rve_inputs PAPER2D_*)"},
+            "results": out}
+
+
+def run_topology3d(args):
+    """Convergence for a fixed topology (Section 4.2): the 30-sphere, 20 %
+    RVE generated on 32^3 and replicated to 64^3 and 96^3 voxels, non-local
+    Lemaitre (the paper's 3D parameters), mixed form, uniaxial tension; the
+    curves at the three resolutions and their largest stress differences."""
+    import torch
+    import rve_inputs as I
+    import paper_2103_04770_gb300 as pkg
+
+    torch.cuda.init()
+    n_incr = int(round(args.study_emax / args.study_de))
+    curves = {}
+    for f in (1, 2, 3):
+        cfg = I.config_fixed_topology(f, model=args.topology_model, n_incr=n_incr, dE=args.study_de)
+        curves[cfg.n[0]] = _run_curve_cfg(pkg, cfg, 1, args.study_budget_s, tag=cfg.name)
+        curves[cfg.n[0]]["summary"] = _curve_summary(curves[cfg.n[0]])
+        curves[cfg.n[0]]["sha256_base"] = cfg.meta["sha256_base"][:16]
+    ref = [p[1] for p in curves[96]["curve"]]
+    diff = {}
+    for N in (32, 64):
+        s = [p[1] for p in curves[N]["curve"]]
+        m = min(len(s), len(ref))
+        diff[str(N)] = max((abs(s[i] - ref[i]) / max(ref) for i in range(m)), default=None)
+    return {"metric": "fixed-topology refinement (Section 4.2): 32^3 geometry on 32^3 / 64^3 / 96^3",
+            "value": diff.get("64"), "unit": "max |Sigma11 - Sigma11_96| / peak, 64^3 curve",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "fixed_topology_3d", "model": args.topology_model, "E11_max": args.study_emax,
+                       "dE11": args.study_de, "spheres": 30, "vf": 0.2, "l_M": "0.05 L", "l_I": "0.001 L"},
+            "max_rel_dS11_vs_96": diff, "curves": {str(N): c for N, c in curves.items()}}
+
+
 def main():
     args = parse()
     rank, ws, dist = dist_init()
+    if args.workload in ("studies2d", "topology3d") and args.impl == "ours":
+        if rank == 0:
+            print(json.dumps(run_studies2d(args) if args.workload == "studies2d" else run_topology3d(args)))
+        return
+    if args.workload == "objectivity" and args.impl == "ours":
+        if rank == 0:
+            print(json.dumps(run_objectivity(args)))
+        return
     if args.curve and args.impl == "ours":
         if rank == 0:
             print(json.dumps(run_curve(args)))

@@ -63,8 +63,8 @@ typedef enum {
 
 /* Per-phase constitutive parameters (Section 2.1.2; Section 4 for the damage
  * cap).  damage_law: 0 = linear elastic (E, nu only); 1 = J2 plasticity with
- * linear hardening sigma_0 = sigma_y + H eps_p on the effective stress and
- * Lemaitre damage D = clamp((abar - eps_C)/(eps_R - eps_C), 0, D_max)
+ * isotropic hardening sigma_0(eps_p) on the effective stress and Lemaitre
+ * damage D = clamp((abar - eps_C)/(eps_R - eps_C), 0, D_max)
  * (Eq. non-local_damage_lemaitre); 2 = cracking elastic particle, an
  * extension of the multi-variable framework of Section 3.1 that the paper
  * does not print: local variable kappa = max(kappa_n, ||<eps>_+||) (norm of
@@ -72,12 +72,35 @@ typedef enum {
  * 0, D_max) with eps_C, eps_R read as kappa_C, kappa_R, sigma = (1 - D) C eps.
  * nonlocal_var: index j of the non-local variable this phase feeds with
  * alpha_j = eps_p (law 1) or kappa (law 2) and reads abar_j from, or -1
- * (Section 3.1: alpha_j = 0 outside the damaging phase). */
+ * (Section 3.1: alpha_j = 0 outside the damaging phase).
+ * 3 = non-local Gurson-Tvergaard-Needleman (Sections 2.1.1 and 2.2.2,
+ * Appendix A.1): yield surface (s/sigma_0)^2 + 2 f* q1 cosh(3 q2 p /
+ * (2 sigma_0)) - 1 - q3 f*^2 with normal flow, matrix equivalent plastic
+ * strain eps_0^p by the work balance sigma : d eps^p = (1 - f) sigma_0
+ * d eps_0^p, porosity f driven by the non-local eps_0^p and tr eps^p
+ * (Eq. non-local_porosity_gurson, Chu-Needleman nucleation f_N, eps_N, s_N
+ * from the initial porosity f_0), effective porosity f*(f) with coalescence
+ * between f_C and f_F, capped at fstar_max < f_V* (Section 4: 0.9 f_V*).
+ * The phase feeds variables nonlocal_var (alpha = eps_0^p) and
+ * nonlocal_var + 1 (alpha = tr eps^p); damage fields report f*.
+ * hardening (laws 1 and 3): 0 = linear, sigma_0 = sigma_y + H e; 1 = the
+ * Aravas power law of Section 4.1 (Eq. aravas), sigma_0 / sigma_y =
+ * (sigma_0 / sigma_y + 3 mu e / sigma_y)^N with mu this phase's shear
+ * modulus and 0 < N < 1.  The remaining fields are read only when they
+ * apply; reserved must be 0. */
 typedef struct {
   double E, nu, sigma_y, H;
   int damage_law;
   int nonlocal_var;
   double eps_C, eps_R, D_max;
+  int hardening;
+  int reserved;
+  double N;
+  double q1, q2, q3;          /* GTN surface coefficients */
+  double f_C, f_F;            /* coalescence onset, porosity at fracture */
+  double f_N, eps_N, s_N;     /* Chu-Needleman nucleation (Eq. nucleation) */
+  double f_0;                 /* initial porosity */
+  double fstar_max;           /* cap on the effective porosity */
 } rve_phase_params;
 
 /* Solver tolerances and budgets.  The paper prints no values (Algorithm 1,
@@ -187,7 +210,8 @@ int rve_homogenized_strain(const rve_t* h, double eps[6]);
 /* Copies a field of the last converged increment to dst (device pointer),
  * FP64, component-major.  which: 0 strain (Mandel, nc comps), 1 stress
  * (Mandel, 6 comps), 2 damage D (1), 3 non-local abar (J comps), 4 eps_p (1),
- * 5 plastic strain (Mandel, 6 comps). */
+ * 5 plastic strain (Mandel, 6 comps), 6 porosity f (1; 0 outside GTN
+ * phases).  For GTN phases field 2 holds f* and field 4 eps_0^p. */
 int rve_get_field(const rve_t* h, int which, double* dst, size_t n_doubles);
 
 /* Number of voxels and carried Mandel components of a handle. */
@@ -228,14 +252,38 @@ int rve_op_return_map(rve_t* h, const double* eps, const double* epsp_n, const d
                       const double* abar, double* sigma, double* epsp, double* ep, double* D,
                       double* alpha);
 
+/* The same with the history of the GTN law (law 3) given explicitly:
+ * abar_n [J][V] the non-local variables of the last converged increment and
+ * f_n [V] its porosity (device; NULL = the handle's converged state); the
+ * new porosity goes to f [V] (device; NULL = handle scratch).  The porosity
+ * of GTN voxels is (f_n + A_N(abar_0) (abar_0 - abar_0,n) + d) / (1 + d),
+ * d = abar_1 - abar_1,n (Appendix A.1 with the non-local variables frozen);
+ * D receives f*, ep eps_0^p, alpha eps_0^p and tr eps^p. */
+int rve_op_return_map_ex(rve_t* h, const double* eps, const double* epsp_n, const double* ep_n,
+                         const double* abar, const double* abar_n, const double* f_n, double* sigma,
+                         double* epsp, double* ep, double* D, double* alpha, double* f);
+
 /* tau = C_T : p with the tangent of the last rve_op_return_map (Eq.
  * lin_stress); p, tau: [nc][V]. */
 int rve_op_tangent_apply(rve_t* h, const double* p, double* tau);
 
 /* out = G*(tau) = F^-1 { G*(xi) : F(tau) } (Eq. eqdiscrete2): the Galerkin
  * projection with the rotated-scheme derivative and the zero frequency
- * projected on the stress-controlled components.  tau, out: [nc][V]. */
+ * projected on the stress-controlled components.  tau, out: [nc][V].
+ * Errors: RVE_ERR_ARG, RVE_ERR_CUDA, RVE_ERR_TIMEOUT (a tile copy of the 3D
+ * projection pass did not arrive within its wait budget). */
 int rve_op_apply_gamma(rve_t* h, const double* tau, double* out);
+
+/* Test hook of the timeout path of the 3D projection pass (not part of the
+ * method): wait_s (0 < wait_s <= 60, default 2) is how long a CTA waits for
+ * its tile copy before it gives up and the call returns RVE_ERR_TIMEOUT;
+ * extra_tx_bytes (0..4096, default 0) are added to the byte count the
+ * tile's barrier expects, which no copy delivers, so that the wait runs out
+ * although the copy lands (the CTA then counts those bytes itself, so that
+ * no copy is in flight when it returns).  A handle that has reported
+ * RVE_ERR_TIMEOUT keeps reporting it and should be freed.
+ * Errors: RVE_ERR_ARG. */
+int rve_test_tile_wait(rve_t* h, double wait_s, int extra_tx_bytes);
 
 /* Ap = G*(C_T : p), the operator of the mechanical CG (Section 3.2.2). */
 int rve_op_matvec(rve_t* h, const double* p, double* Ap);
@@ -258,7 +306,8 @@ int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, d
 
 /* ------------------------------------------------ checkpoint / resume
  * The converged state after the last increment (strain, plastic strain,
- * local history variable, non-local variables and the homogenised values)
+ * local history variable, non-local variables, porosity and the
+ * homogenised values)
  * as a self-describing byte image, so a long load path can be saved and
  * resumed (also on another handle of the same grid and variable count; the
  * phases, options and load path are not part of the image and must be set
@@ -266,7 +315,7 @@ int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, d
  * written by a mixed-precision handle loads into an FP64 handle and the
  * other way round. */
 
-/* Bytes of the image of this handle (header + (nc + 7 + J) V doubles). */
+/* Bytes of the image of this handle (header + (nc + 8 + J) V doubles). */
 long long rve_state_bytes(const rve_t* h);
 
 /* Write the image into the caller's host buffer `buf` of `bytes` bytes.
@@ -353,8 +402,9 @@ int rve_set_stiffness_field(rve_t* h, const double* s);
  * state after 0, k, 2k, ... increments (k = checkpoint_every) in device
  * memory owned by the handle (about (nc + 8 + J) V doubles each, plus k
  * increments' states for the recomputation).  J (nullable): the objective.
- * Errors: RVE_ERR_ARG (FP32/mixed handle, k < 1), RVE_ERR_STATE (phases or
- * load path not set), the step errors of rve_step_increment. */
+ * Errors: RVE_ERR_ARG (FP32/mixed handle, k < 1, a phase with the Aravas
+ * flow stress), RVE_ERR_STATE (phases or load path not set), the step
+ * errors of rve_step_increment. */
 int rve_adjoint_forward(rve_t* h, int checkpoint_every, double* J);
 
 typedef struct {

@@ -40,7 +40,16 @@ class RVEError(RuntimeError):
 class PhaseParams(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("sigma_y", ctypes.c_double),
                 ("H", ctypes.c_double), ("damage_law", ctypes.c_int), ("nonlocal_var", ctypes.c_int),
-                ("eps_C", ctypes.c_double), ("eps_R", ctypes.c_double), ("D_max", ctypes.c_double)]
+                ("eps_C", ctypes.c_double), ("eps_R", ctypes.c_double), ("D_max", ctypes.c_double),
+                ("hardening", ctypes.c_int), ("reserved", ctypes.c_int), ("N", ctypes.c_double),
+                ("q1", ctypes.c_double), ("q2", ctypes.c_double), ("q3", ctypes.c_double),
+                ("f_C", ctypes.c_double), ("f_F", ctypes.c_double), ("f_N", ctypes.c_double),
+                ("eps_N", ctypes.c_double), ("s_N", ctypes.c_double), ("f_0", ctypes.c_double),
+                ("fstar_max", ctypes.c_double)]
+
+# GTN parameters of Section 4.1 (used when a phase dict leaves them out)
+GTN_DEFAULTS = dict(q1=1.5, q2=1.0, q3=2.25, f_C=0.15, f_F=0.25, f_N=0.04, eps_N=0.3, s_N=0.1, f0=0.0,
+                    fstar_max=0.6)
 
 
 class SolverOptions(ctypes.Structure):
@@ -94,9 +103,11 @@ _SIGNATURES = {
     "rve_get_sizes": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rve_status_string": (ctypes.c_char_p, [_I]),
     "rve_op_return_map": (_I, [_P] * 10),
+    "rve_op_return_map_ex": (_I, [_P] * 13),
     "rve_op_tangent_apply": (_I, [_P, _P, _P]),
     "rve_op_apply_gamma": (_I, [_P, _P, _P]),
     "rve_op_matvec": (_I, [_P, _P, _P]),
+    "rve_test_tile_wait": (_I, [_P, _D, _I]),
     "rve_op_cg": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I)]),
     "rve_op_helmholtz_apply": (_I, [_P, _I, _P, _P]),
     "rve_op_helmholtz_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(_I)]),
@@ -201,15 +212,20 @@ def rve_set_options(h, opt):
 def phase_params_array(params):
     arr = (PhaseParams * len(params))()
     for i, p in enumerate(params):
+        d = dict(GTN_DEFAULTS, **{k: v for k, v in p.items() if k in GTN_DEFAULTS})
         arr[i] = PhaseParams(p["E"], p["nu"], p.get("sigma_y", 0.0), p.get("H", 0.0),
                              int(p.get("law", 0)), int(p.get("var", -1)), p.get("eps_C", 0.0),
-                             p.get("eps_R", 1.0), p.get("D_max", 0.0))
+                             p.get("eps_R", 1.0), p.get("D_max", 0.0), int(p.get("hard", 0)), 0,
+                             p.get("N", 0.1), d["q1"], d["q2"], d["q3"], d["f_C"], d["f_F"], d["f_N"],
+                             d["eps_N"], d["s_N"], d["f0"], d["fstar_max"])
     return arr
 
 
 def rve_set_phases(h, phase, params, ell):
     """phase: numpy uint8 array (host) or CUDA uint8 tensor; params: list of
-    dicts (E, nu, sigma_y, H, law, var, eps_C, eps_R, D_max); ell: [J][n_phases]."""
+    dicts (E, nu, sigma_y, H, law, var, eps_C, eps_R, D_max and optionally
+    hard, N and the GTN parameters q1, q2, q3, f_C, f_F, f_N, eps_N, s_N, f0,
+    fstar_max); ell: [J][n_phases]."""
     if hasattr(phase, "data_ptr"):
         pp = _ptr(phase)
         keep = phase
@@ -284,6 +300,16 @@ def rve_op_return_map(h, eps, epsp_n, ep_n, abar, sigma, epsp, ep, D, alpha):
                                    _ptr(epsp), _ptr(ep), _ptr(D), _ptr(alpha)), "rve_op_return_map")
 
 
+def rve_op_return_map_ex(h, eps, epsp_n, ep_n, abar, abar_n, f_n, sigma, epsp, ep, D, alpha, f):
+    """rve_op_return_map with the GTN history given (abar_n, f_n) and the new
+    porosity returned (f); any of abar_n, f_n, f may be None."""
+    def opt(t):
+        return None if t is None else _ptr(t)
+    _check(lib().rve_op_return_map_ex(h, _ptr(eps), _ptr(epsp_n), _ptr(ep_n), opt(abar), opt(abar_n), opt(f_n),
+                                      _ptr(sigma), _ptr(epsp), _ptr(ep), _ptr(D), opt(alpha), opt(f)),
+           "rve_op_return_map_ex")
+
+
 def rve_op_tangent_apply(h, p, tau):
     _check(lib().rve_op_tangent_apply(h, _ptr(p), _ptr(tau)), "rve_op_tangent_apply")
 
@@ -292,13 +318,22 @@ def rve_op_apply_gamma(h, tau, out):
     _check(lib().rve_op_apply_gamma(h, _ptr(tau), _ptr(out)), "rve_op_apply_gamma")
 
 
+def rve_test_tile_wait(h, wait_s=2.0, extra_tx_bytes=0):
+    """Test hook of the tile-wait timeout path (see rve.h)."""
+    _check(lib().rve_test_tile_wait(h, float(wait_s), int(extra_tx_bytes)), "rve_test_tile_wait")
+
+
 def rve_op_matvec(h, p, Ap):
     _check(lib().rve_op_matvec(h, _ptr(p), _ptr(Ap)), "rve_op_matvec")
 
 
-def rve_op_cg(h, b, x, rtol, maxit):
+def rve_op_cg(h, b, x, rtol, maxit, allow_budget=False):
+    """CG iterations taken; with allow_budget, running out of maxit is not an
+    error (a fixed number of iterations, e.g. for timing)."""
     it = ctypes.c_int()
-    _check(lib().rve_op_cg(h, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(it)), "rve_op_cg")
+    s = lib().rve_op_cg(h, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(it))
+    if not (allow_budget and s == RVE_ERR_NOT_CONVERGED):
+        _check(s, "rve_op_cg")
     return it.value
 
 

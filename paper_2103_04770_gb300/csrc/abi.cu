@@ -53,7 +53,7 @@ enum {
   KC_X_INV_RESIDUAL,
   KC_X_INV_STORE,
   KC_HELM_EXPAND,
-  KC_HELM_XMID,
+  KC_HELM_X1,
   KC_HELM_CONTRACT,
   KC_CG_UPDATE,
   KC_PCG_UPDATE,
@@ -61,12 +61,13 @@ enum {
   KC_MISC,
   KC_RES_Y_PASS,
   KC_RES_GAMMA,
+  KC_HELM_STENCIL,
   KC_COUNT
 };
 const char* const kClassNames[KC_COUNT] = {
     "return_map", "x1_fwd_tangent", "x1_fwd_field", "y_pass", "gamma_last_axis", "x1_inv_matvec",
-    "x1_inv_residual", "x1_inv_store", "helmholtz_expand", "helmholtz_x1_mid", "helmholtz_contract",
-    "cg_update", "pcg_update", "finalize", "misc", "residual_y_pass", "residual_gamma"};
+    "x1_inv_residual", "x1_inv_store", "helmholtz_expand", "helmholtz_x1", "helmholtz_contract",
+    "cg_update", "pcg_update", "finalize", "misc", "residual_y_pass", "residual_gamma", "helmholtz_stencil"};
 
 struct PendingEv {
   int cls;
@@ -155,6 +156,14 @@ struct rve {
   double g_pcg_b[kMaxVars][KC_COUNT] = {};
   bool stepped = false;  // an increment has been attempted (autotuning closed)
   double* stiff = nullptr;  // per-voxel modulus factor (nullptr: 1 everywhere)
+  // GTN (law 3): porosity of the last converged increment and of the
+  // current return map; the tangent descriptor takes the extended layout
+  bool gtn = false;
+  double *f_n = nullptr, *f = nullptr;
+  // wait budget of the 3D projection pass's tile copies, and bytes added to
+  // their expected count (tests of the timeout path only)
+  double tile_wait_s = 2.0;
+  int tile_extra_tx = 0;
   // mixed form: stress and FP64-swept residual of the last FP64 sweep of the
   // current increment (reference of the FP32 difference sweeps)
   double* sig_ref = nullptr;
@@ -399,13 +408,17 @@ struct Alg {
     C2<R>* S = (C2<R>*)h->S;
     if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)h->g.nc * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, S, h->g.nc, 1, -1, ctl));
     LAUNCHB(h, KC_GAMMA, 2.0 * (double)h->g.nc * VS(h) * CS,
-            Op::gamma(h->g, t, h->lc, h->st, S, h->smask_f, dc_mode, ctl, &h->ctl->wait_err));
+            Op::gamma(h->g, t, h->lc, h->st, S, h->smask_f, dc_mode, ctl, &h->ctl->wait_err, h->tile_wait_s,
+                      h->tile_extra_tx));
     if (h->g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)h->g.nc * VS(h) * CS, Op::strided_plain(h->g, t, h->lc, h->st, S, h->g.nc, 1, +1, ctl));
   }
 
   static void return_map(rve* h, const double* abar_use) {
-    LAUNCHB(h, KC_RETURN_MAP, VV(h) * (8.0 * h->g.nc + 169.0 + 16.0 * h->J + (2.0 + h->g.nc) * RS), Op::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, h->eps, h->epsp_n, h->ep_n, abar_use,
-                   h->sigma, h->epsp, h->ep, h->D, h->alpha, (R*)h->desc, h->part, h->stiff));
+    const double gb = h->gtn ? VV(h) * (16.0 * h->J + 16.0 + 2.0 * RS) : 0.0;
+    LAUNCHB(h, KC_RETURN_MAP, VV(h) * (8.0 * h->g.nc + 169.0 + 16.0 * h->J + (2.0 + h->g.nc) * RS) + gb,
+            Op::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, h->eps, h->epsp_n, h->ep_n, abar_use,
+                           h->sigma, h->epsp, h->ep, h->D, h->alpha, (R*)h->desc, h->part, h->stiff, h->abar_n,
+                           h->f_n, h->f, h->gtn));
     LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 7, FIN_SUMS, nullptr,
                h->dscal + OFF_SIGMEAN, 1.0 / (double)h->g.V));
     LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 7 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
@@ -426,7 +439,8 @@ struct Alg {
       LAUNCHB(h, KC_RES_Y_PASS, 2.0 * nc * VS(h) * cs64,
               Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, -1, nullptr));
     LAUNCHB(h, KC_RES_GAMMA, 2.0 * nc * VS(h) * cs64,
-            Ops<double>::gamma(g, t64, h->lc64, h->st, S64, h->smask_f, 1, nullptr, &h->ctl->wait_err));
+            Ops<double>::gamma(g, t64, h->lc64, h->st, S64, h->smask_f, 1, nullptr, &h->ctl->wait_err,
+                               h->tile_wait_s, h->tile_extra_tx));
     if (g.d == 3)
       LAUNCHB(h, KC_RES_Y_PASS, 2.0 * nc * VS(h) * cs64,
               Ops<double>::strided_plain(g, t64, h->lc64, h->st, S64, g.nc, 1, +1, nullptr));
@@ -505,7 +519,7 @@ struct Alg {
         for (int i = 0; i < chunk && h->cg_fused; i++) {
           LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS,
                   Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc,
-                                   (C2<R>*)h->S, h->ctl, h->part));
+                                   (C2<R>*)h->S, h->ctl, h->part, h->gtn));
           LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
           gamma_sweep(h, t, 0, h->ctl);
           LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 5.0 * VV(h) * RS),
@@ -515,7 +529,7 @@ struct Alg {
         }
         for (int i = 0; i < chunk && !h->cg_fused; i++) {
           LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S,
-                           h->ctl));
+                           h->ctl, nullptr, h->gtn));
           gamma_sweep(h, t, 0, h->ctl);
           LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 2.0 * VV(h) * RS), Op::xinv_matvec(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, h->ctl));
           LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
@@ -629,16 +643,25 @@ struct Alg {
     LAUNCHB(h, KC_X_INV_STORE, 1.0 * (VS(h) * CS + 8.0 * VV(h)), Op::xinv_store64(h->g, t, h->lc, h->st, in, 1, f));
   }
 
-  // Helmholtz operator application on the spectrum: y = p + conj(k).F(l^2 F^-1(k p)).
+  // Helmholtz operator application on the spectrum (GC of Algorithm 2):
+  // y = p + F(sum_j D_j^T (l^2 D_j F^-1 p)), the flux term applied in real
+  // space, equal to p + conj(k).F(l^2 F^-1(k p)) (reading R15); the identity
+  // stays exact in the spectrum.  The real fields q and the flux term sit in
+  // the mechanical Ap buffer, idle during the solve.
   static void helm_matvec(rve* h, const Tables<R>& t, int j, C2<R>* pvec, const C2<R>* rsrc, C2<R>* y,
                           const KrylovCtl* ctl, int raw) {
     const Geo& g = h->g;
     C2<R>* W = (C2<R>*)h->S;
-    LAUNCHB(h, KC_HELM_EXPAND, (raw ? 1.0 + g.d : 3.0 + g.d) * VS(h) * CS, Op::helm_expand(g, t, h->lc, h->st, W, pvec, rsrc, h->ell2_mean[j], ctl, raw));
-    if (g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)g.d * VS(h) * CS, Op::strided_plain(g, t, h->lc, h->st, W, g.d, 1, +1, ctl));
-    LAUNCHB(h, KC_HELM_XMID, 2.0 * g.d * VS(h) * CS + VV(h), Op::xmid_ell(g, t, h->lc, h->st, W, h->phase, (const R*)h->ell2R + j * kMaxPhases, ctl));
-    if (g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * (double)g.d * VS(h) * CS, Op::strided_plain(g, t, h->lc, h->st, W, g.d, 1, -1, ctl));
-    LAUNCHB(h, KC_HELM_CONTRACT, (g.d + 2.0) * VS(h) * CS, Op::helm_contract(g, t, h->lc, h->st, W, raw ? rsrc : pvec, y, h->part, ctl));
+    R* q = (R*)h->Ap;
+    R* Lq = q + g.V;
+    LAUNCHB(h, KC_HELM_EXPAND, (raw ? 2.0 : 4.0) * VS(h) * CS, Op::helm_expand(g, t, h->lc, h->st, W, pvec, rsrc, h->ell2_mean[j], ctl, raw));
+    if (g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * VS(h) * CS, Op::strided_plain(g, t, h->lc, h->st, W, 1, 1, +1, ctl));
+    LAUNCHB(h, KC_HELM_X1, VS(h) * CS + VV(h) * RS, Op::xinv_storeR(g, t, h->lc, h->st, W, q, ctl));
+    LAUNCHB(h, KC_HELM_STENCIL, VV(h) * (2.0 * RS + 1.0),
+            Op::helm_stencil(g, h->lc, h->st, q, Lq, h->phase, (const R*)h->ell2R + j * kMaxPhases, ctl));
+    LAUNCHB(h, KC_HELM_X1, VS(h) * CS + VV(h) * RS, Op::xfwd_fieldR(g, t, h->lc, h->st, Lq, W, ctl));
+    if (g.d == 3) LAUNCHB(h, KC_Y_PASS, 2.0 * VS(h) * CS, Op::strided_plain(g, t, h->lc, h->st, W, 1, 1, -1, ctl));
+    LAUNCHB(h, KC_HELM_CONTRACT, 3.0 * VS(h) * CS, Op::helm_contract(g, t, h->lc, h->st, W, raw ? rsrc : pvec, y, h->part, ctl));
   }
 
   // Algorithm 2 for variable j: abar = F^-1 PCG(GC, M, F(alpha)).
@@ -762,6 +785,7 @@ struct Alg {
     std::swap(h->epsp_n, h->epsp);
     std::swap(h->ep_n, h->ep);
     std::swap(h->abar_n, h->abar_k);
+    if (h->gtn) std::swap(h->f_n, h->f);
     CK(cudaStreamSynchronize(h->st));
     for (int c = 0; c < 6; c++) h->sig_mean[c] = h->hscal[OFF_SIGMEAN + c] / W6[c];
     for (int c = 0; c < 6; c++) h->eps_mean[c] = 0.0;
@@ -799,16 +823,15 @@ struct Alg {
     LAUNCHB(h, KC_X_FWD_FIELD, (double)h->g.nc * (8.0 * VV(h) + VS(h) * CS), Op::xfwd_field64(h->g, t, h->lc, h->st, tau, h->g.nc, map, nullptr, (C2<R>*)h->S));
     gamma_sweep(h, t, 0, nullptr);
     LAUNCHB(h, KC_X_INV_STORE, (double)h->g.nc * (VS(h) * CS + 8.0 * VV(h)), Op::xinv_store64(h->g, t, h->lc, h->st, (const C2<R>*)h->S, h->g.nc, out));
-    CK(cudaStreamSynchronize(h->st));
-    CK(cudaGetLastError());
-    return RVE_OK;
+    // reads the control block: a tile wait that ran out is RVE_ERR_TIMEOUT
+    return sync_read(h);
   }
 
   static int op_matvec(rve* h, const double* p, double* Ap) {
     const Tables<R> t = tables<R>(h);
     const long long n = (long long)h->g.nc * h->g.V;
     LAUNCHB(h, KC_MISC, (double)n * (8.0 + RS), Op::to_r(h->st, n, p, (R*)h->p));
-    LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (2.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(h->g, t, h->lc, h->st, (R*)h->p, nullptr, (const R*)h->desc, (C2<R>*)h->S, nullptr));
+    LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (2.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(h->g, t, h->lc, h->st, (R*)h->p, nullptr, (const R*)h->desc, (C2<R>*)h->S, nullptr, nullptr, h->gtn));
     gamma_sweep(h, t, 0, nullptr);
     LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 2.0 * VV(h) * RS), Op::xinv_matvec(h->g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, nullptr));
     LAUNCHB(h, KC_MISC, (double)n * (8.0 + RS), Op::from_r(h->st, n, (const R*)h->Ap, Ap));
@@ -914,7 +937,11 @@ int reset_state(rve* h) {
   CK(cudaMemsetAsync(h->abar_n, 0, JV, h->st));
   CK(cudaMemsetAsync(h->abar_k, 0, JV, h->st));
   CK(cudaMemsetAsync(h->abar_new, 0, JV, h->st));
+  CK(cudaMemsetAsync(h->f, 0, V * 8, h->st));
+  if (h->phases_set || h->gtn) k_fill_porosity(h->st, (long long)V, h->phase, h->pt_dev, h->f_n);
+  else CK(cudaMemsetAsync(h->f_n, 0, V * 8, h->st));
   CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
   h->n_done = 0;
   for (int c = 0; c < 6; c++) { h->E_prev[c] = 0; h->S_prev[c] = 0; h->sig_mean[c] = 0; h->eps_mean[c] = 0; }
   h->D_mean = h->D_max = 0;
@@ -922,6 +949,8 @@ int reset_state(rve* h) {
 }
 
 void free_all(rve* h) {
+  // tensor maps are cached by buffer address (the spectra of the projection pass)
+  for (void* p : h->allocs) tensor_map_evict(p);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->hctl) cudaFreeHost(h->hctl);
@@ -1046,7 +1075,10 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   AL(dalloc(h, &h->r, nc * V * rs));
   AL(dalloc(h, &h->p, nc * V * rs));
   AL(dalloc(h, &h->Ap, nc * V * rs));
-  AL(dalloc(h, &h->desc, (2 + nc) * V * rs));
+  // tangent descriptor: c1, c2, m (2 + nc rows) or A, B, C, D, nh (4 + nc)
+  AL(dalloc(h, &h->desc, (4 + nc) * V * rs));
+  AL(dalloc_t(h, &h->f_n, V));
+  AL(dalloc_t(h, &h->f, V));
   AL(dalloc(h, &h->S, (size_t)nc * g.sstride * cs));
   AL(dalloc(h, &h->hx, (size_t)g.sstride * cs));
   AL(dalloc(h, &h->hr, (size_t)g.sstride * cs));
@@ -1246,15 +1278,28 @@ int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase
   }
   PhaseTable pt{};
   pt.n_phases = n_phases;
+  bool gtn = false;
   for (int q = 0; q < n_phases; q++) {
     const rve_phase_params& P = params[q];
     if (!(P.E > 0.0) || !(P.nu > -1.0 && P.nu < 0.5)) return RVE_ERR_ARG;
-    if (P.damage_law < 0 || P.damage_law > 2) return RVE_ERR_ARG;
+    if (P.damage_law < 0 || P.damage_law > 3) return RVE_ERR_ARG;
     if (P.nonlocal_var < -1 || P.nonlocal_var >= h->J) return RVE_ERR_ARG;
-    if (P.damage_law == 1 && (!(P.sigma_y > 0.0) || !(P.H >= 0.0))) return RVE_ERR_ARG;
-    if (P.damage_law != 0 && P.nonlocal_var >= 0 &&
+    const bool plastic = P.damage_law == 1 || P.damage_law == 3;
+    if (plastic && (!(P.sigma_y > 0.0) || !(P.H >= 0.0))) return RVE_ERR_ARG;
+    if (P.hardening < 0 || P.hardening > 1 || P.reserved != 0) return RVE_ERR_ARG;
+    if (plastic && P.hardening == 1 && !(P.N > 0.0 && P.N < 1.0)) return RVE_ERR_ARG;
+    if ((P.damage_law == 1 || P.damage_law == 2) && P.nonlocal_var >= 0 &&
         (!(P.eps_R > P.eps_C) || !(P.D_max >= 0.0 && P.D_max < 1.0)))
       return RVE_ERR_ARG;
+    if (P.damage_law == 3) {
+      // two non-local variables (eps_0^p, tr eps^p) at nonlocal_var, +1
+      if (P.nonlocal_var < 0 || P.nonlocal_var + 1 >= h->J) return RVE_ERR_ARG;
+      if (!(P.q1 > 0.0) || !(P.q2 > 0.0) || !(P.q3 > 0.0) || !(P.q1 * P.q1 >= P.q3)) return RVE_ERR_ARG;
+      const double fV = (P.q1 + std::sqrt(P.q1 * P.q1 - P.q3)) / P.q3;
+      if (!(P.f_C >= 0.0) || !(P.f_F > P.f_C) || !(P.f_F < 1.0)) return RVE_ERR_ARG;
+      if (!(P.f_N >= 0.0) || !(P.s_N > 0.0) || !(P.f_0 >= 0.0 && P.f_0 < 1.0)) return RVE_ERR_ARG;
+      if (!(P.fstar_max > 0.0 && P.fstar_max < fV)) return RVE_ERR_ARG;
+    }
     PhaseDev& d = pt.p[q];
     d.K = P.E / (3.0 * (1.0 - 2.0 * P.nu));
     d.mu = P.E / (2.0 * (1.0 + P.nu));
@@ -1266,6 +1311,16 @@ int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase
     d.inv_dCR = P.eps_R > P.eps_C ? 1.0 / (P.eps_R - P.eps_C) : 0.0;
     d.law = P.damage_law;
     d.var = P.damage_law != 0 ? P.nonlocal_var : -1;
+    d.hard = (P.damage_law == 1 || P.damage_law == 3) ? P.hardening : 0;
+    d.pad_ = 0;
+    d.N = P.N;
+    d.c_hard = P.sigma_y > 0.0 ? 3.0 * d.mu / P.sigma_y : 0.0;
+    d.q1 = P.q1; d.q2 = P.q2; d.q3 = P.q3;
+    d.f_C = P.f_C; d.f_F = P.f_F;
+    d.fV = P.q3 > 0.0 && P.q1 * P.q1 >= P.q3 ? (P.q1 + std::sqrt(P.q1 * P.q1 - P.q3)) / P.q3 : 0.0;
+    d.f_N = P.f_N; d.eps_N = P.eps_N; d.s_N = P.s_N;
+    d.f0 = P.f_0; d.fstar_max = P.fstar_max;
+    if (P.damage_law == 3) gtn = true;
   }
   for (int j = 0; j < h->J; j++) {
     double m = 0.0;
@@ -1280,6 +1335,7 @@ int rve_set_phases(rve_t* h, const uint8_t* phase, int n_phases, const rve_phase
   }
   h->pt_host = pt;
   h->n_phases = n_phases;
+  h->gtn = gtn;
   CK(cudaMemcpy(h->phase, hp.data(), V, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->pt_dev, &pt, sizeof(PhaseTable), cudaMemcpyHostToDevice));
   int s = upload_ell2(h);
@@ -1426,6 +1482,7 @@ int rve_get_field(const rve_t* h, int which, double* dst, size_t n) {
     case 3: src = h->abar_n; cnt = (size_t)h->J * V; break;
     case 4: src = h->ep_n; cnt = V; break;
     case 5: src = h->epsp_n; cnt = 6 * V; break;
+    case 6: src = h->f_n; cnt = V; break;
     default: return RVE_ERR_ARG;
   }
   if (n < cnt) return RVE_ERR_ARG;
@@ -1441,14 +1498,28 @@ int rve_op_return_map(rve_t* h, const double* eps, const double* epsp_n, const d
   if (!h || !eps || !epsp_n || !ep_n || !sigma || !epsp || !ep || !D) return RVE_ERR_ARG;
   if (h->J > 0 && (!abar || !alpha)) return RVE_ERR_ARG;
   if (!h->phases_set) return RVE_ERR_STATE;
+  return rve_op_return_map_ex(h, eps, epsp_n, ep_n, abar, nullptr, nullptr, sigma, epsp, ep, D, alpha, nullptr);
+}
+
+int rve_op_return_map_ex(rve_t* h, const double* eps, const double* epsp_n, const double* ep_n,
+                         const double* abar, const double* abar_n, const double* f_n, double* sigma,
+                         double* epsp, double* ep, double* D, double* alpha, double* f) {
+  if (!h || !eps || !epsp_n || !ep_n || !sigma || !epsp || !ep || !D) return RVE_ERR_ARG;
+  if (h->J > 0 && (!abar || !alpha)) return RVE_ERR_ARG;
+  if (!h->phases_set) return RVE_ERR_STATE;
   double* alpha_use = alpha ? alpha : h->alpha;
   const double* abar_use = abar ? abar : h->abar_n;
+  const double* abar_n_use = abar_n ? abar_n : h->abar_n;
+  const double* f_n_use = f_n ? f_n : h->f_n;
+  double* f_use = f ? f : h->f;
   if (h->prec == RVE_MIXED)
     Ops<float>::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, eps, epsp_n, ep_n, abar_use, sigma,
-                           epsp, ep, D, alpha_use, (float*)h->desc, h->part, h->stiff);
+                           epsp, ep, D, alpha_use, (float*)h->desc, h->part, h->stiff, abar_n_use, f_n_use,
+                           f_use, h->gtn);
   else
     Ops<double>::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, eps, epsp_n, ep_n, abar_use,
-                            sigma, epsp, ep, D, alpha_use, (double*)h->desc, h->part, h->stiff);
+                            sigma, epsp, ep, D, alpha_use, (double*)h->desc, h->part, h->stiff, abar_n_use,
+                            f_n_use, f_use, h->gtn);
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   return RVE_OK;
@@ -1457,9 +1528,9 @@ int rve_op_return_map(rve_t* h, const double* eps, const double* epsp_n, const d
 int rve_op_tangent_apply(rve_t* h, const double* p, double* tau) {
   if (!h || !p || !tau) return RVE_ERR_ARG;
   if (h->prec == RVE_MIXED)
-    Ops<float>::tangent_apply64(h->g, h->lc, h->st, (const float*)h->desc, p, tau);
+    Ops<float>::tangent_apply64(h->g, h->lc, h->st, (const float*)h->desc, p, tau, h->gtn);
   else
-    Ops<double>::tangent_apply64(h->g, h->lc, h->st, (const double*)h->desc, p, tau);
+    Ops<double>::tangent_apply64(h->g, h->lc, h->st, (const double*)h->desc, p, tau, h->gtn);
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   return RVE_OK;
@@ -1468,6 +1539,14 @@ int rve_op_tangent_apply(rve_t* h, const double* p, double* tau) {
 int rve_op_apply_gamma(rve_t* h, const double* tau, double* out) {
   if (!h || !tau || !out) return RVE_ERR_ARG;
   return h->prec == RVE_MIXED ? Alg<float>::op_apply_gamma(h, tau, out) : Alg<double>::op_apply_gamma(h, tau, out);
+}
+
+int rve_test_tile_wait(rve_t* h, double wait_s, int extra_tx_bytes) {
+  if (!h || !(wait_s > 0.0 && wait_s <= 60.0) || extra_tx_bytes < 0 || extra_tx_bytes > 4096) return RVE_ERR_ARG;
+  h->tile_wait_s = wait_s;
+  h->tile_extra_tx = extra_tx_bytes;
+  graphs_reset(h);
+  return RVE_OK;
 }
 
 int rve_op_matvec(rve_t* h, const double* p, double* Ap) {
@@ -1552,7 +1631,8 @@ double time_matvec(rve* h, int reps) {
   if (cudaEventCreate(&a) != cudaSuccess) return 1e30;
   if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 1e30; }
   auto once = [&]() {
-    Ops<R>::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S, nullptr);
+    Ops<R>::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S, nullptr,
+                         nullptr, h->gtn);
     Alg<R>::gamma_sweep(h, t, 0, nullptr);
     Ops<R>::xinv_matvec(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, nullptr);
   };
@@ -1863,18 +1943,8 @@ struct AdjSums {
 };
 
 // real-space gradient fields G_d a = F^-1(k_d F a), d = 0..dim-1, into out [d][V]
-void grad_field(rve* h, const Tables<double>& t, const double* a, double* out) {
-  const Geo& g = h->g;
-  using A = Alg<double>;
-  C2<double>* hr = (C2<double>*)h->hr;
-  C2<double>* W = (C2<double>*)h->S;
-  A::forward1(h, t, a, hr);
-  LAUNCHB(h, KC_MISC, 0.0, Ops<double>::helm_expand(g, t, h->lc, h->st, W, (C2<double>*)h->hp, hr, 0.0, nullptr, 1));
-  if (g.d == 3) LAUNCHB(h, KC_MISC, 0.0, Ops<double>::strided_plain(g, t, h->lc, h->st, W, g.d, 1, +1, nullptr));
-  // one component per store (the x1 store kernels exist for 1, 3 and 6)
-  for (int k = 0; k < g.d; k++)
-    LAUNCHB(h, KC_MISC, 0.0, Ops<double>::xinv_store64(g, t, h->lc, h->st, W + (size_t)k * g.sstride, 1,
-                                                       out + (size_t)k * g.V));
+void grad_field(rve* h, const Tables<double>&, const double* a, double* out) {
+  LAUNCHB(h, KC_MISC, 0.0, k_corner_grad64(h->st, h->g, a, out));
 }
 
 // read `n` finalised scalars from the adjoint reduction area
@@ -2016,6 +2086,10 @@ int rve_adjoint_forward(rve_t* h, int checkpoint_every, double* J) {
   if (!h || checkpoint_every < 1) return RVE_ERR_ARG;
   if (h->prec != RVE_FP64) return RVE_ERR_ARG;
   if (!h->phases_set || !h->path_set) return RVE_ERR_STATE;
+  // the local derivative products are written for linear hardening and
+  // laws 0-2
+  for (int q = 0; q < h->n_phases; q++)
+    if (h->pt_host.p[q].hard != 0 || h->pt_host.p[q].law > 2) return RVE_ERR_ARG;
   try {
     int s = adj_setup(h, checkpoint_every);
     if (s) { adjoint_free(h); return s; }
@@ -2104,13 +2178,13 @@ struct StateHeader {
   double E_prev[6], S_prev[6], sig_mean[6], eps_mean[6], D_mean, D_max;
 };
 const char kStateMagic[8] = {'R', 'V', 'E', 'S', 'T', 'A', 'T', '1'};
-constexpr int kStateVersion = 2;
+constexpr int kStateVersion = 3;
 }  // namespace
 
 long long rve_state_bytes(const rve_t* h) {
   if (!h) return 0;
   const long long V = h->g.V;
-  return (long long)sizeof(StateHeader) + (long long)(h->g.nc + 7 + h->J) * V * 8;
+  return (long long)sizeof(StateHeader) + (long long)(h->g.nc + 8 + h->J) * V * 8;
 }
 
 int rve_save_state(const rve_t* h, void* buf, long long bytes) {
@@ -2146,6 +2220,8 @@ int rve_save_state(const rve_t* h, void* buf, long long bytes) {
   CK(cudaMemcpy(p, h->ep_n, V * 8, cudaMemcpyDeviceToHost));
   p += V * 8;
   if (h->J > 0) CK(cudaMemcpy(p, h->abar_n, (size_t)h->J * V * 8, cudaMemcpyDeviceToHost));
+  p += (size_t)h->J * V * 8;
+  CK(cudaMemcpy(p, h->f_n, V * 8, cudaMemcpyDeviceToHost));
   return RVE_OK;
 }
 
@@ -2169,6 +2245,8 @@ int rve_load_state(rve_t* h, const void* buf, long long bytes) {
   CK(cudaMemcpy(h->ep_n, p, V * 8, cudaMemcpyHostToDevice));
   p += V * 8;
   if (h->J > 0) CK(cudaMemcpy(h->abar_n, p, (size_t)h->J * V * 8, cudaMemcpyHostToDevice));
+  p += (size_t)h->J * V * 8;
+  CK(cudaMemcpy(h->f_n, p, V * 8, cudaMemcpyHostToDevice));
   h->n_done = hd.n_done;
   for (int c = 0; c < 6; c++) {
     h->E_prev[c] = hd.E_prev[c];

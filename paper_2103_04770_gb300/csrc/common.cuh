@@ -54,8 +54,17 @@ struct PhaseDev {
   double K, mu, sigma_y, H;
   double eps_C, eps_R, D_max;
   double inv_dCR;   // 1 / (eps_R - eps_C)
-  int law;    // 0 elastic, 1 J2 + Lemaitre damage
-  int var;    // non-local variable fed / read, -1 none
+  int law;    // 0 elastic, 1 J2 + Lemaitre damage, 2 cracking particle, 3 GTN
+  int var;    // non-local variable fed / read (law 3: var and var + 1), -1 none
+  int hard;   // flow stress: 0 linear, 1 Aravas power law
+  int pad_;
+  double N;        // Aravas exponent
+  double c_hard;   // 3 mu / sigma_y of the unscaled phase (Aravas law)
+  // Gurson-Tvergaard-Needleman (law 3)
+  double q1, q2, q3;
+  double f_C, f_F, fV;       // coalescence onset, fracture, f_V* (surface at the origin)
+  double f_N, eps_N, s_N;    // Chu-Needleman nucleation
+  double f0, fstar_max;      // initial porosity, cap on f*
 };
 
 struct PhaseTable {

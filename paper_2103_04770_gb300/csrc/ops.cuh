@@ -305,49 +305,100 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
   if (NS > 0) block_sum_store<NSA>(acc, part, pstride);
 }
 
-// C2R -> l^2(x) * scale -> R2C of the NC = d gradient components (Algorithm 2, GC).
-template <typename R, int NC, int E, int MCT = 0>
-__global__ void __launch_bounds__(kThreads, XMinBlocks<R, E>::v)
-k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, int nrows, R scale,
-       const uint8_t* __restrict__ phase, const R* __restrict__ ell2, const KrylovCtl* __restrict__ ctl) {
+// The Helmholtz operator of Algorithm 2 in real space (reading R15: the
+// spectral GC(a) = a + sum_j conj(k_j) F(l^2 F^-1(k_j a)) with the rotated
+// symbol k_j is, voxel by voxel, the stencil form q + sum_j D_j^T (l^2 D_j q)).
+// This kernel computes the second part,
+//     y = sum_j D_j^T (l^2 * D_j q),
+// D_j the derivative along x_j at the voxel corner n + 1/2 (mean of the
+// forward differences on the 2^(d-1) cube edges parallel to x_j, stored at
+// index n) and l^2 taken at that index).  One CTA covers SX x SY voxels of
+// the (x1, x2) plane and marches along x3 over zc planes, keeping three
+// planes of q (with a one-voxel periodic halo) and two planes of the corner
+// fluxes l^2 D_j q in shared memory.  With N3 = 1 the x3 neighbours are the
+// plane itself, the x3 flux vanishes and the kernel is the 2D stencil.
+constexpr int kStencilX = 32, kStencilY = kThreads / kStencilX;
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_helm_stencil(Geo g, const R* __restrict__ q, R* __restrict__ y, const uint8_t* __restrict__ phase,
+               const R* __restrict__ ell2_tab, R c0, R c1, R c2, int zc, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
-  constexpr int PS = XPad<R, MCT>::v;
-  const int n1 = MCT > 0 ? 2 * MCT : g.n1;
-  const int M = MCT > 0 ? MCT : g.M;
-  const int P1 = MCT > 0 ? MCT + 1 : g.P1;
-  const int ps = MCT > 0 ? ((MCT + 1 + 15) / 16) * 16 : g.ps;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
-  R* rbuf = reinterpret_cast<R*>(tws + g.n1);
-  C2<R>* cbuf = reinterpret_cast<C2<R>*>(rbuf);
-  C2<R>* xs = reinterpret_cast<C2<R>*>(smraw + xstage_off<R>(g.n1, nrows, NC));
-  const long long row0 = (long long)blockIdx.x * nrows;
-  const int rows = (int)lmin_(nrows, g.nlines - row0);
-  for (int i = threadIdx.x; i < g.n1; i += kThreads) tws[i] = tw1[i];
-  xinv_pre_staged<R, NC, PS, MCT>(g, W, row0, rows, nrows, tws, cbuf, xs);
+  constexpr int SX = kStencilX, SY = kStencilY;
+  constexpr int QX = SX + 2, QY = SY + 2;          // q plane with halo
+  constexpr int GX = SX + 1, GY = SY + 1;          // corner plane
+  __shared__ R Q[3][QY][QX];
+  __shared__ R Lw[3][QY][QX];                      // l^2 at each q-tile voxel
+  __shared__ R G[2][3][GY][GX];
+  __shared__ int colx[QX];
+  __shared__ long long rowy[QY];
+  __shared__ R l2[kMaxPhases];
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  const long long plane = (long long)n1 * n2;
+  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, n3);
+  // periodic tile coordinates, once per CTA (tiles may be wider than short axes)
+  if (threadIdx.x < QX) colx[threadIdx.x] = ((x0 - 1 + (int)threadIdx.x) % n1 + n1) % n1;
+  if (threadIdx.x < QY) rowy[threadIdx.x] = (long long)(((y0 - 1 + (int)threadIdx.x) % n2 + n2) % n2) * n1;
+  if (threadIdx.x < kMaxPhases) l2[threadIdx.x] = ell2_tab[threadIdx.x];
   __syncthreads();
-  if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, +1, true, 2, PS>(cbuf, tws);
-  else fft_lines<R, E, +1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
-  const int nvox = rows * n1;
-  for (int e = threadIdx.x; e < nvox; e += kThreads) {
-    const int r = e / n1, x = e - r * n1;
-    const long long v = (row0 + r) * n1 + x;
-    const R w = ell2[phase[v]] * scale;
+  // planes k in [z0 - 1, z1] wrap at most once
+  auto load_plane = [&](int s, int k) {
+    const long long base = (long long)(k < 0 ? k + n3 : (k >= n3 ? k - n3 : k)) * plane;
+    for (int e = threadIdx.x; e < QX * QY; e += kThreads) {
+      const int iy = e / QX, ix = e - iy * QX;
+      const long long idx = base + rowy[iy] + colx[ix];
+      Q[s][iy][ix] = q[idx];
+      Lw[s][iy][ix] = l2[phase[idx]];
+    }
+  };
+  // corner fluxes of corner plane k from q planes a (k) and b (k + 1); l^2
+  // at the corner's own index (plane a)
+  auto corners = [&](int sg, int a, int b) {
+    for (int e = threadIdx.x; e < GX * GY; e += kThreads) {
+      const int cy = e / GX, cx = e - cy * GX;
+      const R q000 = Q[a][cy][cx], q100 = Q[a][cy][cx + 1], q010 = Q[a][cy + 1][cx], q110 = Q[a][cy + 1][cx + 1];
+      const R q001 = Q[b][cy][cx], q101 = Q[b][cy][cx + 1], q011 = Q[b][cy + 1][cx], q111 = Q[b][cy + 1][cx + 1];
+      const R w = Lw[a][cy][cx];
+      G[sg][0][cy][cx] = w * c0 * ((q100 - q000) + (q110 - q010) + (q101 - q001) + (q111 - q011));
+      G[sg][1][cy][cx] = w * c1 * ((q010 - q000) + (q110 - q100) + (q011 - q001) + (q111 - q101));
+      G[sg][2][cy][cx] = w * c2 * ((q001 - q000) + (q101 - q100) + (q011 - q010) + (q111 - q110));
+    }
+  };
+  int s0 = 0, s1 = 1, s2 = 2, gp = 0, gc = 1;
+  load_plane(s0, z0 - 1);
+  load_plane(s1, z0);
+  __syncthreads();
+  corners(gp, s0, s1);
+  const int ix = threadIdx.x % SX, iy = threadIdx.x / SX;
+  const bool mine = x0 + ix < n1 && y0 + iy < n2;
+  const long long obase = (long long)(y0 + iy) * n1 + (x0 + ix);
+  for (int k = z0; k < z1; k++) {
+    load_plane(s2, k + 1);
+    __syncthreads();
+    corners(gc, s1, s2);
+    __syncthreads();
+    if (mine) {
+      // D_j^T of the fluxes at the eight corners around the voxel (the
+      // identity part of L is added to the spectrum, exactly, by the caller)
+      R v = R(0);
 #pragma unroll
-    for (int c = 0; c < NC; c++) rpad<R, PS>(rbuf, (r * NC + c) * n1 + x) *= w;
-  }
-  __syncthreads();
-  if constexpr (MCT > 0) fft_lines_ct<R, MCT, XRows<MCT, NC>::v * NC, 1, MCT, -1, true, 2, PS>(cbuf, tws);
-  else fft_lines<R, E, -1>(cbuf, pl, rows * NC, 1, g.M, true, tws, 2);
-  const int nout = rows * NC * P1;
-  for (int e = threadIdx.x; e < nout; e += kThreads) {
-    const int l = e / P1, k = e - l * P1;
-    const int r = l / NC, c = l - r * NC;
-    const C2<R> zk = cbuf[cpad<PS>(l * M + (k == M ? 0 : k))];
-    const C2<R> zm = cbuf[cpad<PS>(l * M + (k == 0 ? 0 : M - k))];
-    const C2<R> Ek = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-    const C2<R> Ok = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-    W[c * g.sstride + (row0 + r) * ps + k] = Ek + cmul(tws[k], Ok);
+      for (int e = 0; e < 2; e++) {
+        const int cy = iy + 1 - e, cx = ix + 1 - e;
+        v += (G[gc][0][cy][ix] - G[gc][0][cy][ix + 1]) + (G[gp][0][cy][ix] - G[gp][0][cy][ix + 1]);
+        v += (G[gc][1][iy][cx] - G[gc][1][iy + 1][cx]) + (G[gp][1][iy][cx] - G[gp][1][iy + 1][cx]);
+#pragma unroll
+        for (int f = 0; f < 2; f++) v += G[gp][2][cy][ix + 1 - f] - G[gc][2][cy][ix + 1 - f];
+      }
+      y[(long long)k * plane + obase] = v;
+    }
+    const int t0 = s0;
+    s0 = s1;
+    s1 = s2;
+    s2 = t0;
+    const int tg = gp;
+    gp = gc;
+    gc = tg;
   }
 }
 
@@ -356,10 +407,13 @@ k_xmid(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, C2<R>* __restrict__ W, 
 //   desc = [c1, c2, m_0 .. m_{NC-1}],  tau = c1 tr(p) 1 + c2 dev(p) - m (m . p)
 // (c1 = (1-D) K, c2 = (1-D) 2 mu theta, m = sqrt((1-D) 2 mu thetabar) nhat).
 // Inside CG the direction is refreshed first: p <- r (iter 0) or r + beta p.
-template <typename R, int NC>
+template <typename R, int NC, bool EXT = false>
 struct ProTangent {
   // (p, C_T : p) per CTA into part (when part is set): for p in the range of
-  // the projection this equals (p, G*(C_T : p)), the CG curvature
+  // the projection this equals (p, G*(C_T : p)), the CG curvature.
+  // EXT: the descriptor holds A, B, C, D, nh (the GTN handles' tangent
+  // A I(x)I + B P_dev + C nh(x)nh + D (I(x)nh + nh(x)I)); otherwise c1, c2, m
+  // (c1 I(x)I + c2 P_dev - m(x)m).
   static constexpr bool kDot = true;
   R* p;
   const R* r;
@@ -377,10 +431,16 @@ struct ProTangent {
     constexpr int NN = NC == 6 ? 3 : 2;
     // every load first (r, p, descriptor), then the store of the new p:
     // the store could alias the loads, so it would otherwise serialise them
+    constexpr int M0 = EXT ? 4 : 2;
     R pv[NC], m[NC];
     const R c1 = desc[v], c2 = desc[V + v];
+    R cc = R(0), dd = R(0);
+    if constexpr (EXT) {
+      cc = desc[2 * V + v];
+      dd = desc[3 * V + v];
+    }
 #pragma unroll
-    for (int c = 0; c < NC; c++) m[c] = desc[(2 + c) * V + v];
+    for (int c = 0; c < NC; c++) m[c] = desc[(M0 + c) * V + v];
     if (update) {
       R rv[NC], po[NC];
 #pragma unroll
@@ -404,12 +464,23 @@ struct ProTangent {
     for (int c = 0; c < NC; c++) mp += m[c] * pv[c];
     const R third = tr * R(1.0 / 3.0);
     // summed in the working precision per thread and warp, in FP64 above
+    if constexpr (EXT) {
+      const R w = cc * mp + dd * tr;
 #pragma unroll
-    for (int c = 0; c < NC; c++) {
-      R o = c2 * pv[c] - m[c] * mp;
-      if (c < NN) o += c1 * tr - c2 * third;
-      out[c] = o;
-      acc += pv[c] * o;
+      for (int c = 0; c < NC; c++) {
+        R o = c2 * pv[c] + w * m[c];
+        if (c < NN) o += c1 * tr - c2 * third + dd * mp;
+        out[c] = o;
+        acc += pv[c] * o;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        R o = c2 * pv[c] - m[c] * mp;
+        if (c < NN) o += c1 * tr - c2 * third;
+        out[c] = o;
+        acc += pv[c] * o;
+      }
     }
   }
 };
@@ -548,6 +619,24 @@ struct EpiResidual {
     }
     acc[0] += (R)part;
   }
+};
+
+// out[v] = val (one component, working precision)
+template <typename R>
+struct EpiStoreR {
+  static constexpr int kPrefetch = 0;
+  R* out;
+  __device__ void begin(const KrylovCtl*) {}
+  __device__ __forceinline__ void operator()(long long v, const R (&val)[1], R*) const { out[v] = val[0]; }
+};
+
+// tau = f[v] (one component, working precision)
+template <typename R>
+struct ProFieldR {
+  static constexpr bool kDot = false;
+  const R* f;
+  __device__ void begin(const KrylovCtl*) {}
+  __device__ __forceinline__ void operator()(long long v, R (&out)[1]) const { out[0] = f[v]; }
 };
 
 template <typename R, int NC>
@@ -720,6 +809,19 @@ struct LastSym {
     a[2] = t.two_over_h[2] * s2 * c0 * c1;
     dc = m0 == 0 && m1 == 0 && f == 0;
   }
+  // |k|^2 of mode (m0, m1, f) in 3D, (m0, f) in 2D (the preconditioner's
+  // symbol; no phase factor)
+  __device__ __forceinline__ R k2(const Geo& g, const Tables<R>& t, int f) const {
+    if (g.d == 3) {
+      const R s2 = t.s[2][f], c2 = t.c[2][f];
+      const R a0 = t.two_over_h[0] * s0 * c1 * c2, a1 = t.two_over_h[1] * s1 * c0 * c2,
+              a2 = t.two_over_h[2] * s2 * c0 * c1;
+      return a0 * a0 + a1 * a1 + a2 * a2;
+    }
+    const R sf = t.s[1][f], cf = t.c[1][f];
+    const R a0 = t.two_over_h[0] * s0 * cf, a1 = t.two_over_h[1] * sf * c0;
+    return a0 * a0 + a1 * a1;
+  }
   // modes (m0, m1, f) in 3D, (m0, f) in 2D
   __device__ __forceinline__ void at(const Geo& g, const Tables<R>& t, int f, R a[3], C2<R>& ph,
                                      bool& dc) const {
@@ -850,12 +952,16 @@ __host__ __device__ __forceinline__ size_t gamma_tma_head(int N) {
 // The same last-axis pass in 3D with the tile moved by the tensor memory
 // accelerator: one box {TXR columns, NC components, one y plane, NAX z
 // points} lands as [z][c][col] (point stride NC TXR, no padding), and goes
-// back the same way.  A CTA that waits longer than kWaitNs for its tile
-// records it in *wait_err and skips the tile.
+// back the same way.  A CTA that waits longer than wait_ns for its tile
+// records it in *wait_err and skips the tile.  extra_tx > 0 (tests of that
+// path only) adds bytes that no copy delivers to the expected count, so the
+// wait runs out although the copy lands; the CTA then counts those bytes
+// itself, so the phase completes and no copy is in flight when it returns.
 template <typename R, int NC, int TXR, int NAX>
 __global__ void __launch_bounds__(kThreads, 2)
 k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const C2<R>* __restrict__ tw,
-            Mask6 mask, int dc_mode, const KrylovCtl* __restrict__ ctl, int* __restrict__ wait_err) {
+            Mask6 mask, int dc_mode, const KrylovCtl* __restrict__ ctl, int* __restrict__ wait_err,
+            unsigned long long wait_ns, unsigned extra_tx) {
   if (ctl && ctl->done) return;
   constexpr int RS = NC * TXR;
   constexpr int U8 = (int)sizeof(C2<R>) / 8;    // 8-byte elements per complex entry
@@ -870,7 +976,7 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
   const int cols = min(TXR, g.P1 - q0);
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, kBytes);
+    mbar_expect_tx(&bar, kBytes + extra_tx);
     tma_load_4d(buf, &tmap, q0 * U8, 0, blockIdx.y, 0, &bar);
   }
   for (int i = threadIdx.x; i < NAX; i += kThreads) {
@@ -879,9 +985,12 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
     zc[i] = t.c[2][i];
   }
   __syncthreads();
-  if (!mbar_wait(&bar, 0, kWaitNs)) {
-    if (threadIdx.x == 0 && wait_err) atomicExch(wait_err, 1);
-    mbar_wait(&bar, 0, kWaitNs);   // the copy in flight, once more bounded
+  if (!mbar_wait(&bar, 0, wait_ns)) {
+    if (threadIdx.x == 0) {
+      if (wait_err) atomicExch(wait_err, 1);
+      if (extra_tx) mbar_complete_tx(&bar, extra_tx);
+    }
+    mbar_wait(&bar, 0, wait_ns);   // the copy in flight, once more bounded
     return;
   }
   fftreg_forward<R, NAX, NC * TXR, RS>(buf, tws);
@@ -919,8 +1028,9 @@ __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
   return (q1 == 0 || 2 * q1 == g.n1) ? R(1) : R(2);
 }
 
-// Helmholtz: p <- M r + beta p (M = 1/(1 + <l^2>|k|^2)); W_j = k_j p; inverse
-// transform along the last axis.
+// Helmholtz: p <- M r + beta p (M = 1/(1 + <l^2>|k|^2)); W = p (one
+// component, D = 0: the operator is applied in real space) or W_j = k_j p
+// (D > 0); inverse transform along the last axis.
 template <typename R, int D, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 2)
 k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
@@ -931,7 +1041,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = TXR ? NAX : pl.N;
   if (TXR) tx = TXR;
-  constexpr int d = D;
+  constexpr int d = D > 0 ? D : 1;   // transformed components
   constexpr bool IL = TXR > 0;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
@@ -942,7 +1052,37 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
   const bool first = ctl ? ctl->iter == 0 : true;
   const R beta = ctl ? (R)ctl->beta : R(0);
   for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-  if constexpr (IL) {
+  if constexpr (IL && D == 0) {
+    // one column per thread; every load of the thread's entries first, then
+    // p <- M r + beta p (only |k|^2 needed) into tile row reg_pos(n)
+    constexpr int RPT = kThreads / TXR;
+    constexpr int PER = NAX / RPT;
+    const int col = threadIdx.x % TXR, r0 = threadIdx.x / TXR;
+    if (col < cols) {
+      C2<R> rv[PER], pv[PER];
+      const bool upd = !raw && !first;
+#pragma unroll
+      for (int k = 0; k < PER; k++) {
+        const long long idx = off + (long long)(r0 + k * RPT) * astride + col;
+        rv[k] = r[idx];
+        pv[k] = upd ? p[idx] : mk<R>(0, 0);
+      }
+      LastSym<R> sy;
+      sy.init(g, t, q0 + col);
+#pragma unroll
+      for (int k = 0; k < PER; k++) {
+        const int n = r0 + k * RPT;
+        C2<R> pn = rv[k];
+        if (!raw) {
+          const R Mk = R(1) / (R(1) + ell2m * sy.k2(g, t, n));
+          pn = cscale(rv[k], Mk);
+          if (upd) pn = pn + cscale(pv[k], beta);
+          p[off + (long long)n * astride + col] = pn;
+        }
+        buf[reg_pos<NAX>(n) * TXR + col] = pn;
+      }
+    }
+  } else if constexpr (IL) {
     // one column per thread; frequency n goes to tile row reg_pos(n)
     constexpr int RPT = kThreads / TXR;
     const int col = threadIdx.x % TXR;
@@ -965,10 +1105,14 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
           if (!first) pn = pn + cscale(p[idx], beta);
           p[idx] = pn;
         }
-        const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
         const int e0 = reg_pos<NAX>(n) * (d * TXR) + col;
+        if constexpr (D == 0) {
+          buf[e0] = pn;
+        } else {
+          const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
 #pragma unroll
-        for (int j = 0; j < d; j++) buf[e0 + j * TXR] = cscale(ipp, a[j]);
+          for (int j = 0; j < d; j++) buf[e0 + j * TXR] = cscale(ipp, a[j]);
+        }
       }
     }
   } else {
@@ -990,21 +1134,26 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
         if (!first) pn = pn + cscale(p[idx], beta);
         p[idx] = pn;
       }
-      const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
-      for (int j = 0; j < d; j++) buf[e + j * tile] = cscale(ipp, a[j]);
+      if constexpr (D == 0) {
+        buf[e] = pn;
+      } else {
+        const C2<R> ipp = mul_si<R, 1>(cmul(ph, pn));      // i e^{i phi} p
+        for (int j = 0; j < d; j++) buf[e + j * tile] = cscale(ipp, a[j]);
+      }
     }
   }
   __syncthreads();
   if constexpr (IL) {
-    fftreg_inverse<R, NAX, D * TXR>(buf, tws);
+    fftreg_inverse<R, NAX, d * TXR>(buf, tws);
   } else {
     for (int j = 0; j < d; j++) fft_lines<R, E, +1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
   tile_store<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, IL ? TXR : cols, d * tx);
 }
 
-// Helmholtz: forward transform along the last axis, y = p + sum conj(k_j) W_j,
-// partial Hermitian-weighted (p, y).
+// Helmholtz: forward transform along the last axis, y = p + W (D = 0: W is
+// the transform of the real-space flux term, the identity added here exactly)
+// or y = p + sum conj(k_j) W_j (D > 0); partial Hermitian-weighted (p, y).
 template <typename R, int D, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 3)
 k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C2<R>* __restrict__ W,
@@ -1016,7 +1165,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = TXR ? NAX : pl.N;
   if (TXR) tx = TXR;
-  constexpr int d = D;
+  constexpr int d = D > 0 ? D : 1;   // transformed components
   constexpr bool IL = TXR > 0;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
@@ -1040,7 +1189,7 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
   tile_load_async<R, IL>(buf, W + off, d, g.sstride, N, astride, tx, IL ? TXR : cols, d * tx);
   __syncthreads();
   if constexpr (IL) {
-    fftreg_forward<R, NAX, D * TXR>(buf, tws);
+    fftreg_forward<R, NAX, d * TXR>(buf, tws);
   } else {
     for (int j = 0; j < d; j++) fft_lines<R, E, -1>(buf + j * tile, pl, cols, tx, 1, false, tws, 1);
   }
@@ -1054,17 +1203,22 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
 #pragma unroll
       for (int k = 0; k < PER; k++) {
         const int n = threadIdx.x / TXR + k * RPT;
-        R a[3];
-        C2<R> ph;
-        bool dc;
-        sy.at(g, t, n, a, ph, dc);
         const int e0 = reg_pos<NAX>(n) * (d * TXR) + col;
-        C2<R> s = mk<R>(0, 0);
+        C2<R> yv;
+        if constexpr (D == 0) {
+          yv = pv[k] + buf[e0];
+        } else {
+          R a[3];
+          C2<R> ph;
+          bool dc;
+          sy.at(g, t, n, a, ph, dc);
+          C2<R> s = mk<R>(0, 0);
 #pragma unroll
-        for (int j = 0; j < d; j++) s = s + cscale(buf[e0 + j * TXR], a[j]);
-        // conj(k_j) = -i e^{-i phi} a_j
-        const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
-        const C2<R> yv = pv[k] + ks;
+          for (int j = 0; j < d; j++) s = s + cscale(buf[e0 + j * TXR], a[j]);
+          // conj(k_j) = -i e^{-i phi} a_j
+          const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
+          yv = pv[k] + ks;
+        }
         y[off + n * astride + col] = yv;
         acc[0] += w1 * (pv[k].x * yv.x + pv[k].y * yv.y);
       }
@@ -1075,16 +1229,21 @@ k_contract(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, const C
       if (col >= cols) continue;
       int m0, m1, m2;
       last_modes(g, q0, col, n, m0, m1, m2);
-      R a[3];
-      C2<R> ph;
-      symbol(g, t, m0, m1, m2, a, ph);
-      C2<R> s = mk<R>(0, 0);
-      for (int j = 0; j < d; j++) s = s + cscale(buf[e + j * tile], a[j]);
-      // conj(k_j) = -i e^{-i phi} a_j
-      const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
       const long long idx = off + n * astride + col;
       const C2<R> pn = p[idx];
-      const C2<R> yv = pn + ks;
+      C2<R> yv;
+      if constexpr (D == 0) {
+        yv = pn + buf[e];
+      } else {
+        R a[3];
+        C2<R> ph;
+        symbol(g, t, m0, m1, m2, a, ph);
+        C2<R> s = mk<R>(0, 0);
+        for (int j = 0; j < d; j++) s = s + cscale(buf[e + j * tile], a[j]);
+        // conj(k_j) = -i e^{-i phi} a_j
+        const C2<R> ks = mul_si<R, -1>(cmul(conj_(ph), s));
+        yv = pn + ks;
+      }
       y[idx] = yv;
       acc[0] += q1_weight<R>(g, m0) * (pn.x * yv.x + pn.y * yv.y);
     }
@@ -1311,14 +1470,197 @@ __device__ __forceinline__ double positive_principal_norm(const double (&e)[6]) 
   return sqrt(k);
 }
 
-template <typename R>
+// Flow stress sigma_0(e) and slope d sigma_0 / d e of a phase.  Linear:
+// sigma_y + H e.  Aravas power law (Section 4.1, Eq. aravas):
+// y = sigma_0 / sigma_y solves g(y) = y - (y + c)^N = 0 with c = 3 mu e /
+// sigma_y; g is increasing and convex on y >= 1 with g(1) <= 0, so Newton
+// from y = 1 lands right of the root after one step and then decreases
+// monotonically onto it.  Slope: 3 mu w / (1 - w), w = N (y + c)^(N - 1).
+__device__ __forceinline__ void flow_stress(const PhaseDev& P, double e, double& s0, double& Hp) {
+  if (P.hard == 0) {
+    s0 = P.sigma_y + P.H * e;
+    Hp = P.H;
+    return;
+  }
+  const double c = P.c_hard * e;
+  double y = 1.0;
+  for (int it = 0; it < 60; it++) {
+    const double z = pow(y + c, P.N);
+    const double w = P.N * z / (y + c);
+    const double dy = (y - z) / (1.0 - w);
+    y -= dy;
+    if (fabs(dy) <= 1e-16 * y) break;
+  }
+  const double w = P.N * pow(y + c, P.N - 1.0);
+  s0 = P.sigma_y * y;
+  Hp = P.sigma_y * P.c_hard * w / (1.0 - w);
+}
+
+// ------------------------------------------------ Gurson-Tvergaard-Needleman
+// Backward-Euler update of one voxel of the non-local GTN model (Section
+// 2.1.1, Section 2.2.2, Appendix A.1) with the porosity f (hence f*) fixed by
+// the frozen non-local variables.  Unknowns x = (d_v, d_q, e0): the plastic
+// strain increment d_v I/3 + d_q n along the trial direction n =
+// (3/2) s_dev / s (normality of the cosh surface), the matrix equivalent
+// plastic strain e0; pressure p = p_tr + K d_v, Mises stress s = s_tr -
+// 3 mu d_q.  Residuals:
+//   R1 = (s/s0)^2 + 2 f* q1 cosh(3 q2 p / (2 s0)) - 1 - q3 f*^2     (yield)
+//   R2 = 2 s d_v / s0 + 3 q1 q2 f* sinh(3 q2 p / (2 s0)) d_q      (normality)
+//   R3 = (1 - f)(e0 - e0_n) + (p d_v - s d_q) / s0                (work balance)
+// solved by Newton with backtracking; the consistent tangent (f fixed) is
+// A I(x)I + B P_dev + C nh(x)nh + D (I(x)nh + nh(x)I), nh = n / |n|, from the
+// derivatives of x with respect to the trial invariants (s_tr, p_tr).
+struct GtnPoint {
+  double sig[6], dep[6];
+  double e0, f, fs;
+  double A, B, C, D, nh[6];
+  int ok;
+};
+
+__device__ __forceinline__ void gtn_eval(const PhaseDev& P, double K, double mu, double f, double fs, double s_tr,
+                                         double p_tr, double e0n, double dv, double dq, double e0, double (&Rv)[3],
+                                         double (&Jm)[3][3], double (&Rs)[3], double (&Rp)[3]) {
+  const double s = s_tr - 3.0 * mu * dq;
+  const double p = p_tr + K * dv;
+  double s0, H;
+  flow_stress(P, e0, s0, H);
+  const double is0 = 1.0 / s0;
+  const double a = 1.5 * P.q2 * p * is0;
+  const double ch = cosh(a), sh = sinh(a);
+  const double so = s * is0;
+  const double k3 = 3.0 * P.q1 * P.q2 * fs;
+  Rv[0] = so * so + 2.0 * fs * P.q1 * ch - 1.0 - P.q3 * fs * fs;
+  Rv[1] = 2.0 * so * dv + k3 * sh * dq;
+  Rv[2] = (1.0 - f) * (e0 - e0n) + (p * dv - s * dq) * is0;
+  Jm[0][0] = k3 * K * sh * is0;
+  Jm[0][1] = -6.0 * mu * so * is0;
+  Jm[0][2] = -H * is0 * (2.0 * so * so + 2.0 * fs * P.q1 * a * sh);
+  Jm[1][0] = 2.0 * so + k3 * dq * ch * 1.5 * P.q2 * K * is0;
+  Jm[1][1] = -6.0 * mu * dv * is0 + k3 * sh;
+  Jm[1][2] = -2.0 * so * dv * H * is0 - k3 * dq * ch * a * H * is0;
+  Jm[2][0] = (K * dv + p) * is0;
+  Jm[2][1] = (3.0 * mu * dq - s) * is0;
+  Jm[2][2] = (1.0 - f) - (p * dv - s * dq) * H * is0 * is0;
+  Rs[0] = 2.0 * so * is0;
+  Rs[1] = 2.0 * dv * is0;
+  Rs[2] = -dq * is0;
+  Rp[0] = k3 * sh * is0;
+  Rp[1] = k3 * dq * ch * 1.5 * P.q2 * is0;
+  Rp[2] = dv * is0;
+}
+
+// x = J^-1 b for a 3x3 system (Cramer's rule); false if singular
+__device__ __forceinline__ bool solve3(const double (&Jm)[3][3], const double (&b)[3], double (&x)[3]) {
+  const double c00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+  const double c01 = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+  const double c02 = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+  const double det = Jm[0][0] * c00 + Jm[0][1] * c01 + Jm[0][2] * c02;
+  if (!(fabs(det) > 0.0)) return false;
+  const double id = 1.0 / det;
+  const double c10 = Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2];
+  const double c11 = Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0];
+  const double c12 = Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1];
+  const double c20 = Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1];
+  const double c21 = Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2];
+  const double c22 = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+  x[0] = (c00 * b[0] + c10 * b[1] + c20 * b[2]) * id;
+  x[1] = (c01 * b[0] + c11 * b[1] + c21 * b[2]) * id;
+  x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * id;
+  return true;
+}
+
+static __device__ __noinline__ void gtn_point(const PhaseDev& P, double K, double mu, const double (&ee)[6], double e0n,
+                                       double fn, double a0, double a0n, double at, double atn, GtnPoint& o) {
+  // porosity from the frozen non-local eps_0^p (a0) and tr eps^p (at)
+  const double dat = at - atn;
+  const double z = (a0 - P.eps_N) / P.s_N;
+  const double AN = P.f_N / (P.s_N * 2.50662827463100050242) * exp(-0.5 * z * z);
+  const double f = (fn + AN * (a0 - a0n) + dat) / (1.0 + dat);
+  double fs = f < P.f_C ? f : (f < P.f_F ? P.f_C + (P.fV - P.f_C) / (P.f_F - P.f_C) * (f - P.f_C) : P.fV);
+  fs = fmin(fmax(fs, 0.0), P.fstar_max);
+  o.f = f;
+  o.fs = fs;
+  o.ok = 1;
+  const double tr = ee[0] + ee[1] + ee[2];
+  double dev[6], dd = 0.0;
+  for (int c = 0; c < 6; c++) {
+    dev[c] = ee[c] - (c < 3 ? tr * (1.0 / 3.0) : 0.0);
+    dd += dev[c] * dev[c];
+  }
+  const double p_tr = -K * tr;
+  const double s_tr = 2.0 * mu * sqrt(1.5 * dd);
+  const double in = s_tr > 0.0 ? 3.0 * mu / s_tr : 0.0;   // n = 1.5 (2 mu dev) / s_tr
+  double n[6];
+  for (int c = 0; c < 6; c++) n[c] = in * dev[c];
+  double s0n, hn;
+  flow_stress(P, e0n, s0n, hn);
+  const double atr = 1.5 * P.q2 * p_tr / s0n;
+  const double phi_tr = (s_tr / s0n) * (s_tr / s0n) + 2.0 * fs * P.q1 * cosh(atr) - 1.0 - P.q3 * fs * fs;
+  if (!(phi_tr > 0.0)) {
+    for (int c = 0; c < 6; c++) {
+      o.sig[c] = (c < 3 ? K * tr : 0.0) + 2.0 * mu * dev[c];
+      o.dep[c] = 0.0;
+      o.nh[c] = 0.0;
+    }
+    o.e0 = e0n;
+    o.A = K;
+    o.B = 2.0 * mu;
+    o.C = 0.0;
+    o.D = 0.0;
+    return;
+  }
+  double x[3] = {0.0, 0.0, e0n}, Rv[3], Jm[3][3], Rs[3], Rp[3];
+  gtn_eval(P, K, mu, f, fs, s_tr, p_tr, e0n, x[0], x[1], x[2], Rv, Jm, Rs, Rp);
+  double r0 = sqrt(Rv[0] * Rv[0] + Rv[1] * Rv[1] + Rv[2] * Rv[2]);
+  bool conv = false;
+  for (int it = 0; it < 60 && !conv; it++) {
+    double st[3];
+    if (!solve3(Jm, Rv, st)) break;
+    double lam = 1.0, xn[3], rn = 0.0;
+    for (int bt = 0; bt < 40; bt++) {
+      for (int k = 0; k < 3; k++) xn[k] = x[k] - lam * st[k];
+      gtn_eval(P, K, mu, f, fs, s_tr, p_tr, e0n, xn[0], xn[1], xn[2], Rv, Jm, Rs, Rp);
+      rn = sqrt(Rv[0] * Rv[0] + Rv[1] * Rv[1] + Rv[2] * Rv[2]);
+      if (rn <= r0 * (1.0 - 1e-4 * lam) || !(r0 > 1e-15)) break;
+      lam *= 0.5;
+    }
+    conv = true;
+    for (int k = 0; k < 3; k++) {
+      conv = conv && fabs(lam * st[k]) <= 1e-12 * fmax(fabs(xn[k]), 1e-4);
+      x[k] = xn[k];
+    }
+    r0 = rn;
+  }
+  // x and the Jacobian at x (the last evaluation) give the update and tangent
+  o.ok = conv && fabs(Rv[0]) <= 1e-10 && fabs(Rv[1]) <= 1e-10 && fabs(Rv[2]) <= 1e-10;
+  const double dv = x[0], dq = x[1];
+  const double s = s_tr - 3.0 * mu * dq, p = p_tr + K * dv;
+  for (int c = 0; c < 6; c++) {
+    o.sig[c] = (c < 3 ? -p : 0.0) + (2.0 / 3.0) * s * n[c];
+    o.dep[c] = (c < 3 ? dv * (1.0 / 3.0) : 0.0) + dq * n[c];
+  }
+  o.e0 = x[2];
+  double dxs[3], dxp[3];
+  const double ms[3] = {-Rs[0], -Rs[1], -Rs[2]}, mp[3] = {-Rp[0], -Rp[1], -Rp[2]};
+  if (!solve3(Jm, ms, dxs) || !solve3(Jm, mp, dxp)) o.ok = 0;
+  const double sr = s_tr > 0.0 ? s / s_tr : 1.0;
+  const double r23 = 0.81649658092772603273;   // sqrt(2/3): nh = sqrt(2/3) n
+  o.A = K * (1.0 + K * dxp[0]);
+  o.B = 2.0 * mu * sr;
+  o.C = 2.0 * mu * (1.0 - 3.0 * mu * dxs[1]) - 2.0 * mu * sr;
+  o.D = 1.22474487139158904909 * mu * K * (dxp[1] - dxs[0]);   // sqrt(3/2) mu K (b_p - a_s)
+  for (int c = 0; c < 6; c++) o.nh[c] = r23 * n[c];
+}
+
+template <typename R, bool GTN>
 __global__ void __launch_bounds__(kThreads)
 k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __restrict__ phase,
              const double* __restrict__ eps, const double* __restrict__ epsp_n,
              const double* __restrict__ ep_n, const double* __restrict__ abar,
              double* __restrict__ sigma, double* __restrict__ epsp, double* __restrict__ ep,
              double* __restrict__ Dout, double* __restrict__ alpha, R* __restrict__ desc,
-             double* __restrict__ part, int pstride, const double* __restrict__ stiff) {
+             double* __restrict__ part, int pstride, const double* __restrict__ stiff,
+             const double* __restrict__ abar_n, const double* __restrict__ f_n, double* __restrict__ f_out) {
   const long long V = g.V;
   const int nc = g.nc;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -1337,20 +1679,72 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
     // per-voxel modulus factor (1 without a stiffness field)
     const double sc = stiff ? stiff[v] : 1.0;
     const double K = P.K * sc, mu = P.mu * sc;
+    const double epn = ep_n[v];
+    if constexpr (GTN) {
+      if (P.law == 3) {
+        GtnPoint o;
+        const int j0 = P.var, j1 = P.var + 1;
+        gtn_point(P, K, mu, e, epn, f_n[v], abar[j0 * V + v], abar_n[j0 * V + v], abar[j1 * V + v],
+                  abar_n[j1 * V + v], o);
+        // a local update that did not converge poisons the stress, so the
+        // Newton residual turns non-finite and the increment is rejected
+        const double bad = o.ok ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
+        for (int c = 0; c < 6; c++) {
+          const double sgc = o.sig[c] + bad;
+          sigma[c * V + v] = sgc;
+          epsp[c * V + v] = pn[c] + o.dep[c];
+          acc[c] += sgc;
+        }
+        ep[v] = o.e0;
+        Dout[v] = o.fs;
+        f_out[v] = o.f;
+        // the regularised variables: eps_0^p and the trace of the total
+        // plastic strain (Eq. helmholta_gurson)
+        const double trp = (pn[0] + o.dep[0]) + (pn[1] + o.dep[1]) + (pn[2] + o.dep[2]);
+        for (int j = 0; j < J; j++) alpha[j * V + v] = j == j0 ? o.e0 : (j == j1 ? trp : 0.0);
+        acc[6] += o.fs;
+        dmx[0] = fmax(dmx[0], o.fs);
+        desc[v] = (R)o.A;
+        desc[V + v] = (R)o.B;
+        desc[2 * V + v] = (R)o.C;
+        desc[3 * V + v] = (R)o.D;
+        for (int c = 0; c < nc; c++) desc[(4 + c) * V + v] = (R)o.nh[g.cmap[c]];
+        continue;
+      }
+      f_out[v] = f_n[v];
+    }
     double q = 0.0;
     for (int c = 0; c < 6; c++) q += dev[c] * dev[c];
     q = 2.0 * mu * sqrt(q);
-    const double epn = ep_n[v];
     double dl = 0.0, theta = 1.0, thetab = 0.0, D = 0.0;
     double nh[6] = {0, 0, 0, 0, 0, 0};
     if (P.law == 1) {
-      const double f = q - s23 * (P.sigma_y + P.H * epn);
+      double s0n, hn;
+      flow_stress(P, epn, s0n, hn);
+      const double f = q - s23 * s0n;
       if (f > 0.0) {
-        // two FP64 divisions per plastic voxel (division is slow on the FP64
-        // pipe): 2 mu + 2H/3 = (2/3)(3 mu + H), so 1/(3 mu + H) serves the
-        // multiplier and thetabar, 1/q the flow direction and theta
-        const double ih = 1.0 / (3.0 * mu + P.H);
-        dl = 1.5 * f * ih;
+        double ih;
+        if (P.hard == 0) {
+          // two FP64 divisions per plastic voxel (division is slow on the
+          // FP64 pipe): 2 mu + 2H/3 = (2/3)(3 mu + H), so 1/(3 mu + H) serves
+          // the multiplier and thetabar, 1/q the flow direction and theta
+          ih = 1.0 / (3.0 * mu + P.H);
+          dl = 1.5 * f * ih;
+        } else {
+          // q - 2 mu dl - sqrt(2/3) sigma_0(ep_n + sqrt(2/3) dl) = 0 is convex
+          // and decreasing in dl and positive at 0: Newton from 0 rises
+          // monotonically onto the root
+          double x = 0.0, s0 = s0n, hp = hn;
+          for (int it = 0; it < 60; it++) {
+            const double r = q - 2.0 * mu * x - s23 * s0;
+            const double dx = 1.5 * r / (3.0 * mu + hp);
+            x += dx;
+            flow_stress(P, epn + s23 * x, s0, hp);
+            if (!(dx > 1e-16 * x)) break;
+          }
+          dl = x;
+          ih = 1.0 / (3.0 * mu + hp);   // thetabar with the slope at the end point
+        }
         const double iq = 1.0 / q;
         for (int c = 0; c < 6; c++) nh[c] = 2.0 * mu * dev[c] * iq;
         theta = 1.0 - 2.0 * mu * dl * iq;
@@ -1390,10 +1784,17 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
     dmx[0] = fmax(dmx[0], D);
     desc[v] = (R)(om * K);
     desc[V + v] = (R)(om * 2.0 * mu * theta);
-    // the descriptor is stored in the working precision: its square root in
-    // that precision too
-    const R ms = sqrt((R)(om * 2.0 * mu * thetab));
-    for (int c = 0; c < nc; c++) desc[(2 + c) * V + v] = ms * (R)nh[g.cmap[c]];
+    if constexpr (GTN) {
+      // extended layout A, B, C, D, nh (the GTN handles' tangent form)
+      desc[2 * V + v] = (R)(-om * 2.0 * mu * thetab);
+      desc[3 * V + v] = R(0);
+      for (int c = 0; c < nc; c++) desc[(4 + c) * V + v] = (R)nh[g.cmap[c]];
+    } else {
+      // the descriptor is stored in the working precision: its square root
+      // in that precision too
+      const R ms = sqrt((R)(om * 2.0 * mu * thetab));
+      for (int c = 0; c < nc; c++) desc[(2 + c) * V + v] = ms * (R)nh[g.cmap[c]];
+    }
   }
   block_sum_store<7>(acc, part, pstride);
   __syncthreads();
@@ -1402,15 +1803,27 @@ k_return_map(Geo g, const PhaseTable* __restrict__ pt, int J, const uint8_t* __r
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_tangent64(Geo g, const R* __restrict__ desc, const double* __restrict__ p, double* __restrict__ tau) {
+k_tangent64(Geo g, const R* __restrict__ desc, const double* __restrict__ p, double* __restrict__ tau, int ext) {
   const long long V = g.V;
   const int nc = g.nc, nn = g.d == 3 ? 3 : 2;
   for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
     double pv[6], tr = 0.0, mp = 0.0;
     for (int c = 0; c < nc; c++) pv[c] = p[c * V + v];
     for (int c = 0; c < nn; c++) tr += pv[c];
-    for (int c = 0; c < nc; c++) mp += (double)desc[(2 + c) * V + v] * pv[c];
+    const int m0 = ext ? 4 : 2;
+    for (int c = 0; c < nc; c++) mp += (double)desc[(m0 + c) * V + v] * pv[c];
     const double c1 = desc[v], c2 = desc[V + v];
+    if (ext) {
+      // A tr(p) I + B dev(p) + C (nh.p) nh + D ((nh.p) I + tr(p) nh)
+      const double cc = desc[2 * V + v], dd = desc[3 * V + v];
+      for (int c = 0; c < nc; c++) {
+        const double n = desc[(4 + c) * V + v];
+        double o = c2 * pv[c] + (cc * mp + dd * tr) * n;
+        if (c < nn) o += (c1 - c2 / 3.0) * tr + dd * mp;
+        tau[c * V + v] = o;
+      }
+      continue;
+    }
     for (int c = 0; c < nc; c++) {
       double o = c2 * pv[c] - (double)desc[(2 + c) * V + v] * mp;
       if (c < nn) o += c1 * tr - c2 * tr / 3.0;
@@ -1515,25 +1928,30 @@ static int axis_tx(const LaunchCfg& lc, int N, int ncomp) {
   }
 }
 
-template <typename R, int NC>
+template <typename R, int NC, bool EXT>
 static void xfwd_tangent_nc(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
                             const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl, double* part) {
-  ProTangent<R, NC> pro;
+  ProTangent<R, NC, EXT> pro;
   pro.p = p; pro.r = r; pro.desc = desc; pro.V = g.V;
   pro.update = ctl != nullptr; pro.beta = R(0); pro.first = true;
   pro.part = part; pro.pstride = lc.max_blocks;
-#define KCT_(M) (k_xfwd<R, NC, 4, ProTangent<R, NC>, M>)
-  XLAUNCH(KCT_, (k_xfwd<R, NC, 4, ProTangent<R, NC>>),
-          (k_xfwd<R, NC, 16, ProTangent<R, NC>>), NC, false,
+#define KCT_(M) (k_xfwd<R, NC, 4, ProTangent<R, NC, EXT>, M>)
+  XLAUNCH(KCT_, (k_xfwd<R, NC, 4, ProTangent<R, NC, EXT>>),
+          (k_xfwd<R, NC, 16, ProTangent<R, NC, EXT>>), NC, false,
           g, t.plan_x, t.tw[0], S, nr, pro, ctl);
 #undef KCT_
 }
 
 template <typename R>
 void Ops<R>::xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, R* p,
-                          const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl, double* part) {
-  if (g.nc == 6) xfwd_tangent_nc<R, 6>(g, t, lc, st, p, r, desc, S, ctl, part);
-  else xfwd_tangent_nc<R, 3>(g, t, lc, st, p, r, desc, S, ctl, part);
+                          const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl, double* part, int ext) {
+  if (ext) {
+    if (g.nc == 6) xfwd_tangent_nc<R, 6, true>(g, t, lc, st, p, r, desc, S, ctl, part);
+    else xfwd_tangent_nc<R, 3, true>(g, t, lc, st, p, r, desc, S, ctl, part);
+  } else {
+    if (g.nc == 6) xfwd_tangent_nc<R, 6, false>(g, t, lc, st, p, r, desc, S, ctl, part);
+    else xfwd_tangent_nc<R, 3, false>(g, t, lc, st, p, r, desc, S, ctl, part);
+  }
 }
 
 template <typename R, int NC>
@@ -1655,18 +2073,40 @@ void Ops<R>::xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc,
 }
 
 template <typename R>
-void Ops<R>::xmid_ell(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* W,
-                      const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl) {
-#define KCT3_(M) (k_xmid<R, 3, 4, M>)
-#define KCT2_(M) (k_xmid<R, 2, 4, M>)
-  if (g.d == 3)
-    XLAUNCH(KCT3_, (k_xmid<R, 3, 4>), (k_xmid<R, 3, 16>), 3, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
-            ell2_tab, ctl);
-  else
-    XLAUNCH(KCT2_, (k_xmid<R, 2, 4>), (k_xmid<R, 2, 16>), 2, true, g, t.plan_x, t.tw[0], W, nr, R(2.0 / (double)g.V), phase,
-            ell2_tab, ctl);
-#undef KCT3_
-#undef KCT2_
+void Ops<R>::xinv_storeR(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, const C2<R>* S,
+                         R* out, const KrylovCtl* ctl) {
+  EpiStoreR<R> epi;
+  epi.out = out;
+#define KCT_(M) (k_xinv<R, 1, 4, EpiStoreR<R>, 0, M>)
+  XLAUNCH(KCT_, (k_xinv<R, 1, 4, EpiStoreR<R>, 0>), (k_xinv<R, 1, 16, EpiStoreR<R>, 0>), 1, true,
+          g, t.plan_x, t.tw[0], S, nr, R(2.0 / (double)g.V), epi, nullptr, 0, ctl);
+#undef KCT_
+}
+
+template <typename R>
+void Ops<R>::xfwd_fieldR(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, const R* f,
+                         C2<R>* S, const KrylovCtl* ctl) {
+  ProFieldR<R> pro;
+  pro.f = f;
+#define KCT_(M) (k_xfwd<R, 1, 4, ProFieldR<R>, M>)
+  XLAUNCH(KCT_, (k_xfwd<R, 1, 4, ProFieldR<R>>), (k_xfwd<R, 1, 16, ProFieldR<R>>), 1, false,
+          g, t.plan_x, t.tw[0], S, nr, pro, ctl);
+#undef KCT_
+}
+
+template <typename R>
+void Ops<R>::helm_stencil(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const R* q, R* y,
+                          const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl) {
+  // corner derivative: mean of 2^(d-1) forward differences over h_j; the
+  // kernel sums four edge differences per corner (twice the same two in 2D,
+  // where the x3 neighbour is the plane itself), so 1 / (4 h_j) per D_j and
+  // the same for D_j^T
+  const R c0 = (R)(1.0 / (16.0 * g.h[0] * g.h[0]));
+  const R c1 = (R)(1.0 / (16.0 * g.h[1] * g.h[1]));
+  const R c2 = g.d == 3 ? (R)(1.0 / (16.0 * g.h[2] * g.h[2])) : R(0);
+  const int zc = g.n3 < 16 ? g.n3 : 16;
+  dim3 grid((g.n1 + kStencilX - 1) / kStencilX, (g.n2 + kStencilY - 1) / kStencilY, (g.n3 + zc - 1) / zc);
+  k_helm_stencil<R><<<grid, kThreads, 0, st>>>(g, q, y, phase, ell2_tab, c0, c1, c2, zc, ctl);
 }
 
 template <typename R>
@@ -1696,7 +2136,9 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
 
 template <typename R>
 void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st, C2<R>* S,
-                   const float* stress_mask, int dc_mode, const KrylovCtl* ctl, int* wait_err) {
+                   const float* stress_mask, int dc_mode, const KrylovCtl* ctl, int* wait_err, double wait_s,
+                   int extra_tx) {
+  const unsigned long long wait_ns = (unsigned long long)(wait_s * 1e9);
   const int axis = g.d - 1;
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
@@ -1725,7 +2167,8 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
       dim3 gt((g.P1 + TX6 - 1) / TX6, g.n2, 1);
       auto launch = [&](auto k) {
         set_smem(k, smt);
-        k<<<gt, kThreads, smt, st>>>(g, t, *map, t.tw[axis], m, dc_mode, ctl, wait_err);
+        k<<<gt, kThreads, smt, st>>>(g, t, *map, t.tw[axis], m, dc_mode, ctl, wait_err, wait_ns,
+                                     (unsigned)extra_tx);
       };
       if (si.N == 256) launch(k_gamma_tma<R, 6, TX6, 256>);
       else if (si.N == 128) launch(k_gamma_tma<R, 6, TX6, 128>);
@@ -1755,30 +2198,21 @@ void Ops<R>::helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, 
   const int axis = g.d - 1;
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
-  const int tx = axis_tx<R>(lc, si.N, g.d);
-  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
+  const int tx = axis_tx<R>(lc, si.N, 1);
+  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
     return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
   };
-  if (g.d == 3) {
-    constexpr int T = RegTx<R, 3>::v;
-    auto k = pick(k_expand<R, 3, T, 256>, k_expand<R, 3, T, 128>, k_expand<R, 3, T, 64>, k_expand<R, 3>);
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
-                                  raw);
-  } else {
-    constexpr int T = RegTx<R, 2>::v;
-    auto k = pick(k_expand<R, 2, T, 256>, k_expand<R, 2, T, 128>, k_expand<R, 2, T, 64>, k_expand<R, 2>);
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl,
-                                  raw);
-  }
+  constexpr int T = RegTx<R, 1>::v;
+  auto k = pick(k_expand<R, 0, T, 256>, k_expand<R, 0, T, 128>, k_expand<R, 0, T, 64>, k_expand<R, 0>);
+  set_smem(k, sm);
+  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, r, tx, si.astride, si.ostride, (R)ell2_mean, ctl, raw);
 }
 
 template <typename R>
 int Ops<R>::contract_blocks(const Geo& g, const LaunchCfg& lc) {
-  const int tx = axis_tx<R>(lc, g.d == 3 ? g.n3 : g.n2, g.d);
+  const int tx = axis_tx<R>(lc, g.d == 3 ? g.n3 : g.n2, 1);
   return ((g.P1 + tx - 1) / tx) * (g.d == 3 ? g.n2 : 1);
 }
 
@@ -1788,25 +2222,17 @@ void Ops<R>::helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const int axis = g.d - 1;
   const StrideInfo<R> si = stride_of<R>(g, axis);
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
-  const int tx = axis_tx<R>(lc, si.N, g.d);
-  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * g.d * tx;
+  const int tx = axis_tx<R>(lc, si.N, 1);
+  const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
   dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? 1 : g.n2, 1);
   auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
     return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
   };
-  if (g.d == 3) {
-    constexpr int T = RegTx<R, 3>::v;
-    auto k = pick(k_contract<R, 3, T, 256>, k_contract<R, 3, T, 128>, k_contract<R, 3, T, 64>, k_contract<R, 3>);
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
-                                  lc.max_blocks, ctl);
-  } else {
-    constexpr int T = RegTx<R, 2>::v;
-    auto k = pick(k_contract<R, 2, T, 256>, k_contract<R, 2, T, 128>, k_contract<R, 2, T, 64>, k_contract<R, 2>);
-    set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part,
-                                  lc.max_blocks, ctl);
-  }
+  constexpr int T = RegTx<R, 1>::v;
+  auto k = pick(k_contract<R, 0, T, 256>, k_contract<R, 0, T, 128>, k_contract<R, 0, T, 64>, k_contract<R, 0>);
+  set_smem(k, sm);
+  k<<<grid, kThreads, sm, st>>>(g, t, pl, t.tw[axis], W, p, y, tx, si.astride, si.ostride, part, lc.max_blocks,
+                                ctl);
 }
 
 template <typename R>
@@ -1839,15 +2265,22 @@ template <typename R>
 void Ops<R>::return_map(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const PhaseTable* pt, int J,
                         const uint8_t* phase, const double* eps, const double* epsp_n, const double* ep_n,
                         const double* abar, double* sigma, double* epsp, double* ep, double* D,
-                        double* alpha, R* desc, double* part, const double* stiff) {
-  k_return_map<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, pt, J, phase, eps, epsp_n, ep_n, abar, sigma,
-                                                       epsp, ep, D, alpha, desc, part, lc.max_blocks, stiff);
+                        double* alpha, R* desc, double* part, const double* stiff, const double* abar_n,
+                        const double* f_n, double* f_out, int gtn) {
+  if (gtn)
+    k_return_map<R, true><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, pt, J, phase, eps, epsp_n, ep_n, abar, sigma,
+                                                               epsp, ep, D, alpha, desc, part, lc.max_blocks,
+                                                               stiff, abar_n, f_n, f_out);
+  else
+    k_return_map<R, false><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, pt, J, phase, eps, epsp_n, ep_n, abar, sigma,
+                                                                epsp, ep, D, alpha, desc, part, lc.max_blocks,
+                                                                stiff, abar_n, f_n, f_out);
 }
 
 template <typename R>
 void Ops<R>::tangent_apply64(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const R* desc,
-                             const double* p, double* tau) {
-  k_tangent64<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, desc, p, tau);
+                             const double* p, double* tau, int ext) {
+  k_tangent64<R><<<lc.n_ew_blocks, kThreads, 0, st>>>(g, desc, p, tau, ext);
 }
 
 template <typename R>

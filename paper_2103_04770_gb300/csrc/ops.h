@@ -51,9 +51,11 @@ struct Ops {
   // ---------------------------------------------------------------- x1 passes
   // forward: tau = C_T : p  (with p <- r + beta p when ctl != null and iter > 0);
   // partial (p, tau) into part when part != null
+  // ext: descriptor in the extended layout A, B, C, D, nh (handles with a
+  // GTN phase), else c1, c2, m
   static void xfwd_tangent(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                            R* p, const R* r, const R* desc, C2<R>* S, const KrylovCtl* ctl,
-                           double* part = nullptr);
+                           double* part = nullptr, int ext = 0);
   // forward: tau_c = f[map c][v] - mean[c] (ncomp components, comp stride V),
   // minus f2[map c][v] - mean2[c] when f2 / mean2 are given
   static void xfwd_field64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
@@ -78,9 +80,18 @@ struct Ops {
   // inverse: out64[c][v] = scale * C2R(S)
   static void xinv_store64(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                            const C2<R>* S, int ncomp, double* out);
-  // C2R -> * l^2(phase) * scale -> R2C for d components (Helmholtz)
-  static void xmid_ell(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
-                       C2<R>* W, const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl);
+  // inverse along x1 of one spectral component into a real field in the
+  // working precision: out[v] = C2R(S)[v] / V
+  static void xinv_storeR(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                          const C2<R>* S, R* out, const KrylovCtl* ctl);
+  // forward along x1 of one real field in the working precision
+  static void xfwd_fieldR(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
+                          const R* f, C2<R>* S, const KrylovCtl* ctl);
+  // y = sum_j D_j^T (l^2(phase) D_j q) in real space (the flux term of the
+  // Helmholtz operator of Algorithm 2 with the rotated-scheme corner
+  // derivative; the identity part is added to the spectrum by helm_contract)
+  static void helm_stencil(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const R* q, R* y,
+                           const uint8_t* phase, const R* ell2_tab, const KrylovCtl* ctl);
 
   // ---------------------------------------------------------- strided passes
   // plain transform along axis (1 = y, 2 = z) of ncomp components
@@ -88,16 +99,17 @@ struct Ops {
                             C2<R>* S, int ncomp, int axis, int sign, const KrylovCtl* ctl);
   // last axis: forward, modified projection (dc_mode 0: stress-mask at xi=0,
   // 1: zero at xi=0), inverse.  In 3D the tiles move by TMA; a CTA whose
-  // tile did not arrive within its wait budget sets *wait_err (if given).
+  // tile did not arrive within wait_s seconds sets *wait_err (if given).
+  // extra_tx > 0 only in tests of that path (bytes no copy delivers).
   static void gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                     C2<R>* S, const float* stress_mask, int dc_mode, const KrylovCtl* ctl,
-                    int* wait_err = nullptr);
-  // last axis inverse with p <- M r + beta p, W_j = k_j p
-  // raw = 1: W_j = k_j r without touching p (operator application only)
+                    int* wait_err = nullptr, double wait_s = 2.0, int extra_tx = 0);
+  // last axis inverse of one component with p <- M r + beta p, W = p
+  // raw = 1: W = r without touching p (operator application only)
   static void helm_expand(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
                           C2<R>* W, C2<R>* p, const C2<R>* r, double ell2_mean, const KrylovCtl* ctl,
                           int raw = 0);
-  // last axis forward; y = p + sum_j conj(k_j) W_j; partial (p, y)
+  // last axis forward of one component; y = p + W; partial (p, y)
   // CTAs of helm_contract (rows of partial sums it writes)
   static int contract_blocks(const Geo& g, const LaunchCfg& lc);
   static void helm_contract(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaStream_t st,
@@ -116,13 +128,17 @@ struct Ops {
                          double* part, const KrylovCtl* ctl);
 
   // ------------------------------------------------------------- local
+  // gtn != 0: a phase follows the GTN law (law 3); it reads the converged
+  // non-local variables abar_n and porosity f_n, writes the new porosity to
+  // f_out (f_n copied elsewhere) and the descriptor in the extended layout
   static void return_map(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const PhaseTable* pt,
                          int J, const uint8_t* phase, const double* eps, const double* epsp_n,
                          const double* ep_n, const double* abar, double* sigma, double* epsp,
                          double* ep, double* D, double* alpha, R* desc, double* part,
-                         const double* stiff = nullptr);
+                         const double* stiff = nullptr, const double* abar_n = nullptr,
+                         const double* f_n = nullptr, double* f_out = nullptr, int gtn = 0);
   static void tangent_apply64(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const R* desc,
-                              const double* p, double* tau);
+                              const double* p, double* tau, int ext = 0);
   // eps += x; partials: max |x| per comp, sum eps per comp
   static void eps_update(const Geo& g, const LaunchCfg& lc, cudaStream_t st, double* eps,
                          const R* x, double* part);
@@ -140,6 +156,13 @@ void k_err_abar(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const double
 // rtol2 = scale and maxit = imax into ctl.
 void k_finalize(cudaStream_t st, const double* part, int nblocks, int nblk_stride, int nslots,
                 int mode, KrylovCtl* ctl, double* out, double scale, int imax = 0, int stall = 0);
+// out[j][v] = rotated-scheme derivative along x_j of the FP64 field a at the
+// voxel corner v + 1/2 (j < d)
+void k_corner_grad64(cudaStream_t st, const Geo& g, const double* a, double* out);
+// forget the cached TMA tensor maps over a device buffer before it is freed
+void tensor_map_evict(const void* base);
+// f[v] = initial porosity f0 of the voxel's phase (GTN, law 3), else 0
+void k_fill_porosity(cudaStream_t st, long long V, const uint8_t* phase, const PhaseTable* pt, double* f);
 // dst[c][v] = src[c][v] + add[c]  (c < nc, FP64)
 void k_copy_add(cudaStream_t st, long long V, int nc, const double* src, double* dst, const double* add_host6);
 

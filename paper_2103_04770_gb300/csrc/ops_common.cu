@@ -2,8 +2,11 @@
 // partial sums (FP64) into Krylov scalars, and the staggered-error sweeps
 // of Algorithm 1 (iii).
 #include "ops.h"
+#include "tma.cuh"
 
 namespace rvk {
+
+void tensor_map_evict(const void* base) { tensor_map_evict_impl(base); }
 
 // One CTA of kFinThreads: slot s is reduced in a fixed order (thread t sums
 // blocks t, t + kFinThreads, ... in eight interleaved accumulators; then a
@@ -137,6 +140,48 @@ k_copy_add_impl(long long V, int nc, const double* __restrict__ src, double* __r
   const long long n = (long long)nc * V;
   for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
     dst[i] = src[i] + add.a[i / V];
+}
+
+// Corner derivatives of the rotated scheme (R5) in real space: out[j][n] is
+// the mean of the forward differences along x_j on the 2^(d-1) cube edges
+// parallel to x_j, at the voxel corner n + 1/2 (periodic).  With N3 = 1 the
+// x3 neighbour is the voxel itself, which gives the 2D stencil.
+__global__ void __launch_bounds__(kThreads)
+k_corner_grad64_impl(Geo g, const double* __restrict__ a, double* __restrict__ out) {
+  const long long V = g.V;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  const double c0 = 1.0 / (4.0 * g.h[0]), c1 = 1.0 / (4.0 * g.h[1]), c2 = g.d == 3 ? 1.0 / (4.0 * g.h[2]) : 0.0;
+  for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
+    const int i = (int)(v % n1);
+    const long long rest = v / n1;
+    const int j = (int)(rest % n2), k = (int)(rest / n2);
+    const int ip = i + 1 == n1 ? 0 : i + 1, jp = j + 1 == n2 ? 0 : j + 1, kp = k + 1 >= n3 ? 0 : k + 1;
+    auto at = [&](int x, int y, int z) { return a[((long long)z * n2 + y) * n1 + x]; };
+    const double q000 = at(i, j, k), q100 = at(ip, j, k), q010 = at(i, jp, k), q110 = at(ip, jp, k);
+    const double q001 = at(i, j, kp), q101 = at(ip, j, kp), q011 = at(i, jp, kp), q111 = at(ip, jp, kp);
+    out[v] = c0 * ((q100 - q000) + (q110 - q010) + (q101 - q001) + (q111 - q011));
+    out[V + v] = c1 * ((q010 - q000) + (q110 - q100) + (q011 - q001) + (q111 - q101));
+    if (g.d == 3) out[2 * V + v] = c2 * ((q001 - q000) + (q101 - q100) + (q011 - q010) + (q111 - q110));
+  }
+}
+
+void k_corner_grad64(cudaStream_t st, const Geo& g, const double* a, double* out) {
+  const long long nb = (g.V + kThreads - 1) / kThreads;
+  k_corner_grad64_impl<<<(int)(nb < 8192 ? nb : 8192), kThreads, 0, st>>>(g, a, out);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_fill_porosity_impl(long long V, const uint8_t* __restrict__ phase, const PhaseTable* __restrict__ pt,
+                     double* __restrict__ f) {
+  for (long long v = blockIdx.x * (long long)kThreads + threadIdx.x; v < V; v += (long long)gridDim.x * kThreads) {
+    const PhaseDev& P = pt->p[phase[v]];
+    f[v] = P.law == 3 ? P.f0 : 0.0;
+  }
+}
+
+void k_fill_porosity(cudaStream_t st, long long V, const uint8_t* phase, const PhaseTable* pt, double* f) {
+  const long long nb = (V + kThreads - 1) / kThreads;
+  k_fill_porosity_impl<<<(int)(nb < 4096 ? nb : 4096), kThreads, 0, st>>>(V, phase, pt, f);
 }
 
 void k_copy_add(cudaStream_t st, long long V, int nc, const double* src, double* dst, const double* add_host6) {

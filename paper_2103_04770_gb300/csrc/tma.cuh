@@ -29,6 +29,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+// Count `bytes` as arrived on the barrier's transaction counter without a
+// copy (used when a CTA gives up on a tile whose expected count exceeds what
+// its copy delivers, so that the phase still completes once the copy lands).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -82,24 +90,51 @@ __device__ __forceinline__ void tma_store_4d_and_wait(const CUtensorMap* map, co
 
 __device__ __forceinline__ void tma_fence_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// time a CTA waits for a tile before it gives up (a TMA tile arrives within
-// microseconds)
-constexpr unsigned long long kWaitNs = 2000000000ULL;
-
 // ------------------------------------------------------------------ host
 // Tiled tensor map over 8-byte elements: dims[0] innermost (contiguous),
 // strides in bytes for dims 1..rank-1.  Maps are cached by their
 // parameters (encoding is a driver call); nullptr when the driver entry
 // point or the encoding is not available.
+using TmapKey = std::tuple<void*, int, unsigned long long, unsigned long long, unsigned long long,
+                           unsigned long long, unsigned long long, unsigned long long, unsigned long long,
+                           unsigned, unsigned, unsigned, unsigned>;
+
+struct TmapCache {
+  std::mutex mu;
+  std::map<TmapKey, CUtensorMap*> maps;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  bool tried = false;
+};
+
+// one cache for the whole library (an inline function's static is unique)
+inline TmapCache& tmap_cache() {
+  static TmapCache c;
+  return c;
+}
+
+// Drop the cached maps over a buffer that is about to be freed (a later
+// allocation at the same address must get maps of its own shapes).
+inline void tensor_map_evict_impl(const void* base) {
+  TmapCache& c = tmap_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  for (auto it = c.maps.begin(); it != c.maps.end();) {
+    if (std::get<0>(it->first) == base) {
+      delete it->second;
+      it = c.maps.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 inline const CUtensorMap* tensor_map_8b(void* base, int rank, const unsigned long long* dims,
                                         const unsigned long long* strides, const unsigned* box) {
-  using Key = std::tuple<void*, int, unsigned long long, unsigned long long, unsigned long long,
-                         unsigned long long, unsigned long long, unsigned long long, unsigned long long,
-                         unsigned, unsigned, unsigned, unsigned>;
-  static std::mutex mu;
-  static std::map<Key, CUtensorMap*> cache;
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  static bool tried = false;
+  using Key = TmapKey;
+  TmapCache& c = tmap_cache();
+  std::mutex& mu = c.mu;
+  std::map<Key, CUtensorMap*>& cache = c.maps;
+  PFN_cuTensorMapEncodeTiled_v12000& encode = c.encode;
+  bool& tried = c.tried;
   unsigned long long d[4] = {1, 1, 1, 1}, s[3] = {0, 0, 0};
   unsigned b[4] = {1, 1, 1, 1};
   for (int i = 0; i < rank; i++) { d[i] = dims[i]; b[i] = box[i]; }

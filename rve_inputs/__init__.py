@@ -311,3 +311,78 @@ def config_adjoint(N=96, n_incr=30, dE=1e-3, precision=0):
     two non-local variables, 30 increments of 1e-3, FP64."""
     return config_spheres_two_var((N, N, N), 0.20, 30, 0, n_incr=n_incr, dE=dE, precision=precision,
                                   name="adjoint_%d" % N)
+
+
+# ------------------------------------------- the paper's parameter studies
+# Section 4.1 (2D examples): matrix E_M = 300 GPa, nu_M = 0.3, sigma_Y = 1 GPa;
+# Lemaitre with eps_C = 0.03, eps_R = 0.2, linear hardening k = 10 GPa, D
+# capped at 0.99; Gurson-Tvergaard-Needleman with q1 = 1.5, q2 = 1, q3 = 2.25,
+# f_C = 0.15, f_F = 0.25, f_N = 0.04, eps_N = 0.3, s_N = 0.1, no initial
+# porosity, the Aravas flow stress with N = 0.1 and f* capped at 0.9 f_V* =
+# 0.6; elastic inclusion E_I = 900 GPa, nu_I = 0.3 occupying 10 % of the cell.
+PAPER2D_LEMAITRE = dict(E=300000.0, nu=0.3, sigma_y=1000.0, H=10000.0, law=1, eps_C=0.03, eps_R=0.2,
+                        D_max=0.99, var=0)
+PAPER2D_GTN = dict(E=300000.0, nu=0.3, sigma_y=1000.0, H=0.0, law=3, eps_C=0.0, eps_R=1.0, D_max=0.0, var=0,
+                   hard=1, N=0.1, q1=1.5, q2=1.0, q3=2.25, f_C=0.15, f_F=0.25, f_N=0.04, eps_N=0.3, s_N=0.1,
+                   f0=0.0, fstar_max=0.6)
+PAPER2D_INCLUSION = dict(E=900000.0, nu=0.3, sigma_y=0.0, H=0.0, law=0, eps_C=0.0, eps_R=1.0, D_max=0.0,
+                         var=-1)
+# Section 4.2 (3D examples): E_M = 70 GPa, nu_M = 0.33, sigma_Y = 200 MPa,
+# Lemaitre as above with k = 10 GPa; GTN with eps_N = 0.1, s_N = 0.05;
+# inclusions E_I = 400 GPa, nu_I = 0.2, 30 spheres at 20 % volume fraction.
+PAPER3D_LEMAITRE = dict(E=70000.0, nu=0.33, sigma_y=200.0, H=10000.0, law=1, eps_C=0.03, eps_R=0.2,
+                        D_max=0.99, var=0)
+PAPER3D_GTN = dict(PAPER2D_GTN, E=70000.0, nu=0.33, sigma_y=200.0, eps_N=0.1, s_N=0.05)
+PAPER3D_INCLUSION = dict(PARTICLE)
+
+
+def config_paper2d(N, model="lemaitre", local=False, ell_M=0.05, ell_I=0.001, n_incr=50, dE=2e-3,
+                   precision=0):
+    """The 2D example of Section 4.1 on N x N: one centred circular
+    inclusion of 10 % area (radius L / sqrt(10 pi)), plane strain, uniaxial
+    E11 under mixed control.  Lengths in units of the cell L: the non-local
+    model takes l_M, l_I (0.05 L and 0.001 L in the paper); the local limit
+    takes l_M = l_I = 1e-4 L (smaller than a voxel).  model: "lemaitre" (one
+    non-local variable) or "gtn" (two: eps_0^p and tr eps^p)."""
+    n = (N, N)
+    ph = disc_phase_map(n, 0.1)
+    ctrl, tgt = uniaxial_path(n_incr, dE)
+    ctrl = plane_strain_mask(ctrl)
+    lM, lI = (1e-4, 1e-4) if local else (ell_M, ell_I)
+    mat = PAPER2D_GTN if model == "gtn" else PAPER2D_LEMAITRE
+    J = 2 if model == "gtn" else 1
+    ell = np.array([[lM * N, lI * N]] * J)
+    name = "paper2d_%s_%s_%d" % (model, "local" if local else "nonlocal", N)
+    return RVEConfig(name, n, (float(N), float(N)), ph, [dict(mat), dict(PAPER2D_INCLUSION)], ell, ctrl, tgt,
+                     precision, dict(area_fraction=0.1, ell_M=lM, ell_I=lI, model=model, sha256=phase_sha256(ph)))
+
+
+def upsample_phase(ph, factor):
+    """Each voxel of a phase map becomes a factor^d block (the same topology
+    on a finer grid, Section 4.2, 'Convergence for a fixed topology')."""
+    out = ph
+    for ax in range(ph.ndim):
+        out = np.repeat(out, factor, axis=ax)
+    return out
+
+
+def config_fixed_topology(factor, base=32, model="lemaitre", seed=0, n_incr=40, dE=2e-3, precision=1):
+    """The 3D RVE of Section 4.2 (30 non-overlapping spheres, 20 % volume
+    fraction, random sequential addition with seed) generated on base^3
+    and resampled to (factor * base)^3 by voxel replication, so the particle
+    arrangement is the same at every resolution.  l_M = 0.05 L, l_I =
+    0.001 L; uniaxial E11 under mixed control."""
+    n0 = (base, base, base)
+    r = sphere_radius_for_count(n0, 30, 0.20)
+    ph0 = voxelize_spheres(n0, rsa_sphere_centres(n0, r, 30, seed), r)
+    ph = upsample_phase(ph0, factor)
+    N = base * factor
+    n = (N, N, N)
+    ctrl, tgt = uniaxial_path(n_incr, dE)
+    mat = PAPER3D_GTN if model == "gtn" else PAPER3D_LEMAITRE
+    J = 2 if model == "gtn" else 1
+    ell = np.array([[0.05 * N, 0.001 * N]] * J)
+    return RVEConfig("topology_%s_%d_from_%d" % (model, N, base), n, tuple(float(x) for x in n), ph,
+                     [dict(mat), dict(PAPER3D_INCLUSION)], ell, ctrl, tgt, precision,
+                     dict(base=base, factor=factor, radius_base=r, seed=seed, vf_voxel=float(ph.mean()),
+                          sha256_base=phase_sha256(ph0), sha256=phase_sha256(ph)))

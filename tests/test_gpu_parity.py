@@ -166,6 +166,46 @@ def test_return_map_and_tangent(n, prec):
         pkg.rve_free(h)
 
 
+@pytest.mark.parametrize("n", [(24, 20), (12, 15, 8)])
+def test_return_map_aravas(n):
+    """Lemaitre return map with the Aravas flow stress (nested Newton on the
+    GPU, bisection in the oracle): stress, plastic strains, damage and the
+    tangent against the oracle."""
+    g = O.Grid(n)
+    d = g.d
+    nc = 6 if d == 3 else 3
+    phase, eps, epsp_n, ep_n, abar = rand_state(g, 2)
+    ep_n = ep_n * 0.1
+    params = [ARAVAS_3D, I.PARTICLE]
+    h = handle(n, phase, 0, params=params)
+    try:
+        rm = O.return_map(O.embed(eps, d), epsp_n, ep_n, abar, phase.ravel().astype(int),
+                          O.phases_from_dicts(params))
+        V = g.V
+        outs = dict(sigma=torch.empty(6, V, device="cuda", dtype=torch.float64),
+                    epsp=torch.empty(6, V, device="cuda", dtype=torch.float64),
+                    ep=torch.empty(V, device="cuda", dtype=torch.float64),
+                    D=torch.empty(V, device="cuda", dtype=torch.float64),
+                    alpha=torch.empty(1, V, device="cuda", dtype=torch.float64))
+        pkg.rve_op_return_map(h, dev(eps.T), dev(epsp_n.T), dev(ep_n), dev(abar), outs["sigma"],
+                              outs["epsp"], outs["ep"], outs["D"], outs["alpha"])
+        s_ref = rm["sigma"].T
+        assert np.abs(host(outs["sigma"]) - s_ref).max() <= 1e-12 * np.abs(s_ref).max()
+        assert np.abs(host(outs["epsp"]) - rm["epsp"].T).max() <= 1e-15
+        assert np.abs(host(outs["ep"]) - rm["ep"]).max() <= 1e-15
+        assert np.abs(host(outs["D"]) - rm["D"]).max() <= 1e-13
+        assert (rm["ep"] > ep_n).sum() > 0.1 * V
+        rng = np.random.default_rng(9)
+        p = rng.standard_normal((V, nc))
+        comps = O.carried(d)
+        tau_ref = np.einsum("vij,vj->vi", rm["C"][:, comps][:, :, comps], p)
+        tau = torch.empty(nc, V, device="cuda", dtype=torch.float64)
+        pkg.rve_op_tangent_apply(h, dev(p.T), tau)
+        assert np.abs(host(tau) - tau_ref.T).max() <= 1e-11 * np.abs(tau_ref).max()
+    finally:
+        pkg.rve_free(h)
+
+
 GAMMA_GRIDS = [(32, 30), (40, 16), (2, 2), (6, 5), (16, 12, 10), (12, 15, 8), (8, 8, 8), (4, 3, 5),
                # several q1 tiles per line and two-stage radix-8 axes
                (96, 20), (128, 64), (80, 12, 10), (64, 64, 16), (64, 24, 64),
@@ -312,14 +352,37 @@ def _sphere2_cfg(N, r, n_incr, dE):
     return cfg
 
 
+# the Aravas flow stress of Section 4.1 (Eq. aravas) on the matrix
+ARAVAS_2D = dict(EARLY_DAMAGE_2D, hard=1, N=0.1)
+ARAVAS_3D = dict(EARLY_DAMAGE_3D, hard=1, N=0.1)
+
+
+def _aravas(cfg, mat):
+    cfg.params = [mat] + cfg.params[1:]
+    return cfg
+
+
 CASES = {
     "2d_disc_16": lambda: _disc_cfg(16, 3.0, 6, 1e-3),
     "3d_sphere_8": lambda: _sphere_cfg(8, 2.6, 5, 1.5e-3),
     "3d_sphere_cracking_8": lambda: _sphere2_cfg(8, 2.6, 5, 1.5e-3),
+    "2d_disc_16_aravas": lambda: _aravas(_disc_cfg(16, 3.0, 6, 1e-3), ARAVAS_2D),
+    "3d_sphere_8_aravas": lambda: _aravas(_sphere_cfg(8, 2.6, 5, 1.5e-3), ARAVAS_3D),
 }
 
 
-def _run_pair(cfg, prec):
+def _fields(h, V, nc, J):
+    """Per-voxel fields of the last converged increment (rve_get_field):
+    strain [nc][V], damage [V], non-local variables [J][V], eps_p [V]."""
+    out = {}
+    for name, which, n in (("eps", 0, nc * V), ("D", 2, V), ("abar", 3, J * V), ("ep", 4, V)):
+        t = torch.empty(n, device="cuda", dtype=torch.float64)
+        pkg.rve_get_field(h, which, t)
+        out[name] = host(t)
+    return out
+
+
+def _run_pair(cfg, prec, fields=False):
     g = O.Grid(cfg.n, cfg.L)
     st = O.make_state(g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
     oopt = O.PARITY_OPTIONS
@@ -327,29 +390,46 @@ def _run_pair(cfg, prec):
     if prec == 0:
         opt.tol_stag, opt.tol_newton, opt.cg_rtol, opt.pcg_rtol = (oopt.tol_stag, oopt.tol_newton,
                                                                    oopt.cg_rtol, oopt.pcg_rtol)
-    recs, infos = [], []
+    recs, infos, fl = [], [], []
     prev = np.zeros(6)
+    nc = 6 if g.d == 3 else 3
+    J = cfg.ell.shape[0]
     with pkg.RVE(cfg, precision=prec, options=opt) as r:
         for i in range(cfg.target.shape[0]):
             infos.append(r.step())
             recs.append(O.step_increment(st, cfg.strain_ctrl, prev, cfg.target[i], oopt))
             prev = cfg.target[i]
-    return recs, infos
+            if fields:
+                gpu = _fields(r.h, g.V, nc, J)
+                ref = dict(eps=st.eps.T.ravel(), D=st.D, abar=st.abar.ravel(), ep=st.ep)
+                fl.append((gpu, ref))
+    return (recs, infos, fl) if fields else (recs, infos)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("case", list(CASES))
 def test_increments_match_oracle(case, prec):
+    """Whole increments against the oracle: homogenised stress and strain,
+    damage maximum, staggered counts (FP64), and per voxel the strain,
+    damage, non-local and equivalent plastic strain fields read back through
+    rve_get_field after every increment."""
     cfg = CASES[case]()
-    recs, infos = _run_pair(cfg, prec)
+    recs, infos, fl = _run_pair(cfg, prec, fields=True)
     smax = max(abs(r["S"][0]) for r in recs)
     tol = 1e-10 if prec == 0 else 1e-4
-    for rec, info in zip(recs, infos):
+    for rec, info, (gpu, ref) in zip(recs, infos, fl):
         assert np.abs(info["sigma"] - rec["S"]).max() <= tol * smax
         assert np.abs(info["eps"] - rec["E"]).max() <= tol * abs(rec["E"][0])
         assert abs(info["D_max"] - rec["D_max"]) <= (1e-9 if prec == 0 else 1e-3)
         if prec == 0:
             assert info["staggered_iters"] == rec["stag"]
+        emax = np.abs(ref["eps"]).max()
+        assert np.abs(gpu["eps"] - ref["eps"]).max() <= (1e-9 if prec == 0 else 1e-3) * emax
+        assert np.abs(gpu["D"] - ref["D"]).max() <= (1e-8 if prec == 0 else 5e-3)
+        amax = max(np.abs(ref["abar"]).max(), 1e-300)
+        assert np.abs(gpu["abar"] - ref["abar"]).max() <= (1e-8 if prec == 0 else 5e-3) * amax
+        pmax = max(np.abs(ref["ep"]).max(), 1e-300)
+        assert np.abs(gpu["ep"] - ref["ep"]).max() <= (1e-8 if prec == 0 else 5e-3) * pmax
     assert recs[-1]["D_max"] > 0.0        # the path reached damage
 
 
