@@ -12,7 +12,9 @@ damage, iteration counts and ERR; the damage and non-local fields at the
 first damaged increment, at the peak and at the last increment.
 
 Test infrastructure: calls only the oracle and the input generators.
-Usage:  python tests/golden/make_curves.py N [l_vox] [fft_threads]
+The file is rewritten after every increment, so a run stopped early keeps
+its curve so far.
+Usage:  python tests/golden/make_curves.py N [l_vox] [fft_threads] [max_increments]
 """
 import dataclasses
 import json
@@ -33,7 +35,7 @@ OPTIONS = dataclasses.replace(O.PARITY_OPTIONS, max_stag=1000)
 DROP = 0.10
 
 
-def run(N, ell_vox, n_incr=50, dE=1e-3, threads=None, log=sys.stderr):
+def run(N, ell_vox, n_incr=50, dE=1e-3, threads=None, log=sys.stderr, max_incr=None):
     cfg = I.config_2d_disc(N, ell_vox=ell_vox, n_incr=n_incr, dE=dE)
     g = O.Grid(cfg.n, cfg.L)
     st = O.make_state(g, cfg.phase, O.phases_from_dicts(cfg.params), cfg.ell)
@@ -45,7 +47,21 @@ def run(N, ell_vox, n_incr=50, dE=1e-3, threads=None, log=sys.stderr):
     prev = np.zeros(6)
     peak, peak_i, first_dmg, stop = -np.inf, -1, None, "end of path"
     t0 = time.time()
-    for i in range(n_incr):
+    path = os.path.join(HERE, "curve_2d_disc_%d.npz" % N)
+
+    def save(stop):
+        out = dict(E=np.array(E), S=np.array(S), **{k: np.array(v) for k, v in rows.items()},
+                   peak_increment=peak_i + 1, phase_sha256=cfg.meta["sha256"],
+                   meta=json.dumps({"grid": [N, N], "ell_vox": ell_vox, "dE": dE, "n_incr": n_incr,
+                                    "options": dataclasses.asdict(OPTIONS), "stop": stop,
+                                    "seconds": round(time.time() - t0, 1)}))
+        for name, (i, D, ab) in fields.items():
+            out["incr_" + name] = i + 1
+            out["D_" + name] = D
+            out["abar_" + name] = ab
+        np.savez_compressed(path, **out)
+
+    for i in range(n_incr if max_incr is None else min(n_incr, max_incr)):
         try:
             rec = O.step_increment(st, cfg.strain_ctrl, prev, cfg.target[i], OPTIONS)
         except RuntimeError as e:
@@ -69,17 +85,12 @@ def run(N, ell_vox, n_incr=50, dE=1e-3, threads=None, log=sys.stderr):
         if s11 <= (1.0 - DROP) * peak:
             stop = "stress dropped %.0f %% below the peak at increment %d" % (100 * DROP, i + 1)
             break
-    out = dict(E=np.array(E), S=np.array(S), **{k: np.array(v) for k, v in rows.items()},
-               peak_increment=peak_i + 1, phase_sha256=cfg.meta["sha256"],
-               meta=json.dumps({"grid": [N, N], "ell_vox": ell_vox, "dE": dE, "n_incr": n_incr,
-                                "options": dataclasses.asdict(OPTIONS), "stop": stop,
-                                "seconds": round(time.time() - t0, 1)}))
-    for name, (i, D, ab) in fields.items():
-        out["incr_" + name] = i + 1
-        out["D_" + name] = D
-        out["abar_" + name] = ab
-    path = os.path.join(HERE, "curve_2d_disc_%d.npz" % N)
-    np.savez_compressed(path, **out)
+        # the curve so far is kept after every increment
+        save("running: %d increments done" % (i + 1))
+    else:
+        if max_incr is not None and max_incr < n_incr:
+            stop = "increment cap %d reached" % max_incr
+    save(stop)
     return path, stop
 
 
@@ -87,4 +98,5 @@ if __name__ == "__main__":
     N = int(sys.argv[1])
     ell = float(sys.argv[2]) if len(sys.argv) > 2 else (4.0 if N == 64 else N / 16.0)
     th = int(sys.argv[3]) if len(sys.argv) > 3 else None
-    print(run(N, ell, threads=th))
+    mx = int(sys.argv[4]) if len(sys.argv) > 4 else None
+    print(run(N, ell, threads=th, max_incr=mx))
