@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default schedule instead of rve_autotune before the first increment")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="increments of the instrumented replay that gives the per-class times (0: all)")
     ap.add_argument("--curve", action="store_true",
@@ -56,6 +58,9 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--obj-grids", type=lambda v: [int(x) for x in v.split(",")], default=[128, 256, 512])
     ap.add_argument("--obj-incr", type=int, default=50)
+    ap.add_argument("--obj-max-cg", type=int, default=20000,
+                    help="CG budget per Newton step of the objectivity runs (the count grows with the grid "
+                         "in the plastic range)")
     ap.add_argument("--study-models", type=lambda v: v.split(","), default=["lemaitre", "gtn"])
     ap.add_argument("--study-emax", type=float, default=0.1)
     ap.add_argument("--study-de", type=float, default=2e-3)
@@ -63,9 +68,12 @@ def parse():
     ap.add_argument("--study-profile-e", type=float, default=0.05)
     ap.add_argument("--topology-model", default="lemaitre", choices=["lemaitre", "gtn"])
     ap.add_argument("--workload", default="spheres256",
-                    choices=["spheres256", "batch", "adjoint", "objectivity", "studies2d", "topology3d"],
+                    choices=["spheres256", "batch", "adjoint", "objectivity", "studies2d", "topology3d",
+                             "formcurve"],
                     help="batch: the 32-RVE {64,96,128}^3 two-variable workload; adjoint: gradients of "
-                         "the final stress of the 96^3 two-variable RVE (each its own JSON line)")
+                         "the final stress of the 96^3 two-variable RVE; formcurve: the sphere RVE's load "
+                         "path (--n, --curve-incr) in the mixed and the FP64 form, compared increment by "
+                         "increment (each its own JSON line)")
     ap.add_argument("--adj-incr", type=int, default=30)
     ap.add_argument("--adj-every", type=int, default=5)
     ap.add_argument("--adj-fd", default="0:sigma_y,ell0",
@@ -293,6 +301,16 @@ def cg_iteration_ms(pkg, h, V, nc, iters=24):
     return ms / max(it, 1), it
 
 
+def tune_schedule(pkg, h, args):
+    """rve_autotune on a fresh handle (before its first increment): the FFT
+    schedule and the projection pass's tile width, timed on the matvec."""
+    if args.no_autotune:
+        return {"autotuned": False, "gamma_narrow": pkg.rve_get_gamma_tile(h)}
+    ms, tx, _ = pkg.rve_autotune(h, 3)
+    return {"autotuned": True, "matvec_ms": round(ms, 4), "strided_tile": tx,
+            "gamma_narrow": pkg.rve_get_gamma_tile(h)}
+
+
 def run_ours(args, rank, ws, dist):
     import torch
     import paper_2103_04770_gb300 as pkg
@@ -309,6 +327,7 @@ def run_ours(args, rank, ws, dist):
     # -------- device-resident timing: graph replay of the Krylov chunks on,
     # no per-launch events in the timed region
     r = pkg.RVE(cfg, precision=prec, stream=stream)
+    schedule = tune_schedule(pkg, r.h, args)
     pkg.rve_set_graphs(r.h, True)
     for _ in range(args.warmup):
         r.step()
@@ -398,7 +417,7 @@ def run_ours(args, rank, ws, dist):
            "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if prec == pkg.RVE_MIXED else "f64", "data": "synthetic",
-           "config": workload_config(cfg, args.precision), "roofline": roofline,
+           "config": workload_config(cfg, args.precision), "schedule": schedule, "roofline": roofline,
            "gpu_launches": gpu_launches, "clocks": ck,
            "timed_region": "increments %d..%d, graph replay of the Krylov chunks, no per-launch events"
                            % (args.warmup + 1, args.warmup + K),
@@ -423,6 +442,7 @@ def run_ours(args, rank, ws, dist):
     # run's converged state before it
     if samples:
         r3 = pkg.RVE(cfg, precision=pkg.RVE_FP64, stream=stream)
+        schedule64 = tune_schedule(pkg, r3.h, args)
         pkg.rve_set_graphs(r3.h, True)
         r3.step()                                                     # kernels loaded, graphs captured
         t64, vi64, tm, vim, errs, rows = 0.0, 0.0, 0.0, 0.0, [], []
@@ -449,7 +469,7 @@ def run_ours(args, rank, ws, dist):
             del s
         v64 = vi64 / (t64 * 1e-3)
         vmix = vim / (tm * 1e-3)
-        out["fp64_form"] = {"value": v64, "unit": UNIT, "increments": rows,
+        out["fp64_form"] = {"value": v64, "unit": UNIT, "schedule": schedule64, "increments": rows,
                             "mixed_same_increments": vmix, "mixed_over_fp64": vmix / v64,
                             "time_ratio_fp64_over_mixed": t64 / tm,
                             "sigma11_rel_err_mixed_vs_fp64": max(errs),
@@ -461,6 +481,7 @@ def run_ours(args, rank, ws, dist):
     # the timed increments go host -> device inside the timed region
     if not args.no_e2e:
         r2 = pkg.RVE(cfg, precision=prec, stream=stream)
+        pkg.rve_set_gamma_tile(r2.h, schedule["gamma_narrow"])                # the timed handle's schedule
         pkg.rve_set_graphs(r2.h, True)
         r2.step()                                                     # kernels loaded
         phase_host = np.ascontiguousarray(cfg.phase)
@@ -788,6 +809,59 @@ def run_curve(args):
             "curve_columns": ["E11", "S11", "D_max", "substeps", "cg", "pcg"], "curve": curve}
 
 
+def run_formcurve(args):
+    """The sphere RVE's load path (radius 10 voxels, 25 % spheres, l = 4
+    voxels, uniaxial E11 in steps of 1e-3) run twice, independently, through
+    the cut-back step: once in the mixed form, once in the FP64 form.  At every
+    increment the mixed form's Sigma11 is compared with the FP64 form's,
+    relative to the FP64 curve's max |Sigma11|; both forms' device times are
+    reported (time to curve of each)."""
+    import torch
+    import paper_2103_04770_gb300 as pkg
+
+    torch.cuda.init()
+    stream = torch.cuda.current_stream()
+    cfg = workload(args.n, args.grid)
+    n_incr = cfg.target.shape[0] if args.curve_incr <= 0 else min(args.curve_incr, cfg.target.shape[0])
+    runs = {}
+    for name, prec in (("mixed", pkg.RVE_MIXED), ("fp64", pkg.RVE_FP64)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        curve, status = [], "ok"
+        with pkg.RVE(cfg, precision=prec, stream=stream) as r:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(n_incr):
+                info = r.step_adaptive(max_cuts=7, raise_on_error=False)
+                if info["status"] != pkg.RVE_OK:
+                    status = "increment %d: %s (%s budget)" % (
+                        i + 1, pkg.rve_status_string(info["status"]), FAIL_STAGES.get(info["fail_stage"], "?"))
+                    break
+                curve.append([round(info["eps"][0], 6), float(info["sigma"][0]), float(info["D_max"]),
+                              info["substeps"], int(info["cg_iters"]), int(info["pcg_iters"])])
+                print(json.dumps({"form": name, "increment": i + 1, "point": curve[-1]}), file=sys.stderr,
+                      flush=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        runs[name] = {"curve": curve, "status": status, "device_s": e0.elapsed_time(e1) * 1e-3}
+    m, f = runs["mixed"]["curve"], runs["fp64"]["curve"]
+    k = min(len(m), len(f))
+    smax = max((abs(p[1]) for p in f), default=0.0)
+    errs = [abs(m[i][1] - f[i][1]) / smax for i in range(k)] if smax > 0 else []
+    return {"metric": "max |Sigma11_mixed - Sigma11_fp64| / max |Sigma11_fp64| over the load path",
+            "value": max(errs) if errs else None, "unit": "relative", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f32+f64 vs f64", "data": "synthetic",
+            "config": workload_config(cfg, "mixed vs fp64"), "increments_compared": k,
+            "within_1e-4": bool(errs) and max(errs) <= 1e-4, "per_increment_rel_err": errs,
+            "time_to_curve_s": {n: runs[n]["device_s"] for n in runs},
+            "status": {n: runs[n]["status"] for n in runs},
+            "curve_columns": ["E11", "S11", "D_max", "substeps", "cg", "pcg"],
+            "curves": {n: runs[n]["curve"] for n in runs}}
+
+
+FAIL_STAGES = {0: "none", 1: "Newton", 2: "CG", 3: "PCG", 4: "staggered", 5: "numeric"}
+
+
 def run_objectivity(args):
     """Mesh objectivity of the 2D single-particle cell: the FP64 GPU form
     runs the load path (uniaxial E11 in steps of 1e-3) at 128^2, 256^2 and
@@ -806,17 +880,20 @@ def run_objectivity(args):
         cfg = I.config_mesh_objectivity(N, n_incr=args.obj_incr)
         opt = pkg.rve_default_options(0)
         opt.max_stag = 1000
+        opt.max_cg = args.obj_max_cg
         t0 = time.perf_counter()
         pts, status = [], "end of path"
         with pkg.RVE(cfg, precision=0, options=opt) as r:
             for i in range(cfg.target.shape[0]):
                 info = r.step(raise_on_error=False)
                 if info["status"] != pkg.RVE_OK:
-                    status = "increment %d: %s" % (i + 1, pkg.rve_status_string(info["status"]))
+                    status = "increment %d: %s (%s budget)" % (
+                        i + 1, pkg.rve_status_string(info["status"]), FAIL_STAGES.get(info["fail_stage"], "?"))
                     break
                 pts.append([round(info["eps"][0], 6), info["sigma"][0], info["D_max"], info["staggered_iters"]])
                 print(json.dumps({"N": N, "increment": i + 1, "S11": info["sigma"][0], "D_max": info["D_max"],
-                                  "stag": info["staggered_iters"]}), file=sys.stderr, flush=True)
+                                  "stag": info["staggered_iters"], "newton": info["newton_iters"],
+                                  "cg": info["cg_iters"], "pcg": info["pcg_iters"]}), file=sys.stderr, flush=True)
         curves[N] = {"curve": pts, "status": status, "seconds": round(time.perf_counter() - t0, 1)}
     ref_N = max(curves)
     ref = np.array([p[1] for p in curves[ref_N]["curve"]])
@@ -839,7 +916,8 @@ def run_objectivity(args):
             "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "2d_disc_objectivity", "grids": list(curves), "ell": "L/16",
                        "load": "uniaxial E11 steps of 1e-3, Sigma22 = Sigma12 = 0, plane strain",
-                       "options": "production FP64 (tol 1e-6), staggered budget 1000"},
+                       "options": "production FP64 (tol 1e-6), staggered budget 1000, CG budget %d per Newton step"
+                                  % args.obj_max_cg},
             "peak_increment_%d" % ref_N: ipk + 1, "comparison": out,
             "curves": {str(N): c for N, c in curves.items()}}
 
@@ -856,7 +934,8 @@ def _run_curve_cfg(pkg, cfg, precision, budget_s, max_cuts=6, tag=None):
         for i in range(cfg.target.shape[0]):
             info = r.step_adaptive(max_cuts=max_cuts, raise_on_error=False)
             if info["status"] != pkg.RVE_OK:
-                status = "increment %d: %s" % (i + 1, pkg.rve_status_string(info["status"]))
+                status = "increment %d: %s (%s budget)" % (
+                    i + 1, pkg.rve_status_string(info["status"]), FAIL_STAGES.get(info["fail_stage"], "?"))
                 break
             pts.append([round(info["eps"][0], 6), round(info["sigma"][0], 5), round(info["D_max"], 5),
                         info["substeps"]])
@@ -1008,6 +1087,10 @@ def main():
     if args.workload == "objectivity" and args.impl == "ours":
         if rank == 0:
             print(json.dumps(run_objectivity(args)))
+        return
+    if args.workload == "formcurve" and args.impl == "ours":
+        if rank == 0:
+            print(json.dumps(run_formcurve(args)))
         return
     if args.curve and args.impl == "ours":
         if rank == 0:

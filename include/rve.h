@@ -343,10 +343,22 @@ int rve_load_state(rve_t* h, const void* buf, long long bytes);
  * Errors: RVE_ERR_ARG, RVE_ERR_CUDA. */
 int rve_set_graphs(rve_t* h, int enable);
 
+/* Width of the tile of the 3D projection pass (G* of Eq. eqdiscrete2 with the
+ * last-axis transform, six-component handles whose last axis has 64, 128
+ * or 256 points): narrow = 0 (default) moves 8 columns (FP32; 4 in FP64)
+ * per CTA of 256 threads, narrow = 1 half as many per CTA of 128 threads,
+ * so that twice as many CTAs share an SM.  Results are identical; only the
+ * time differs (rve_autotune picks it).  Drops captured Krylov chunks.
+ * Errors: RVE_ERR_ARG (h null, narrow not 0 or 1), RVE_ERR_CUDA. */
+int rve_set_gamma_tile(rve_t* h, int narrow);
+/* The current choice of rve_set_gamma_tile.  Errors: RVE_ERR_ARG. */
+int rve_get_gamma_tile(const rve_t* h, int* narrow);
+
 /* Pick the FFT schedule of the handle's mechanical matvec by timing:
  * for every axis transformed by the runtime mixed-radix code, each radix
  * order with the fewest stages; then the column-tile width of the strided
- * passes.  Each candidate is timed over `reps` matvecs G*(C_T : p) that
+ * passes; then the width of the 3D projection pass's tile
+ * (rve_set_gamma_tile).  Each candidate is timed over `reps` matvecs G*(C_T : p) that
  * overwrite only the Krylov scratch vectors (CUDA events on the handle's
  * stream); a candidate replaces
  * the current choice when it is at least 2 % faster.  Axes with compile-time

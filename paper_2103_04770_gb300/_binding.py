@@ -120,6 +120,8 @@ _SIGNATURES = {
     "rve_adjoint_forward": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "rve_adjoint_backward": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(AdjointInfo)]),
     "rve_set_graphs": (_I, [_P, _I]),
+    "rve_set_gamma_tile": (_I, [_P, _I]),
+    "rve_get_gamma_tile": (_I, [_P, ctypes.POINTER(_I)]),
     "rve_autotune": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rve_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _I]),
     "rve_batch_step": (_I, [_P, ctypes.POINTER(StepInfo)]),
@@ -433,6 +435,16 @@ def rve_adjoint_backward(h, dJ, n_phases, n_vars, n_voxels):
 # ------------------------------------------- graphs, autotuning, batches
 def rve_set_graphs(h, enable=True):
     _check(lib().rve_set_graphs(h, 1 if enable else 0), "rve_set_graphs")
+
+
+def rve_set_gamma_tile(h, narrow):
+    _check(lib().rve_set_gamma_tile(h, int(narrow)), "rve_set_gamma_tile")
+
+
+def rve_get_gamma_tile(h):
+    v = ctypes.c_int()
+    _check(lib().rve_get_gamma_tile(h, ctypes.byref(v)), "rve_get_gamma_tile")
+    return v.value
 
 
 def rve_autotune(h, reps=3):

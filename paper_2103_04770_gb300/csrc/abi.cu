@@ -128,6 +128,7 @@ struct rve {
   // reductions and control
   double* part = nullptr;
   KrylovCtl* ctl = nullptr;
+  FinScratch* fin = nullptr;     // two-level reduction scratch of k_finalize
   double* dscal = nullptr;
   KrylovCtl* hctl = nullptr;     // pinned
   double* hscal = nullptr;       // pinned
@@ -419,9 +420,9 @@ struct Alg {
             Op::return_map(h->g, h->lc, h->st, h->pt_dev, h->J, h->phase, h->eps, h->epsp_n, h->ep_n, abar_use,
                            h->sigma, h->epsp, h->ep, h->D, h->alpha, (R*)h->desc, h->part, h->stiff, h->abar_n,
                            h->f_n, h->f, h->gtn));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 7, FIN_SUMS, nullptr,
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 7, FIN_SUMS, nullptr,
                h->dscal + OFF_SIGMEAN, 1.0 / (double)h->g.V));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 7 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part + 7 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
                FIN_MAXS, nullptr, h->dscal + OFF_DMAX, 1.0));
   }
 
@@ -447,7 +448,7 @@ struct Alg {
     LAUNCHB(h, KC_X_INV_RESIDUAL, nc * (VS(h) * cs64 + VV(h) * RS),
             Ops<double>::template xinv_residual<R>(g, t64, h->lc64, h->st, S64, (R*)h->r,
                                                    h->dscal + OFF_SIGMEAN, h->smask_d, sbar_c, h->part));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
                                             h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
   }
 
@@ -464,7 +465,7 @@ struct Alg {
     LAUNCHB(h, KC_X_INV_RESIDUAL, nc * (VS(h) * CS + VV(h) * RS),
             Op::template xinv_residual<R>(g, t, h->lc, h->st, S, (R*)h->r, h->dscal + OFF_SIGMEAN, h->smask_d,
                                           sbar_c, h->part));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
                                             h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
   }
 
@@ -496,7 +497,7 @@ struct Alg {
     LAUNCHB(h, KC_X_INV_RESIDUAL, nc * (VS(h) * CS + 2.0 * VV(h) * RS),
             Op::template xinv_residual<R>(g, t, h->lc, h->st, S, (R*)h->r, h->dscal + OFF_SIGMEAN, h->smask_d,
                                           zero, h->part, (const R*)h->r_ref, h->dscal + OFF_SIGREF));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, xblocks(h, g.nc), h->lc.max_blocks, 1, FIN_CG_INIT,
                                             h->ctl, nullptr, rtol * rtol, maxit, stall_window()));
   }
 
@@ -520,21 +521,21 @@ struct Alg {
           LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS,
                   Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc,
                                    (C2<R>*)h->S, h->ctl, h->part, h->gtn));
-          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
           gamma_sweep(h, t, 0, h->ctl);
           LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 5.0 * VV(h) * RS),
                   Op::xinv_cg(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->x, (R*)h->r, (const R*)h->p,
                               h->part, h->ctl));
-          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, nbx, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
         }
         for (int i = 0; i < chunk && !h->cg_fused; i++) {
           LAUNCHB(h, KC_X_FWD_TANGENT, VV(h) * RS * (4.0 * h->g.nc + 2.0) + h->g.nc * VS(h) * CS, Op::xfwd_tangent(g, t, h->lc, h->st, (R*)h->p, (const R*)h->r, (const R*)h->desc, (C2<R>*)h->S,
                            h->ctl, nullptr, h->gtn));
           gamma_sweep(h, t, 0, h->ctl);
           LAUNCHB(h, KC_X_INV_MATVEC, (double)h->g.nc * (VS(h) * CS + 2.0 * VV(h) * RS), Op::xinv_matvec(g, t, h->lc, h->st, (const C2<R>*)h->S, (R*)h->Ap, (const R*)h->p, h->part, h->ctl));
-          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, nbx, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
           LAUNCHB(h, KC_CG_UPDATE, 6.0 * g.nc * VV(h) * RS, Op::cg_update(g, h->lc, h->st, (R*)h->x, (R*)h->r, (const R*)h->p, (const R*)h->Ap, h->part, h->ctl));
-          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_BETA, h->ctl, nullptr, 1.0));
         }
       });
       if (s) return s;
@@ -614,9 +615,9 @@ struct Alg {
                      h->hctl->status, h->hctl->pAp, h->hctl->rnorm2, h->hctl->b2, s);
       if (s) return s;
       LAUNCHB(h, KC_MISC, g.nc * VV(h) * (16.0 + RS), Op::eps_update(g, h->lc, h->st, h->eps, (const R*)h->x, h->part));
-      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 6, FIN_SUMS, nullptr,
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 6, FIN_SUMS, nullptr,
                  h->dscal + OFF_EPSMEAN, 1.0 / (double)g.V));
-      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 6 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part + 6 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
                  FIN_MAXS, nullptr, h->dscal + OFF_MAXDX, 1.0));
       s = sync_read(h);
       if (s) return s;
@@ -674,7 +675,7 @@ struct Alg {
     C2<R>* hy = (C2<R>*)h->hy;
     forward1(h, t, alpha_j, hr);
     LAUNCHB(h, KC_PCG_UPDATE, 2.0 * VS(h) * CS, Op::pcg_init(g, t, h->lc, h->st, hx, hr, h->ell2_mean[j], h->part));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_INIT, h->ctl, nullptr,
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_INIT, h->ctl, nullptr,
                rtol * rtol, maxit, stall_window()));
     const int chunk = std::max(1, h->opt.check_every);
     const int nbl = Op::contract_blocks(g, h->lc);
@@ -682,9 +683,9 @@ struct Alg {
       int s = run_chunk(h, &h->g_pcg[j], h->g_pcg_n[j], h->g_pcg_b[j], [&]() {
         for (int i = 0; i < chunk; i++) {
           helm_matvec(h, t, j, hp, hr, hy, h->ctl, 0);
-          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, nbl, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, nbl, h->lc.max_blocks, 1, FIN_ALPHA, h->ctl, nullptr, 1.0));
           LAUNCHB(h, KC_PCG_UPDATE, 6.0 * VS(h) * CS, Op::pcg_update(g, t, h->lc, h->st, hx, hr, hp, hy, h->ell2_mean[j], h->part, h->ctl));
-          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_BETA, h->ctl, nullptr, 1.0));
+          LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_PCG_BETA, h->ctl, nullptr, 1.0));
         }
       });
       if (s) return s;
@@ -739,13 +740,13 @@ struct Alg {
       }
       if (status) break;
       LAUNCHB(h, KC_MISC, 16.0 * g.nc * VV(h), k_err_eps(g, h->lc, h->st, h->eps, h->eps_prev, h->part));
-      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 6, FIN_SUMS, nullptr,
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 6, FIN_SUMS, nullptr,
                  h->dscal + OFF_ERRMEAN, 1.0 / (double)g.V));
-      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part + 6 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part + 6 * (size_t)h->lc.max_blocks, h->lc.n_ew_blocks, h->lc.max_blocks, 1,
                  FIN_MAXS, nullptr, h->dscal + OFF_ERRMAX, 1.0));
       for (int j = 0; j < h->J; j++) {
         LAUNCHB(h, KC_MISC, 16.0 * VV(h), k_err_abar(g, h->lc, h->st, h->abar_new + (size_t)j * g.V, h->abar_k + (size_t)j * g.V, h->part));
-        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_SUMS, nullptr,
+        LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 2, FIN_SUMS, nullptr,
                    h->dscal + OFF_ABAR + 2 * j, 1.0));
       }
       status = sync_read(h);
@@ -845,7 +846,7 @@ struct Alg {
     const long long n = (long long)h->g.nc * h->g.V;
     LAUNCHB(h, KC_MISC, (double)n * (8.0 + RS), Op::to_r(h->st, n, b, (R*)h->r));
     LAUNCHB(h, KC_CG_UPDATE, 2.0 * h->g.nc * VV(h) * RS, Op::cg_init(h->g, h->lc, h->st, (R*)h->x, (const R*)h->r, h->part));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_INIT, h->ctl, nullptr,
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, h->part, h->lc.n_ew_blocks, h->lc.max_blocks, 1, FIN_CG_INIT, h->ctl, nullptr,
                rtol * rtol, maxit));
     int it = 0;
     int s = cg_loop(h, t, &it);
@@ -1033,6 +1034,7 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   const int tx64 = tx_for(ET64);
   mb = std::max<long long>(mb, (long long)((g.P1 + tx64 - 1) / tx64) * std::max(nn[1], 1));
   lc.max_blocks = (int)mb;
+  lc.gamma_narrow = 0;
   h->lc64 = lc;
   h->lc64.tx = tx64;
   {
@@ -1088,7 +1090,9 @@ int create_impl(rve** out, int dim, const int n[3], const double L[3], int preci
   AL(dalloc_t(h, &h->pt_dev, 1));
   AL(dalloc_t(h, &h->part, (size_t)kSlots * lc.max_blocks));
   AL(dalloc_t(h, &h->ctl, 1));
-  if (cudaMemset(h->ctl, 0, sizeof(KrylovCtl)) != cudaSuccess) {
+  AL(dalloc_t(h, &h->fin, 1));
+  if (cudaMemset(h->ctl, 0, sizeof(KrylovCtl)) != cudaSuccess ||
+      cudaMemset(h->fin, 0, sizeof(FinScratch)) != cudaSuccess) {
     cudaGetLastError();
     free_all(h);
     delete h;
@@ -1577,6 +1581,20 @@ int rve_op_helmholtz_solve(rve_t* h, int j, const double* alpha, double* abar, d
 }  // extern "C"
 
 // ============================================================ graphs, autotuning, batches
+int rve_set_gamma_tile(rve_t* h, int narrow) {
+  if (!h || narrow < 0 || narrow > 1) return RVE_ERR_ARG;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return RVE_ERR_CUDA;
+  graphs_reset(h);
+  h->lc.gamma_narrow = narrow;
+  return RVE_OK;
+}
+
+int rve_get_gamma_tile(const rve_t* h, int* narrow) {
+  if (!h || !narrow) return RVE_ERR_ARG;
+  *narrow = h->lc.gamma_narrow;
+  return RVE_OK;
+}
+
 int rve_set_graphs(rve_t* h, int enable) {
   if (!h) return RVE_ERR_ARG;
   if (cudaStreamSynchronize(h->st) != cudaSuccess) return RVE_ERR_CUDA;
@@ -1692,6 +1710,14 @@ int autotune_impl(rve* h, int reps, double* best_ms) {
       if (ms < best * 0.98) { best = ms; keep = tx; }
     }
     h->lc.tx = keep;
+  }
+  // width of the 3D six-component last-axis TMA tile
+  if (!s && g.d == 3 && g.nc == 6 && reg_axis(g.n3)) {
+    const int keep0 = h->lc.gamma_narrow;
+    h->lc.gamma_narrow = 1 - keep0;
+    const double ms = time_matvec<R>(h, reps);
+    if (ms < best * 0.98) best = ms;
+    else h->lc.gamma_narrow = keep0;
   }
   std::memcpy(h->launches, n0, sizeof(n0));
   std::memcpy(h->prof_bytes, b0, sizeof(b0));
@@ -2006,10 +2032,10 @@ int adj_increment(rve* h, int k, double seed, AdjSums& acc) {
     // change of both adjoints since the last sweep
     double r[4] = {0, 0, 0, 0};
     LAUNCHB(h, KC_MISC, 0.0, adj_absmax2((long long)nc * V, a->lam2, a->lam, part, ps, nb, h->st));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part, nb, ps, 2, FIN_MAXS, nullptr, a->red, 1.0));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, part, nb, ps, 2, FIN_MAXS, nullptr, a->red, 1.0));
     if (J > 0) {
       LAUNCHB(h, KC_MISC, 0.0, adj_absmax2((long long)J * V, a->mu2, a->mu, part, ps, nb, h->st));
-      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part, nb, ps, 2, FIN_MAXS, nullptr, a->red + 2, 1.0));
+      LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, part, nb, ps, 2, FIN_MAXS, nullptr, a->red + 2, 1.0));
     }
     if ((s = red_read(h, r, 4))) return s;
     std::swap(a->lam, a->lam2);
@@ -2032,7 +2058,7 @@ int adj_increment(rve* h, int k, double seed, AdjSums& acc) {
   LAUNCHB(h, KC_MISC, 0.0, adj_phase_sums(V, h->phase, a->v_theta, part, ps, nb, h->st));
   // the finaliser reduces at most 16 slots per call
   for (int half = 0; half < 4 * kMaxPhases; half += 16)
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part + (size_t)half * ps, nb, ps, 16, FIN_SUMS, nullptr, a->red + half, 1.0));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, part + (size_t)half * ps, nb, ps, 16, FIN_SUMS, nullptr, a->red + half, 1.0));
   double th[4 * kMaxPhases];
   int s = red_read(h, th, 4 * kMaxPhases);
   if (s) return s;
@@ -2048,7 +2074,7 @@ int adj_increment(rve* h, int k, double seed, AdjSums& acc) {
     grad_field(h, t, a->mu + (size_t)j * V, a->G1);
     grad_field(h, t, a->seg_abar[k] + (size_t)j * V, a->G2);
     LAUNCHB(h, KC_MISC, 0.0, adj_weighted_dot(V, g.d, h->phase, w, a->G1, a->G2, part, ps, nb, h->st));
-    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, part, nb, ps, 1, FIN_SUMS, nullptr, a->red, 1.0));
+    LAUNCHB(h, KC_FINALIZE, 0.0, k_finalize(h->st, h->fin, part, nb, ps, 1, FIN_SUMS, nullptr, a->red, 1.0));
     double dv = 0.0;
     if ((s = red_read(h, &dv, 1))) return s;
     acc.ell[j] -= dv;

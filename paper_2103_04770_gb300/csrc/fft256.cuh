@@ -178,18 +178,18 @@ __device__ __forceinline__ void dft_reg(C2<R> (&v)[RAD]) {
 }
 
 // One pass over NL lines of N = R1 R2 points (element n of line l at
-// buf[n ES + l]): STRIDED takes, for task (l, a), a < R1, the R2 entries
+// buf[n ES + l]), spread over the CTA's NTH threads: STRIDED takes, for task (l, a), a < R1, the R2 entries
 // a + R1 i; otherwise, for task (l, r), r < R2, the R1 entries i + R1 r.
 // TWID multiplies output i by tw[q i] (conjugated for SIGN > 0), q the
 // task's a or r; tw[m] = exp(-2 pi i m / N).
-template <typename R, int N, int NL, int ES, int SIGN, bool STRIDED, bool TWID>
+template <typename R, int N, int NL, int ES, int SIGN, bool STRIDED, bool TWID, int NTH = kThreads>
 __device__ __forceinline__ void fftreg_pass(C2<R>* buf, const C2<R>* tw) {
   constexpr int R1 = RegSplit<N>::r1, R2 = RegSplit<N>::r2;
   constexpr int L = STRIDED ? R2 : R1;          // DFT length
   constexpr int Q = STRIDED ? R1 : R2;          // tasks per line
   constexpr int NT = NL * Q;
 #pragma unroll 1
-  for (int t = threadIdx.x; t < NT; t += kThreads) {
+  for (int t = threadIdx.x; t < NT; t += NTH) {
     const int l = t % NL, q = t / NL;
     C2<R>* p = buf + l + (STRIDED ? q : R1 * q) * ES;
     constexpr int step = (STRIDED ? R1 : 1) * ES;
@@ -212,20 +212,20 @@ __device__ __forceinline__ void fftreg_pass(C2<R>* buf, const C2<R>* tw) {
 
 // Forward transform of NL lines, natural order in, reg_pos order out.  The
 // caller synchronises before the call; the call ends with a barrier.
-template <typename R, int N, int NL, int ES = NL>
+template <typename R, int N, int NL, int ES = NL, int NTH = kThreads>
 __device__ __forceinline__ void fftreg_forward(C2<R>* buf, const C2<R>* tw) {
-  fftreg_pass<R, N, NL, ES, -1, true, true>(buf, tw);
+  fftreg_pass<R, N, NL, ES, -1, true, true, NTH>(buf, tw);
   __syncthreads();
-  fftreg_pass<R, N, NL, ES, -1, false, false>(buf, tw);
+  fftreg_pass<R, N, NL, ES, -1, false, false, NTH>(buf, tw);
   __syncthreads();
 }
 
 // Inverse transform of NL lines, reg_pos order in, natural order out.
-template <typename R, int N, int NL, int ES = NL>
+template <typename R, int N, int NL, int ES = NL, int NTH = kThreads>
 __device__ __forceinline__ void fftreg_inverse(C2<R>* buf, const C2<R>* tw) {
-  fftreg_pass<R, N, NL, ES, 1, false, true>(buf, tw);
+  fftreg_pass<R, N, NL, ES, 1, false, true, NTH>(buf, tw);
   __syncthreads();
-  fftreg_pass<R, N, NL, ES, 1, true, false>(buf, tw);
+  fftreg_pass<R, N, NL, ES, 1, true, false, NTH>(buf, tw);
   __syncthreads();
 }
 

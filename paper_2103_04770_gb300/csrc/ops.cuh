@@ -312,93 +312,138 @@ k_xinv(Geo g, FftPlan pl, const C2<R>* __restrict__ tw1, const C2<R>* __restrict
 //     y = sum_j D_j^T (l^2 * D_j q),
 // D_j the derivative along x_j at the voxel corner n + 1/2 (mean of the
 // forward differences on the 2^(d-1) cube edges parallel to x_j, stored at
-// index n) and l^2 taken at that index).  One CTA covers SX x SY voxels of
-// the (x1, x2) plane and marches along x3 over zc planes, keeping three
-// planes of q (with a one-voxel periodic halo) and two planes of the corner
-// fluxes l^2 D_j q in shared memory.  With N3 = 1 the x3 neighbours are the
-// plane itself, the x3 flux vanishes and the kernel is the 2D stencil.
-constexpr int kStencilX = 32, kStencilY = kThreads / kStencilX;
+// index n) and l^2 taken at that index).
+//
+// Each warp owns a strip: 32 consecutive x1 columns (the first and last lane
+// are halo: 30 outputs per warp), SYT rows along x2, and it marches along x3
+// over zc planes.  Lane x holds q on its column for the strip's rows plus a
+// one-row halo; q at x + 1 comes by shuffle, so a lane forms the fluxes of
+// the corners at x + 1/2 alone.  Of the eight corners around a voxel, the
+// four at x + 1/2 are the lane's own and the four at x - 1/2 belong to the
+// lane on its left: each lane sums, per output row, the signed fluxes it owes
+// itself (B) and its right neighbour (A), and one shuffle per output moves
+// A.  The partial sums of corner plane k - 1/2 carry over to the next plane
+// in registers, so every corner is formed once.  No shared memory, no block
+// barrier; the next plane's loads are issued before the current plane's
+// arithmetic.  With N3 = 1 the x3 neighbours are the plane itself, the x3
+// flux vanishes and the kernel is the 2D stencil.
+constexpr int kStencilWarps = 4;                   // warps per CTA (consecutive x2 strips)
+constexpr int kStencilOut = 30;                    // outputs per warp along x1
+template <typename R>
+struct StencilRows {
+  static constexpr int SYT = sizeof(R) == 4 ? 4 : 4;
+};
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(32 * kStencilWarps)
 k_helm_stencil(Geo g, const R* __restrict__ q, R* __restrict__ y, const uint8_t* __restrict__ phase,
                const R* __restrict__ ell2_tab, R c0, R c1, R c2, int zc, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
-  constexpr int SX = kStencilX, SY = kStencilY;
-  constexpr int QX = SX + 2, QY = SY + 2;          // q plane with halo
-  constexpr int GX = SX + 1, GY = SY + 1;          // corner plane
-  __shared__ R Q[3][QY][QX];
-  __shared__ R Lw[3][QY][QX];                      // l^2 at each q-tile voxel
-  __shared__ R G[2][3][GY][GX];
-  __shared__ int colx[QX];
-  __shared__ long long rowy[QY];
+  constexpr int SYT = StencilRows<R>::SYT;
+  constexpr unsigned kAll = 0xffffffffu;
   __shared__ R l2[kMaxPhases];
-  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
-  const long long plane = (long long)n1 * n2;
-  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, n3);
-  // periodic tile coordinates, once per CTA (tiles may be wider than short axes)
-  if (threadIdx.x < QX) colx[threadIdx.x] = ((x0 - 1 + (int)threadIdx.x) % n1 + n1) % n1;
-  if (threadIdx.x < QY) rowy[threadIdx.x] = (long long)(((y0 - 1 + (int)threadIdx.x) % n2 + n2) % n2) * n1;
   if (threadIdx.x < kMaxPhases) l2[threadIdx.x] = ell2_tab[threadIdx.x];
   __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  const int y0 = (blockIdx.y * kStencilWarps + wid) * SYT;
+  if (y0 >= n2) return;                            // whole warp (y0 is warp-uniform)
+  const int x = blockIdx.x * kStencilOut - 1 + lane;
+  const int xw = ((x % n1) + n1) % n1;
+  const bool outx = lane >= 1 && lane <= kStencilOut && x < n1;
+  const long long plane = (long long)n1 * n2;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, n3);
+  int ro[SYT + 2];                                 // rows y0 - 1 .. y0 + SYT, periodic
+#pragma unroll
+  for (int r = 0; r < SYT + 2; r++) ro[r] = (((y0 - 1 + r) % n2 + n2) % n2) * n1 + xw;
   // planes k in [z0 - 1, z1] wrap at most once
-  auto load_plane = [&](int s, int k) {
-    const long long base = (long long)(k < 0 ? k + n3 : (k >= n3 ? k - n3 : k)) * plane;
-    for (int e = threadIdx.x; e < QX * QY; e += kThreads) {
-      const int iy = e / QX, ix = e - iy * QX;
-      const long long idx = base + rowy[iy] + colx[ix];
-      Q[s][iy][ix] = q[idx];
-      Lw[s][iy][ix] = l2[phase[idx]];
+  auto pbase = [&](int k) -> long long { return (long long)(k < 0 ? k + n3 : (k >= n3 ? k - n3 : k)) * plane; };
+  R nq[SYT + 2];
+  uint8_t nph[SYT + 1];
+  auto fetch = [&](int k) {
+    const long long b = pbase(k);
+#pragma unroll
+    for (int r = 0; r < SYT + 2; r++) nq[r] = q[b + ro[r]];
+#pragma unroll
+    for (int r = 0; r < SYT + 1; r++) nph[r] = phase[b + ro[r]];
+  };
+  R qa[SYT + 2], qra[SYT + 2], wa[SYT + 1];        // plane a: q, q at x + 1, l^2 at the corner index
+  R Ap[SYT], Bp[SYT];                              // sums owed by corner plane k - 1/2
+  auto take = [&](R* qv, R* qr, R* w) {
+#pragma unroll
+    for (int r = 0; r < SYT + 2; r++) {
+      qv[r] = nq[r];
+      qr[r] = __shfl_down_sync(kAll, nq[r], 1);
+    }
+#pragma unroll
+    for (int r = 0; r < SYT + 1; r++) w[r] = l2[nph[r]];
+  };
+  // corner plane between planes a (low) and b (high): the sums it owes the
+  // output plane above it (as its lower corner plane) and below it
+  auto corner_plane = [&](const R* qb, const R* qrb, R* Alo, R* Blo, R* Ahi, R* Bhi) {
+    R fx[SYT + 1], fy[SYT + 1], fz[SYT + 1];
+#pragma unroll
+    for (int c = 0; c < SYT + 1; c++) {
+      const R mx = ((qra[c] - qa[c]) + (qra[c + 1] - qa[c + 1])) + ((qrb[c] - qb[c]) + (qrb[c + 1] - qb[c + 1]));
+      const R my = ((qa[c + 1] - qa[c]) + (qra[c + 1] - qra[c])) + ((qb[c + 1] - qb[c]) + (qrb[c + 1] - qrb[c]));
+      const R mz = ((qb[c] - qa[c]) + (qrb[c] - qra[c])) + ((qb[c + 1] - qa[c + 1]) + (qrb[c + 1] - qra[c + 1]));
+      const R w = wa[c];
+      fx[c] = w * c0 * mx;
+      fy[c] = w * c1 * my;
+      fz[c] = w * c2 * mz;
+    }
+    // D_j^T: a corner on the low side of the voxel along x_j adds its flux
+    // F_j, one on the high side subtracts it.  Row r's corners: c = r (at
+    // y - 1/2) and c = r + 1 (at y + 1/2).
+#pragma unroll
+    for (int r = 0; r < SYT; r++) {
+      const R a = fx[r] + fy[r], b = fx[r] - fy[r];
+      const R a1 = fx[r + 1] + fy[r + 1], b1 = fx[r + 1] - fy[r + 1];
+      // output plane above (this corner plane is below it: +F_z)
+      Ahi[r] = (a + fz[r]) + (b1 + fz[r + 1]);
+      Bhi[r] = -((b - fz[r]) + (a1 - fz[r + 1]));
+      // output plane below (this corner plane is above it: -F_z)
+      Alo[r] = (a - fz[r]) + (b1 - fz[r + 1]);
+      Blo[r] = -((b + fz[r]) + (a1 + fz[r + 1]));
     }
   };
-  // corner fluxes of corner plane k from q planes a (k) and b (k + 1); l^2
-  // at the corner's own index (plane a)
-  auto corners = [&](int sg, int a, int b) {
-    for (int e = threadIdx.x; e < GX * GY; e += kThreads) {
-      const int cy = e / GX, cx = e - cy * GX;
-      const R q000 = Q[a][cy][cx], q100 = Q[a][cy][cx + 1], q010 = Q[a][cy + 1][cx], q110 = Q[a][cy + 1][cx + 1];
-      const R q001 = Q[b][cy][cx], q101 = Q[b][cy][cx + 1], q011 = Q[b][cy + 1][cx], q111 = Q[b][cy + 1][cx + 1];
-      const R w = Lw[a][cy][cx];
-      G[sg][0][cy][cx] = w * c0 * ((q100 - q000) + (q110 - q010) + (q101 - q001) + (q111 - q011));
-      G[sg][1][cy][cx] = w * c1 * ((q010 - q000) + (q110 - q100) + (q011 - q001) + (q111 - q101));
-      G[sg][2][cy][cx] = w * c2 * ((q001 - q000) + (q101 - q100) + (q011 - q010) + (q111 - q110));
+  fetch(z0 - 1);
+  take(qa, qra, wa);
+  fetch(z0);
+  {
+    R qb[SYT + 2], qrb[SYT + 2], wb[SYT + 1], Ad[SYT], Bd[SYT];
+    take(qb, qrb, wb);
+    if (z0 + 1 <= z1) fetch(z0 + 1);
+    corner_plane(qb, qrb, Ad, Bd, Ap, Bp);
+#pragma unroll
+    for (int r = 0; r < SYT + 2; r++) {
+      qa[r] = qb[r];
+      qra[r] = qrb[r];
     }
-  };
-  int s0 = 0, s1 = 1, s2 = 2, gp = 0, gc = 1;
-  load_plane(s0, z0 - 1);
-  load_plane(s1, z0);
-  __syncthreads();
-  corners(gp, s0, s1);
-  const int ix = threadIdx.x % SX, iy = threadIdx.x / SX;
-  const bool mine = x0 + ix < n1 && y0 + iy < n2;
-  const long long obase = (long long)(y0 + iy) * n1 + (x0 + ix);
+#pragma unroll
+    for (int r = 0; r < SYT + 1; r++) wa[r] = wb[r];
+  }
   for (int k = z0; k < z1; k++) {
-    load_plane(s2, k + 1);
-    __syncthreads();
-    corners(gc, s1, s2);
-    __syncthreads();
-    if (mine) {
-      // D_j^T of the fluxes at the eight corners around the voxel (the
-      // identity part of L is added to the spectrum, exactly, by the caller)
-      R v = R(0);
+    R qb[SYT + 2], qrb[SYT + 2], wb[SYT + 1], Al[SYT], Bl[SYT], Ah[SYT], Bh[SYT];
+    take(qb, qrb, wb);                             // plane k + 1
+    if (k + 2 <= z1) fetch(k + 2);                 // in flight during this plane's arithmetic
+    corner_plane(qb, qrb, Al, Bl, Ah, Bh);
+    const long long ob = (long long)k * plane;
 #pragma unroll
-      for (int e = 0; e < 2; e++) {
-        const int cy = iy + 1 - e, cx = ix + 1 - e;
-        v += (G[gc][0][cy][ix] - G[gc][0][cy][ix + 1]) + (G[gp][0][cy][ix] - G[gp][0][cy][ix + 1]);
-        v += (G[gc][1][iy][cx] - G[gc][1][iy + 1][cx]) + (G[gp][1][iy][cx] - G[gp][1][iy + 1][cx]);
-#pragma unroll
-        for (int f = 0; f < 2; f++) v += G[gp][2][cy][ix + 1 - f] - G[gc][2][cy][ix + 1 - f];
-      }
-      y[(long long)k * plane + obase] = v;
+    for (int r = 0; r < SYT; r++) {
+      const R v = __shfl_up_sync(kAll, Ap[r] + Al[r], 1) + (Bp[r] + Bl[r]);
+      // the identity part of L is added to the spectrum, exactly, by the caller
+      if (outx && y0 + r < n2) y[ob + ro[r + 1]] = v;
+      Ap[r] = Ah[r];
+      Bp[r] = Bh[r];
     }
-    const int t0 = s0;
-    s0 = s1;
-    s1 = s2;
-    s2 = t0;
-    const int tg = gp;
-    gp = gc;
-    gc = tg;
+#pragma unroll
+    for (int r = 0; r < SYT + 2; r++) {
+      qa[r] = qb[r];
+      qra[r] = qrb[r];
+    }
+#pragma unroll
+    for (int r = 0; r < SYT + 1; r++) wa[r] = wb[r];
   }
 }
 
@@ -957,8 +1002,12 @@ __host__ __device__ __forceinline__ size_t gamma_tma_head(int N) {
 // path only) adds bytes that no copy delivers to the expected count, so the
 // wait runs out although the copy lands; the CTA then counts those bytes
 // itself, so the phase completes and no copy is in flight when it returns.
-template <typename R, int NC, int TXR, int NAX>
-__global__ void __launch_bounds__(kThreads, 2)
+//
+// NTH threads per CTA: 256 with the default tile (two CTAs per SM), 128 with
+// a tile half as wide (four CTAs per SM, so that more tiles are in flight
+// per SM); the per-column arithmetic is the same, so are the results.
+template <typename R, int NC, int TXR, int NAX, int NTH = kThreads>
+__global__ void __launch_bounds__(NTH, NTH == kThreads ? 2 : 4)
 k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const C2<R>* __restrict__ tw,
             Mask6 mask, int dc_mode, const KrylovCtl* __restrict__ ctl, int* __restrict__ wait_err,
             unsigned long long wait_ns, unsigned extra_tx) {
@@ -979,7 +1028,7 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
     mbar_expect_tx(&bar, kBytes + extra_tx);
     tma_load_4d(buf, &tmap, q0 * U8, 0, blockIdx.y, 0, &bar);
   }
-  for (int i = threadIdx.x; i < NAX; i += kThreads) {
+  for (int i = threadIdx.x; i < NAX; i += NTH) {
     tws[i] = tw[i];
     zs[i] = t.s[2][i];
     zc[i] = t.c[2][i];
@@ -993,10 +1042,10 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
     mbar_wait(&bar, 0, wait_ns);   // the copy in flight, once more bounded
     return;
   }
-  fftreg_forward<R, NAX, NC * TXR, RS>(buf, tws);
+  fftreg_forward<R, NAX, NC * TXR, RS, NTH>(buf, tws);
   {
     // the register passes leave frequency reg_freq(n) at tile row n
-    constexpr int RPT = kThreads / TXR;
+    constexpr int RPT = NTH / TXR;
     const int col = threadIdx.x % TXR;
     if (col < cols) {
       LastSym<R> sy;
@@ -1017,7 +1066,7 @@ k_gamma_tma(Geo g, Tables<R> t, const __grid_constant__ CUtensorMap tmap, const 
     }
   }
   __syncthreads();
-  fftreg_inverse<R, NAX, NC * TXR, RS>(buf, tws);
+  fftreg_inverse<R, NAX, NC * TXR, RS, NTH>(buf, tws);
   tma_fence_smem();
   __syncthreads();
   if (threadIdx.x == 0) tma_store_4d_and_wait(&tmap, buf, q0 * U8, 0, blockIdx.y, 0);
@@ -2105,8 +2154,9 @@ void Ops<R>::helm_stencil(const Geo& g, const LaunchCfg& lc, cudaStream_t st, co
   const R c1 = (R)(1.0 / (16.0 * g.h[1] * g.h[1]));
   const R c2 = g.d == 3 ? (R)(1.0 / (16.0 * g.h[2] * g.h[2])) : R(0);
   const int zc = g.n3 < 16 ? g.n3 : 16;
-  dim3 grid((g.n1 + kStencilX - 1) / kStencilX, (g.n2 + kStencilY - 1) / kStencilY, (g.n3 + zc - 1) / zc);
-  k_helm_stencil<R><<<grid, kThreads, 0, st>>>(g, q, y, phase, ell2_tab, c0, c1, c2, zc, ctl);
+  constexpr int rows = kStencilWarps * StencilRows<R>::SYT;
+  dim3 grid((g.n1 + kStencilOut - 1) / kStencilOut, (g.n2 + rows - 1) / rows, (g.n3 + zc - 1) / zc);
+  k_helm_stencil<R><<<grid, 32 * kStencilWarps, 0, st>>>(g, q, y, phase, ell2_tab, c0, c1, c2, zc, ctl);
 }
 
 template <typename R>
@@ -2153,26 +2203,35 @@ void Ops<R>::gamma(const Geo& g, const Tables<R>& t, const LaunchCfg& lc, cudaSt
     // TMA path: the box {TX6 columns, 6 components, 1, N} of the half
     // spectrum seen as 8-byte elements [z][y][c][x]
     constexpr int TX6 = RegTx<R, 6>::v;
+    constexpr int TXN = TX6 / 2;                  // the narrow tile (128 threads)
+    const bool narrow = lc.gamma_narrow != 0;
+    const int txc = narrow ? TXN : TX6;
     constexpr int U8 = (int)sizeof(C2<R>) / 8;
     const unsigned long long cb = sizeof(C2<R>);
     const unsigned long long dims[4] = {(unsigned long long)g.ps * U8, 6ULL, (unsigned long long)g.n2,
                                         (unsigned long long)g.n3};
     const unsigned long long strides[3] = {(unsigned long long)g.sstride * cb, (unsigned long long)g.ps * cb,
                                            (unsigned long long)g.ps * g.n2 * cb};
-    const unsigned box[4] = {(unsigned)(TX6 * U8), 6u, 1u, (unsigned)si.N};
+    const unsigned box[4] = {(unsigned)(txc * U8), 6u, 1u, (unsigned)si.N};
     const CUtensorMap* map = tensor_map_8b(S, 4, dims, strides, box);
     if (map) {
       // column tiles up to P1 (inside the padded row: ps is a multiple of 16)
-      const size_t smt = gamma_tma_head<R>(si.N) + (size_t)si.N * 6 * TX6 * sizeof(C2<R>);
-      dim3 gt((g.P1 + TX6 - 1) / TX6, g.n2, 1);
-      auto launch = [&](auto k) {
+      const size_t smt = gamma_tma_head<R>(si.N) + (size_t)si.N * 6 * txc * sizeof(C2<R>);
+      dim3 gt((g.P1 + txc - 1) / txc, g.n2, 1);
+      auto launch = [&](auto k, int nth) {
         set_smem(k, smt);
-        k<<<gt, kThreads, smt, st>>>(g, t, *map, t.tw[axis], m, dc_mode, ctl, wait_err, wait_ns,
-                                     (unsigned)extra_tx);
+        k<<<gt, nth, smt, st>>>(g, t, *map, t.tw[axis], m, dc_mode, ctl, wait_err, wait_ns, (unsigned)extra_tx);
       };
-      if (si.N == 256) launch(k_gamma_tma<R, 6, TX6, 256>);
-      else if (si.N == 128) launch(k_gamma_tma<R, 6, TX6, 128>);
-      else launch(k_gamma_tma<R, 6, TX6, 64>);
+      if (!narrow) {
+        if (si.N == 256) launch(k_gamma_tma<R, 6, TX6, 256>, kThreads);
+        else if (si.N == 128) launch(k_gamma_tma<R, 6, TX6, 128>, kThreads);
+        else launch(k_gamma_tma<R, 6, TX6, 64>, kThreads);
+      } else {
+        constexpr int NT = kThreads / 2;
+        if (si.N == 256) launch(k_gamma_tma<R, 6, TXN, 256, NT>, NT);
+        else if (si.N == 128) launch(k_gamma_tma<R, 6, TXN, 128, NT>, NT);
+        else launch(k_gamma_tma<R, 6, TXN, 64, NT>, NT);
+      }
       return;
     }
   }

@@ -44,6 +44,7 @@ struct LaunchCfg {
   int tx;                // q1 columns per CTA of the strided passes
   int n_ew_blocks;       // CTAs of element-wise kernels
   int max_blocks;        // upper bound of CTAs of any reducing kernel
+  int gamma_narrow;      // 3D six-component last-axis pass: half-width TMA tile, 128 threads
 };
 
 template <typename R>
@@ -152,9 +153,16 @@ void k_err_eps(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const double*
                const double* eps_old, double* part);
 void k_err_abar(const Geo& g, const LaunchCfg& lc, cudaStream_t st, const double* a_new,
                 const double* a_old, double* part);
-// finalize: reduce nslots slots of per-CTA partials; INIT modes also store
-// rtol2 = scale and maxit = imax into ctl.
-void k_finalize(cudaStream_t st, const double* part, int nblocks, int nblk_stride, int nslots,
+// finalize: reduce nslots (<= 16) slots of per-CTA partials; INIT modes
+// also store rtol2 = scale and maxit = imax into ctl.  fs: the handle's
+// scratch of the two-level reduction (ticket zero between launches; the
+// launches of one handle are serialised on its stream).
+constexpr int kFinMaxCtas = 64;
+struct FinScratch {
+  double stage[16 * kFinMaxCtas];
+  unsigned ticket;
+};
+void k_finalize(cudaStream_t st, FinScratch* fs, const double* part, int nblocks, int nblk_stride, int nslots,
                 int mode, KrylovCtl* ctl, double* out, double scale, int imax = 0, int stall = 0);
 // out[j][v] = rotated-scheme derivative along x_j of the FP64 field a at the
 // voxel corner v + 1/2 (j < d)

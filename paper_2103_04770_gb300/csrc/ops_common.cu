@@ -1,6 +1,8 @@
 // Precision-independent reductions: deterministic finalisation of per-CTA
 // partial sums (FP64) into Krylov scalars, and the staggered-error sweeps
 // of Algorithm 1 (iii).
+#include <algorithm>
+
 #include "ops.h"
 #include "tma.cuh"
 
@@ -8,47 +10,72 @@ namespace rvk {
 
 void tensor_map_evict(const void* base) { tensor_map_evict_impl(base); }
 
-// One CTA of kFinThreads: slot s is reduced in a fixed order (thread t sums
-// blocks t, t + kFinThreads, ... in eight interleaved accumulators; then a
-// fixed tree), so results are reproducible.  Eight loads in flight per
-// thread over 1024 threads keep the 32 K partials of the x1 passes at
-// 256^3 to a few round trips.
-constexpr int kFinThreads = 1024;
+// Partial sums of the producing kernels (one per CTA and slot) are reduced
+// in two levels, both in a fixed order so that results are reproducible:
+// CTA c of the finalisation sums the contiguous block range c of every slot
+// (its threads strided over the range, then a fixed tree) into fs->stage;
+// the CTA that arrives last (atomic ticket) sums the stage entries of each
+// slot in index order, applies the mode's Krylov update and re-arms the
+// ticket.  At 256^3 the 64 K partials of the x1 passes take one load round
+// per thread instead of eight sequential ones in a single CTA.
+constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads)
 k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int nslots, int mode,
-                KrylovCtl* ctl, double* out, double scale, int imax, int stall) {
-  __shared__ double red[kFinThreads];
+                KrylovCtl* ctl, double* out, double scale, int imax, int stall, FinScratch* __restrict__ fs) {
+  __shared__ double red[kFinThreads / 32];
   __shared__ double vals[16];
+  __shared__ int last;
   const bool is_max = mode == FIN_MAXS;
+  const int chunk = (nblocks + gridDim.x - 1) / gridDim.x;
+  const int b0 = blockIdx.x * chunk, b1 = min(nblocks, b0 + chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int s = 0; s < nslots; s++) {
     const double* ps = part + (long long)s * stride;
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int b = threadIdx.x;
-    for (; b + 7 * kFinThreads < nblocks; b += 8 * kFinThreads) {
-      double x[8];
+    double a[4] = {0, 0, 0, 0};
+    int b = b0 + threadIdx.x;
+    for (; b + 3 * kFinThreads < b1; b += 4 * kFinThreads) {
+      double x[4];
 #pragma unroll
-      for (int k = 0; k < 8; k++) x[k] = ps[b + k * kFinThreads];
+      for (int k = 0; k < 4; k++) x[k] = ps[b + k * kFinThreads];
 #pragma unroll
-      for (int k = 0; k < 8; k++) a[k] = is_max ? fmax(a[k], x[k]) : a[k] + x[k];
+      for (int k = 0; k < 4; k++) a[k] = is_max ? fmax(a[k], x[k]) : a[k] + x[k];
     }
-    for (; b < nblocks; b += kFinThreads) a[0] = is_max ? fmax(a[0], ps[b]) : a[0] + ps[b];
-    double acc;
-    if (is_max) acc = fmax(fmax(fmax(a[0], a[1]), fmax(a[2], a[3])), fmax(fmax(a[4], a[5]), fmax(a[6], a[7])));
-    else acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    red[threadIdx.x] = acc;
+    for (; b < b1; b += kFinThreads) a[0] = is_max ? fmax(a[0], ps[b]) : a[0] + ps[b];
+    double acc = is_max ? fmax(fmax(a[0], a[1]), fmax(a[2], a[3])) : (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, acc, o);
+      acc = is_max ? fmax(acc, y) : acc + y;
+    }
+    if (lane == 0) red[wid] = acc;
     __syncthreads();
-    for (int o = kFinThreads / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
-        red[threadIdx.x] = is_max ? fmax(red[threadIdx.x], red[threadIdx.x + o])
-                                  : red[threadIdx.x] + red[threadIdx.x + o];
-      }
-      __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = red[0];
+      for (int w = 1; w < kFinThreads / 32; w++) t = is_max ? fmax(t, red[w]) : t + red[w];
+      fs->stage[s * kFinMaxCtas + blockIdx.x] = t;
     }
-    if (threadIdx.x == 0) vals[s] = red[0];
     __syncthreads();
   }
+  // the stage entries of this CTA are visible before its ticket is taken
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&fs->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < nslots) {
+    const int s = threadIdx.x;
+    double t = __ldcg(&fs->stage[s * kFinMaxCtas]);
+    for (int c = 1; c < (int)gridDim.x; c++) {
+      const double y = __ldcg(&fs->stage[s * kFinMaxCtas + c]);
+      t = is_max ? fmax(t, y) : t + y;
+    }
+    vals[s] = t;
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  fs->ticket = 0u;
   switch (mode) {
     case FIN_SUMS:
     case FIN_MAXS:
@@ -127,10 +154,12 @@ k_finalize_impl(const double* __restrict__ part, int nblocks, int stride, int ns
   }
 }
 
-void k_finalize(cudaStream_t st, const double* part, int nblocks, int nblk_stride, int nslots, int mode,
-                KrylovCtl* ctl, double* out, double scale, int imax, int stall) {
-  k_finalize_impl<<<1, kFinThreads, 0, st>>>(part, nblocks, nblk_stride, nslots, mode, ctl, out, scale, imax,
-                                             stall);
+void k_finalize(cudaStream_t st, FinScratch* fs, const double* part, int nblocks, int nblk_stride, int nslots,
+                int mode, KrylovCtl* ctl, double* out, double scale, int imax, int stall) {
+  // about 1024 partials per CTA of the first level
+  const int ctas = std::max(1, std::min(kFinMaxCtas, (nblocks + 1023) / 1024));
+  k_finalize_impl<<<ctas, kFinThreads, 0, st>>>(part, nblocks, nblk_stride, nslots, mode, ctl, out, scale, imax,
+                                                stall, fs);
 }
 
 struct Add6 { double a[6]; };

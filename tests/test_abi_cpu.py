@@ -103,6 +103,8 @@ def test_batch_adjoint_and_field_calls_reject_bad_arguments(pkg):
     assert lib.rve_batch_size(None) == 0
     lib.rve_batch_free(None)
     assert lib.rve_set_graphs(None, 1) == pkg.RVE_ERR_ARG
+    assert lib.rve_set_gamma_tile(None, 1) == pkg.RVE_ERR_ARG
+    assert lib.rve_get_gamma_tile(None, None) == pkg.RVE_ERR_ARG
     assert lib.rve_autotune(None, 1, None, None, None) == pkg.RVE_ERR_ARG
     assert lib.rve_set_stiffness_field(None, None) == pkg.RVE_ERR_ARG
     J = ctypes.c_double()

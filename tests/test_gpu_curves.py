@@ -46,7 +46,10 @@ def _golden(N):
     if not os.path.exists(path):
         pytest.skip("no stored curve for %d^2" % N)
     z = np.load(path)
-    return z, json.loads(str(z["meta"]))
+    meta = json.loads(str(z["meta"]))
+    if str(meta.get("stop", "")).startswith("running"):
+        pytest.skip("stored curve for %d^2 is still being written (%s)" % (N, meta["stop"]))
+    return z, meta
 
 
 def _options(meta, prec):

@@ -237,6 +237,34 @@ def test_apply_gamma(n, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [(16, 8, 256), (40, 6, 256), (130, 4, 256), (16, 64, 128), (12, 128, 64),
+                               (70, 5, 128)])
+def test_gamma_tile_widths_agree(n, prec):
+    """The 3D projection pass with the narrow TMA tile (rve_set_gamma_tile):
+    bit-identical to the default tile, ragged last column tiles included
+    (P1 = 66 and 36 are not multiples of the tile widths)."""
+    g = O.Grid(n)
+    rng = np.random.default_rng(5)
+    phase = (rng.random(g.shape) < 0.3).astype(np.uint8)
+    ctrl = mixed_ctrl(3)
+    h = handle(n, phase, prec, ctrl=ctrl)
+    try:
+        tau = rng.standard_normal(g.shape + (6,)) + np.array([3.0, -1.0, 0.5, 0.2, 0.1, -0.3])
+        outs = []
+        for narrow in (0, 1, 0):
+            pkg.rve_set_gamma_tile(h, narrow)
+            out = torch.empty(6, g.V, device="cuda", dtype=torch.float64)
+            pkg.rve_op_apply_gamma(h, dev(cm(tau, 6)), out)
+            outs.append(host(out))
+        assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+        ref = O.G_apply(tau, g, stress_mask_c(ctrl, 3))
+        tol = 1e-12 if prec == 0 else 5e-6
+        assert np.abs(outs[1] - cm(ref, 6)).max() <= tol * np.abs(tau).max()
+    finally:
+        pkg.rve_free(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [(24, 20), (40, 15), (8, 6, 10), (12, 15, 8), (96, 20), (64, 16, 24),
                                (256, 8, 8), (16, 8, 256), (16, 64, 128), (128, 8, 10)])
 def test_matvec_and_cg(n, prec):
