@@ -865,9 +865,10 @@ FAIL_STAGES = {0: "none", 1: "Newton", 2: "CG", 3: "PCG", 4: "staggered", 5: "nu
 def run_objectivity(args):
     """Mesh objectivity of the 2D single-particle cell: the FP64 GPU form
     runs the load path (uniaxial E11 in steps of 1e-3) at 128^2, 256^2 and
-    512^2 with the length fixed in physical units (l = L/16), each until the
-    end of the path or the first increment the staggered scheme cannot
-    converge.  Past the peak of the 512^2 curve, the softening branches of the
+    512^2 with the length fixed in physical units (l = L/16), each increment
+    through the cut-back step (on the finer grids Newton needs sub-steps where
+    plasticity spreads from the particle), until the end of the path or the
+    first increment that cannot be converged.  Past the peak of the 512^2 curve, the softening branches of the
     coarser grids are compared with it: the largest |Sigma11(E) - Sigma11_512(E)|
     over the common increments, relative to the 512^2 peak."""
     import torch
@@ -885,15 +886,17 @@ def run_objectivity(args):
         pts, status = [], "end of path"
         with pkg.RVE(cfg, precision=0, options=opt) as r:
             for i in range(cfg.target.shape[0]):
-                info = r.step(raise_on_error=False)
+                info = r.step_adaptive(max_cuts=7, raise_on_error=False)
                 if info["status"] != pkg.RVE_OK:
                     status = "increment %d: %s (%s budget)" % (
                         i + 1, pkg.rve_status_string(info["status"]), FAIL_STAGES.get(info["fail_stage"], "?"))
                     break
-                pts.append([round(info["eps"][0], 6), info["sigma"][0], info["D_max"], info["staggered_iters"]])
+                pts.append([round(info["eps"][0], 6), info["sigma"][0], info["D_max"], info["staggered_iters"],
+                            info["substeps"]])
                 print(json.dumps({"N": N, "increment": i + 1, "S11": info["sigma"][0], "D_max": info["D_max"],
-                                  "stag": info["staggered_iters"], "newton": info["newton_iters"],
-                                  "cg": info["cg_iters"], "pcg": info["pcg_iters"]}), file=sys.stderr, flush=True)
+                                  "stag": info["staggered_iters"], "substeps": info["substeps"],
+                                  "newton": info["newton_iters"], "cg": info["cg_iters"],
+                                  "pcg": info["pcg_iters"]}), file=sys.stderr, flush=True)
         curves[N] = {"curve": pts, "status": status, "seconds": round(time.perf_counter() - t0, 1)}
     ref_N = max(curves)
     ref = np.array([p[1] for p in curves[ref_N]["curve"]])
@@ -916,9 +919,10 @@ def run_objectivity(args):
             "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "2d_disc_objectivity", "grids": list(curves), "ell": "L/16",
                        "load": "uniaxial E11 steps of 1e-3, Sigma22 = Sigma12 = 0, plane strain",
-                       "options": "production FP64 (tol 1e-6), staggered budget 1000, CG budget %d per Newton step"
-                                  % args.obj_max_cg},
+                       "options": "production FP64 (tol 1e-6), staggered budget 1000, CG budget %d per Newton step, "
+                                  "cut-back step (max 7 halvings)" % args.obj_max_cg},
             "peak_increment_%d" % ref_N: ipk + 1, "comparison": out,
+            "curve_columns": ["E11", "S11", "D_max", "staggered", "substeps"],
             "curves": {str(N): c for N, c in curves.items()}}
 
 

@@ -40,12 +40,22 @@ static void set_smem(K kernel, size_t bytes) {
   // never lowered, so a concurrent caller with a smaller tile cannot shrink
   // it between another caller's check and launch.  Each launch still gets
   // only its own dynamic size.
-  if (bytes <= 48 * 1024) return;
+  //
+  // Every kernel launched through here stages its tiles in shared memory and
+  // reads global memory once: it asks, once, for the largest shared-memory
+  // carveout, so that the resident CTAs per SM are limited by its tile and
+  // registers rather than by an L1-leaning split.
   static std::mutex mu;
-  static std::unordered_set<const void*> done;
+  static std::unordered_set<const void*> done, carved;
   const void* key = reinterpret_cast<const void*>(kernel);
   std::lock_guard<std::mutex> lock(mu);
-  if (done.count(key)) return;
+  if (!carved.count(key)) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+      cudaGetLastError();
+    carved.insert(key);
+  }
+  if (bytes <= 48 * 1024 || done.count(key)) return;
   int dev = 0, optin = 0;
   cudaFuncAttributes fa{};
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -367,67 +377,78 @@ k_helm_stencil(Geo g, const R* __restrict__ q, R* __restrict__ y, const uint8_t*
 #pragma unroll
     for (int r = 0; r < SYT + 1; r++) nph[r] = phase[b + ro[r]];
   };
-  R qa[SYT + 2], qra[SYT + 2], wa[SYT + 1];        // plane a: q, q at x + 1, l^2 at the corner index
+  // plane a (the lower plane of the current corner plane): q, q at x + 1,
+  // l^2 at the corner index, and two terms of its corner derivatives kept
+  // from the step where it was the upper plane: dx = q(x+1) - q(x) per row
+  // and dy = the two x2 edge differences per corner row
+  R qa[SYT + 2], qra[SYT + 2], wa[SYT + 1], dxa[SYT + 2], dya[SYT + 1];
   R Ap[SYT], Bp[SYT];                              // sums owed by corner plane k - 1/2
-  auto take = [&](R* qv, R* qr, R* w) {
+  auto take = [&](R* qv, R* qr, R* w, R* dx, R* dy) {
 #pragma unroll
     for (int r = 0; r < SYT + 2; r++) {
       qv[r] = nq[r];
       qr[r] = __shfl_down_sync(kAll, nq[r], 1);
+      dx[r] = qr[r] - qv[r];
     }
+#pragma unroll
+    for (int c = 0; c < SYT + 1; c++) dy[c] = (qv[c + 1] - qv[c]) + (qr[c + 1] - qr[c]);
 #pragma unroll
     for (int r = 0; r < SYT + 1; r++) w[r] = l2[nph[r]];
   };
   // corner plane between planes a (low) and b (high): the sums it owes the
   // output plane above it (as its lower corner plane) and below it
-  auto corner_plane = [&](const R* qb, const R* qrb, R* Alo, R* Blo, R* Ahi, R* Bhi) {
-    R fx[SYT + 1], fy[SYT + 1], fz[SYT + 1];
+  auto corner_plane = [&](const R* qb, const R* qrb, const R* dxb, const R* dyb, R* Alo, R* Blo, R* Ahi,
+                          R* Bhi) {
+    R zr[SYT + 2], fx[SYT + 1], fy[SYT + 1], fz[SYT + 1];
+#pragma unroll
+    for (int r = 0; r < SYT + 2; r++) zr[r] = (qb[r] - qa[r]) + (qrb[r] - qra[r]);
 #pragma unroll
     for (int c = 0; c < SYT + 1; c++) {
-      const R mx = ((qra[c] - qa[c]) + (qra[c + 1] - qa[c + 1])) + ((qrb[c] - qb[c]) + (qrb[c + 1] - qb[c + 1]));
-      const R my = ((qa[c + 1] - qa[c]) + (qra[c + 1] - qra[c])) + ((qb[c + 1] - qb[c]) + (qrb[c + 1] - qrb[c]));
-      const R mz = ((qb[c] - qa[c]) + (qrb[c] - qra[c])) + ((qb[c + 1] - qa[c + 1]) + (qrb[c + 1] - qra[c + 1]));
       const R w = wa[c];
-      fx[c] = w * c0 * mx;
-      fy[c] = w * c1 * my;
-      fz[c] = w * c2 * mz;
+      fx[c] = (w * c0) * ((dxa[c] + dxa[c + 1]) + (dxb[c] + dxb[c + 1]));
+      fy[c] = (w * c1) * (dya[c] + dyb[c]);
+      fz[c] = (w * c2) * (zr[c] + zr[c + 1]);
     }
     // D_j^T: a corner on the low side of the voxel along x_j adds its flux
     // F_j, one on the high side subtracts it.  Row r's corners: c = r (at
-    // y - 1/2) and c = r + 1 (at y + 1/2).
+    // y - 1/2) and c = r + 1 (at y + 1/2); the x3 flux enters with + for the
+    // output plane above this corner plane and with - for the one below.
 #pragma unroll
     for (int r = 0; r < SYT; r++) {
-      const R a = fx[r] + fy[r], b = fx[r] - fy[r];
-      const R a1 = fx[r + 1] + fy[r + 1], b1 = fx[r + 1] - fy[r + 1];
-      // output plane above (this corner plane is below it: +F_z)
-      Ahi[r] = (a + fz[r]) + (b1 + fz[r + 1]);
-      Bhi[r] = -((b - fz[r]) + (a1 - fz[r + 1]));
-      // output plane below (this corner plane is above it: -F_z)
-      Alo[r] = (a - fz[r]) + (b1 - fz[r + 1]);
-      Blo[r] = -((b + fz[r]) + (a1 + fz[r + 1]));
+      const R P = (fx[r] + fy[r]) + (fx[r + 1] - fy[r + 1]);      // owed to the lane on the right
+      const R Q = -((fx[r] - fy[r]) + (fx[r + 1] + fy[r + 1]));   // owed to this lane
+      const R Z = fz[r] + fz[r + 1];
+      Ahi[r] = P + Z;
+      Bhi[r] = Q + Z;
+      Alo[r] = P - Z;
+      Blo[r] = Q - Z;
     }
   };
   fetch(z0 - 1);
-  take(qa, qra, wa);
+  take(qa, qra, wa, dxa, dya);
   fetch(z0);
   {
-    R qb[SYT + 2], qrb[SYT + 2], wb[SYT + 1], Ad[SYT], Bd[SYT];
-    take(qb, qrb, wb);
+    R qb[SYT + 2], qrb[SYT + 2], wb[SYT + 1], dxb[SYT + 2], dyb[SYT + 1], Ad[SYT], Bd[SYT];
+    take(qb, qrb, wb, dxb, dyb);
     if (z0 + 1 <= z1) fetch(z0 + 1);
-    corner_plane(qb, qrb, Ad, Bd, Ap, Bp);
+    corner_plane(qb, qrb, dxb, dyb, Ad, Bd, Ap, Bp);
 #pragma unroll
     for (int r = 0; r < SYT + 2; r++) {
       qa[r] = qb[r];
       qra[r] = qrb[r];
+      dxa[r] = dxb[r];
     }
 #pragma unroll
-    for (int r = 0; r < SYT + 1; r++) wa[r] = wb[r];
+    for (int r = 0; r < SYT + 1; r++) {
+      wa[r] = wb[r];
+      dya[r] = dyb[r];
+    }
   }
   for (int k = z0; k < z1; k++) {
-    R qb[SYT + 2], qrb[SYT + 2], wb[SYT + 1], Al[SYT], Bl[SYT], Ah[SYT], Bh[SYT];
-    take(qb, qrb, wb);                             // plane k + 1
+    R qb[SYT + 2], qrb[SYT + 2], wb[SYT + 1], dxb[SYT + 2], dyb[SYT + 1], Al[SYT], Bl[SYT], Ah[SYT], Bh[SYT];
+    take(qb, qrb, wb, dxb, dyb);                   // plane k + 1
     if (k + 2 <= z1) fetch(k + 2);                 // in flight during this plane's arithmetic
-    corner_plane(qb, qrb, Al, Bl, Ah, Bh);
+    corner_plane(qb, qrb, dxb, dyb, Al, Bl, Ah, Bh);
     const long long ob = (long long)k * plane;
 #pragma unroll
     for (int r = 0; r < SYT; r++) {
@@ -441,9 +462,13 @@ k_helm_stencil(Geo g, const R* __restrict__ q, R* __restrict__ y, const uint8_t*
     for (int r = 0; r < SYT + 2; r++) {
       qa[r] = qb[r];
       qra[r] = qrb[r];
+      dxa[r] = dxb[r];
     }
 #pragma unroll
-    for (int r = 0; r < SYT + 1; r++) wa[r] = wb[r];
+    for (int r = 0; r < SYT + 1; r++) {
+      wa[r] = wb[r];
+      dya[r] = dyb[r];
+    }
   }
 }
 
@@ -789,10 +814,17 @@ template <typename R, int NCOMP> struct RegRs {
 
 // TXR > 0: NAX-point axis (64, 128 or 256) through the register passes, TXR
 // columns per CTA.
+//
+// nyq > 0 (register passes, P1 = 1 + a multiple of TXR): the last column of
+// the half spectrum (q1 = N1/2) is not given a tile of its own per plane,
+// which would transform TXR columns for one; instead the CTAs of the last
+// x tile take that column from TXR consecutive planes (blockIdx.y groups
+// them; groups past the plane count exit), so that every transformed column
+// is a real one.
 template <typename R, int SIGN, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 2)
 k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
-                long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
+                long long astride, long long ostride, const KrylovCtl* __restrict__ ctl, int nyq, int nplanes) {
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -800,6 +832,30 @@ k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restri
   if (TXR) tx = TXR;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
+  if constexpr (TXR > 0) {
+    if (nyq && blockIdx.x == gridDim.x - 1) {
+      const int p0 = blockIdx.y * TXR;
+      if (p0 >= nplanes) return;
+      C2<R>* base = S + blockIdx.z * g.sstride + (g.P1 - 1);
+      for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
+      // forward: natural rows in; inverse: the spectrum into the reg_pos order
+      for (int e = threadIdx.x; e < NAX * TXR; e += kThreads) {
+        const int n = e / TXR, c = e - n * TXR;
+        const int m = (SIGN > 0) ? reg_pos<NAX>(n) : n;
+        buf[m * TXR + c] = p0 + c < nplanes ? base[(long long)(p0 + c) * ostride + (long long)n * astride]
+                                            : mk<R>(0, 0);
+      }
+      __syncthreads();
+      if constexpr (SIGN < 0) fftreg_forward<R, NAX, TXR>(buf, tws);
+      else fftreg_inverse<R, NAX, TXR>(buf, tws);
+      for (int e = threadIdx.x; e < NAX * TXR; e += kThreads) {
+        const int n = e / TXR, c = e - n * TXR;
+        const int m = (SIGN < 0) ? reg_pos<NAX>(n) : n;
+        if (p0 + c < nplanes) base[(long long)(p0 + c) * ostride + (long long)n * astride] = buf[m * TXR + c];
+      }
+      return;
+    }
+  }
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   C2<R>* base = S + blockIdx.z * g.sstride + blockIdx.y * ostride + q0;
@@ -1081,7 +1137,7 @@ __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
 // component, D = 0: the operator is applied in real space) or W_j = k_j p
 // (D > 0); inverse transform along the last axis.
 template <typename R, int D, int TXR = 0, int NAX = 256>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, D == 0 && TXR > 0 && sizeof(R) == 4 ? 3 : 2)
 k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
          C2<R>* __restrict__ p, const C2<R>* __restrict__ r, int tx, long long astride,
          long long ostride, R ell2m, const KrylovCtl* __restrict__ ctl, int raw) {
@@ -1108,27 +1164,33 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
     constexpr int PER = NAX / RPT;
     const int col = threadIdx.x % TXR, r0 = threadIdx.x / TXR;
     if (col < cols) {
-      C2<R> rv[PER], pv[PER];
+      // two halves of the thread's entries, each with all its loads issued
+      // before it is used (registers for three CTAs per SM)
+      constexpr int HALF = PER / 2;
       const bool upd = !raw && !first;
-#pragma unroll
-      for (int k = 0; k < PER; k++) {
-        const long long idx = off + (long long)(r0 + k * RPT) * astride + col;
-        rv[k] = r[idx];
-        pv[k] = upd ? p[idx] : mk<R>(0, 0);
-      }
       LastSym<R> sy;
       sy.init(g, t, q0 + col);
+#pragma unroll 1
+      for (int h = 0; h < 2; h++) {
+        C2<R> rv[HALF], pv[HALF];
 #pragma unroll
-      for (int k = 0; k < PER; k++) {
-        const int n = r0 + k * RPT;
-        C2<R> pn = rv[k];
-        if (!raw) {
-          const R Mk = R(1) / (R(1) + ell2m * sy.k2(g, t, n));
-          pn = cscale(rv[k], Mk);
-          if (upd) pn = pn + cscale(pv[k], beta);
-          p[off + (long long)n * astride + col] = pn;
+        for (int k = 0; k < HALF; k++) {
+          const long long idx = off + (long long)(r0 + (h * HALF + k) * RPT) * astride + col;
+          rv[k] = r[idx];
+          pv[k] = upd ? p[idx] : mk<R>(0, 0);
         }
-        buf[reg_pos<NAX>(n) * TXR + col] = pn;
+#pragma unroll
+        for (int k = 0; k < HALF; k++) {
+          const int n = r0 + (h * HALF + k) * RPT;
+          C2<R> pn = rv[k];
+          if (!raw) {
+            const R Mk = R(1) / (R(1) + ell2m * sy.k2(g, t, n));
+            pn = cscale(rv[k], Mk);
+            if (upd) pn = pn + cscale(pv[k], beta);
+            p[off + (long long)n * astride + col] = pn;
+          }
+          buf[reg_pos<NAX>(n) * TXR + col] = pn;
+        }
       }
     }
   } else if constexpr (IL) {
@@ -2166,8 +2228,12 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
   const int tx = axis_tx<R>(lc, si.N, 1);
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
-  dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? g.n3 : g.n2, ncomp);
+  const int nplanes = axis == 1 ? g.n3 : g.n2;
+  dim3 grid((g.P1 + tx - 1) / tx, nplanes, ncomp);
   constexpr int TXR = RegTx<R, 1>::v;
+  // the q1 = N1/2 column packed TXR planes to a CTA (register passes only)
+  const int nyq = (reg_axis(si.N) && g.P1 > 1 && (g.P1 - 1) % TXR == 0) ? 1 : 0;
+  if (nyq) grid.x = (g.P1 - 1) / TXR + 1;
   auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
     return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
   };
@@ -2175,12 +2241,12 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
     auto k = pick(k_strided_plain<R, -1, TXR, 256>, k_strided_plain<R, -1, TXR, 128>,
                   k_strided_plain<R, -1, TXR, 64>, k_strided_plain<R, -1>);
     set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl, nyq, nplanes);
   } else {
     auto k = pick(k_strided_plain<R, 1, TXR, 256>, k_strided_plain<R, 1, TXR, 128>,
                   k_strided_plain<R, 1, TXR, 64>, k_strided_plain<R, 1>);
     set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl, nyq, nplanes);
   }
 }
 

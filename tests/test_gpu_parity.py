@@ -212,7 +212,10 @@ GAMMA_GRIDS = [(32, 30), (40, 16), (2, 2), (6, 5), (16, 12, 10), (12, 15, 8), (8
                # compile-time FFT paths: N1 = 256 rows, 256-point y and last axes
                (256, 256), (256, 8, 8), (16, 256, 8), (16, 8, 256), (40, 6, 256),
                # register passes on 64- and 128-point axes; N1 = 96 and 64 compile-time rows
-               (16, 64, 128), (12, 128, 64), (24, 128), (20, 64), (96, 6, 8), (64, 10, 6)]
+               (16, 64, 128), (12, 128, 64), (24, 128), (20, 64), (96, 6, 8), (64, 10, 6),
+               # register-pass y axes with the q1 = N1/2 column packed across planes
+               # (8 planes: one partial group; 20 planes: a full and a partial group)
+               (96, 128, 8), (256, 64, 20), (64, 256, 6)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -237,12 +240,12 @@ def test_apply_gamma(n, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n", [(16, 8, 256), (40, 6, 256), (130, 4, 256), (16, 64, 128), (12, 128, 64),
-                               (70, 5, 128)])
+@pytest.mark.parametrize("n", [(16, 8, 256), (40, 6, 256), (120, 4, 256), (16, 64, 128), (12, 128, 64),
+                               (72, 5, 128)])
 def test_gamma_tile_widths_agree(n, prec):
     """The 3D projection pass with the narrow TMA tile (rve_set_gamma_tile):
     bit-identical to the default tile, ragged last column tiles included
-    (P1 = 66 and 36 are not multiples of the tile widths)."""
+    (P1 = 61 and 37 are not multiples of the tile widths)."""
     g = O.Grid(n)
     rng = np.random.default_rng(5)
     phase = (rng.random(g.shape) < 0.3).astype(np.uint8)
