@@ -106,8 +106,9 @@ typedef struct {
 /* Solver tolerances and budgets.  The paper prints no values (Algorithm 1,
  * Algorithm 2 use a symbolic TOL); rve_default_options fills the production
  * set (tol_stag = tol_newton = 1e-6, cg_rtol 1e-3 mixed / 1e-8 FP64,
- * pcg_rtol 1e-8).  In the mixed form each Newton correction is solved
- * inexactly in FP32 while the Newton residual is evaluated in FP64. */
+ * pcg_rtol 1e-7 mixed, the FP32 round-off level / 1e-8 FP64).  In the mixed
+ * form each Newton correction is solved inexactly in FP32 while the Newton
+ * residual is evaluated in FP64. */
 typedef struct {
   double tol_stag;     /* staggered ERR tolerance (Algorithm 1 (iii)) */
   double tol_newton;   /* Newton residual and correction tolerance */

@@ -40,22 +40,12 @@ static void set_smem(K kernel, size_t bytes) {
   // never lowered, so a concurrent caller with a smaller tile cannot shrink
   // it between another caller's check and launch.  Each launch still gets
   // only its own dynamic size.
-  //
-  // Every kernel launched through here stages its tiles in shared memory and
-  // reads global memory once: it asks, once, for the largest shared-memory
-  // carveout, so that the resident CTAs per SM are limited by its tile and
-  // registers rather than by an L1-leaning split.
+  if (bytes <= 48 * 1024) return;
   static std::mutex mu;
-  static std::unordered_set<const void*> done, carved;
+  static std::unordered_set<const void*> done;
   const void* key = reinterpret_cast<const void*>(kernel);
   std::lock_guard<std::mutex> lock(mu);
-  if (!carved.count(key)) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-      cudaGetLastError();
-    carved.insert(key);
-  }
-  if (bytes <= 48 * 1024 || done.count(key)) return;
+  if (done.count(key)) return;
   int dev = 0, optin = 0;
   cudaFuncAttributes fa{};
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -341,7 +331,7 @@ constexpr int kStencilWarps = 4;                   // warps per CTA (consecutive
 constexpr int kStencilOut = 30;                    // outputs per warp along x1
 template <typename R>
 struct StencilRows {
-  static constexpr int SYT = sizeof(R) == 4 ? 4 : 4;
+  static constexpr int SYT = 4;
 };
 
 template <typename R>
@@ -814,17 +804,11 @@ template <typename R, int NCOMP> struct RegRs {
 
 // TXR > 0: NAX-point axis (64, 128 or 256) through the register passes, TXR
 // columns per CTA.
-//
-// nyq > 0 (register passes, P1 = 1 + a multiple of TXR): the last column of
-// the half spectrum (q1 = N1/2) is not given a tile of its own per plane,
-// which would transform TXR columns for one; instead the CTAs of the last
-// x tile take that column from TXR consecutive planes (blockIdx.y groups
-// them; groups past the plane count exit), so that every transformed column
-// is a real one.
+
 template <typename R, int SIGN, int TXR = 0, int NAX = 256>
 __global__ void __launch_bounds__(kThreads, 2)
 k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
-                long long astride, long long ostride, const KrylovCtl* __restrict__ ctl, int nyq, int nplanes) {
+                long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   constexpr int E = StridedE<R>::E;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -832,30 +816,6 @@ k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restri
   if (TXR) tx = TXR;
   C2<R>* tws = reinterpret_cast<C2<R>*>(smraw);
   C2<R>* buf = reinterpret_cast<C2<R>*>(smraw + tw_bytes<R>(N));
-  if constexpr (TXR > 0) {
-    if (nyq && blockIdx.x == gridDim.x - 1) {
-      const int p0 = blockIdx.y * TXR;
-      if (p0 >= nplanes) return;
-      C2<R>* base = S + blockIdx.z * g.sstride + (g.P1 - 1);
-      for (int i = threadIdx.x; i < N; i += kThreads) tws[i] = tw[i];
-      // forward: natural rows in; inverse: the spectrum into the reg_pos order
-      for (int e = threadIdx.x; e < NAX * TXR; e += kThreads) {
-        const int n = e / TXR, c = e - n * TXR;
-        const int m = (SIGN > 0) ? reg_pos<NAX>(n) : n;
-        buf[m * TXR + c] = p0 + c < nplanes ? base[(long long)(p0 + c) * ostride + (long long)n * astride]
-                                            : mk<R>(0, 0);
-      }
-      __syncthreads();
-      if constexpr (SIGN < 0) fftreg_forward<R, NAX, TXR>(buf, tws);
-      else fftreg_inverse<R, NAX, TXR>(buf, tws);
-      for (int e = threadIdx.x; e < NAX * TXR; e += kThreads) {
-        const int n = e / TXR, c = e - n * TXR;
-        const int m = (SIGN < 0) ? reg_pos<NAX>(n) : n;
-        if (p0 + c < nplanes) base[(long long)(p0 + c) * ostride + (long long)n * astride] = buf[m * TXR + c];
-      }
-      return;
-    }
-  }
   const int q0 = blockIdx.x * tx;
   const int cols = min(tx, g.P1 - q0);
   C2<R>* base = S + blockIdx.z * g.sstride + blockIdx.y * ostride + q0;
@@ -2215,9 +2175,37 @@ void Ops<R>::helm_stencil(const Geo& g, const LaunchCfg& lc, cudaStream_t st, co
   const R c0 = (R)(1.0 / (16.0 * g.h[0] * g.h[0]));
   const R c1 = (R)(1.0 / (16.0 * g.h[1] * g.h[1]));
   const R c2 = g.d == 3 ? (R)(1.0 / (16.0 * g.h[2] * g.h[2])) : R(0);
-  const int zc = g.n3 < 16 ? g.n3 : 16;
   constexpr int rows = kStencilWarps * StencilRows<R>::SYT;
-  dim3 grid((g.n1 + kStencilOut - 1) / kStencilOut, (g.n2 + rows - 1) / rows, (g.n3 + zc - 1) / zc);
+  const int bx = (g.n1 + kStencilOut - 1) / kStencilOut, by = (g.n2 + rows - 1) / rows;
+  // planes per CTA: each CTA also reads the two halo planes, and the last
+  // wave of CTAs may leave SMs idle, so zc minimises (waves) x (zc + 2)
+  // over the resident CTAs of the whole GPU
+  static int slots = 0;
+  if (slots == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_helm_stencil<R>, 32 * kStencilWarps, 0) !=
+            cudaSuccess || per < 1) {
+      cudaGetLastError();
+      nsm = 1;
+      per = 1;
+    }
+    slots = nsm * per;
+  }
+  int zc = g.n3 < 16 ? g.n3 : 16;
+  if (g.n3 > 16) {
+    long long best = -1;
+    for (int z = 8; z <= 32 && z <= g.n3; z++) {
+      const long long ctas = (long long)bx * by * ((g.n3 + z - 1) / z);
+      const long long cost = ((ctas + slots - 1) / slots) * (z + 2);
+      if (best < 0 || cost < best) {
+        best = cost;
+        zc = z;
+      }
+    }
+  }
+  dim3 grid(bx, by, (g.n3 + zc - 1) / zc);
   k_helm_stencil<R><<<grid, 32 * kStencilWarps, 0, st>>>(g, q, y, phase, ell2_tab, c0, c1, c2, zc, ctl);
 }
 
@@ -2228,12 +2216,8 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
   const FftPlan& pl = axis == 1 ? t.plan_y : t.plan_z;
   const int tx = axis_tx<R>(lc, si.N, 1);
   const size_t sm = tw_bytes<R>(si.N) + (size_t)si.N * sizeof(C2<R>) * tx;
-  const int nplanes = axis == 1 ? g.n3 : g.n2;
-  dim3 grid((g.P1 + tx - 1) / tx, nplanes, ncomp);
+  dim3 grid((g.P1 + tx - 1) / tx, axis == 1 ? g.n3 : g.n2, ncomp);
   constexpr int TXR = RegTx<R, 1>::v;
-  // the q1 = N1/2 column packed TXR planes to a CTA (register passes only)
-  const int nyq = (reg_axis(si.N) && g.P1 > 1 && (g.P1 - 1) % TXR == 0) ? 1 : 0;
-  if (nyq) grid.x = (g.P1 - 1) / TXR + 1;
   auto pick = [&](auto k256, auto k128, auto k64, auto kgen) {
     return si.N == 256 ? k256 : si.N == 128 ? k128 : si.N == 64 ? k64 : kgen;
   };
@@ -2241,12 +2225,12 @@ void Ops<R>::strided_plain(const Geo& g, const Tables<R>& t, const LaunchCfg& lc
     auto k = pick(k_strided_plain<R, -1, TXR, 256>, k_strided_plain<R, -1, TXR, 128>,
                   k_strided_plain<R, -1, TXR, 64>, k_strided_plain<R, -1>);
     set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl, nyq, nplanes);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
   } else {
     auto k = pick(k_strided_plain<R, 1, TXR, 256>, k_strided_plain<R, 1, TXR, 128>,
                   k_strided_plain<R, 1, TXR, 64>, k_strided_plain<R, 1>);
     set_smem(k, sm);
-    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl, nyq, nplanes);
+    k<<<grid, kThreads, sm, st>>>(g, pl, t.tw[axis], S, tx, si.astride, si.ostride, ctl);
   }
 }
 
