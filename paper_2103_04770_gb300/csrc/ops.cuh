@@ -806,7 +806,7 @@ template <typename R, int NCOMP> struct RegRs {
 // columns per CTA.
 
 template <typename R, int SIGN, int TXR = 0, int NAX = 256>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, (TXR > 0 && sizeof(R) == 4) ? 4 : 2)
 k_strided_plain(Geo g, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ S, int tx,
                 long long astride, long long ostride, const KrylovCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
@@ -1097,7 +1097,7 @@ __device__ __forceinline__ R q1_weight(const Geo& g, int q1) {
 // component, D = 0: the operator is applied in real space) or W_j = k_j p
 // (D > 0); inverse transform along the last axis.
 template <typename R, int D, int TXR = 0, int NAX = 256>
-__global__ void __launch_bounds__(kThreads, D == 0 && TXR > 0 && sizeof(R) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, D == 0 && TXR > 0 && sizeof(R) == 4 ? 4 : 2)
 k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __restrict__ W,
          C2<R>* __restrict__ p, const C2<R>* __restrict__ r, int tx, long long astride,
          long long ostride, R ell2m, const KrylovCtl* __restrict__ ctl, int raw) {
@@ -1125,7 +1125,7 @@ k_expand(Geo g, Tables<R> t, FftPlan pl, const C2<R>* __restrict__ tw, C2<R>* __
     const int col = threadIdx.x % TXR, r0 = threadIdx.x / TXR;
     if (col < cols) {
       // two halves of the thread's entries, each with all its loads issued
-      // before it is used (registers for three CTAs per SM)
+      // before it is used (registers for four CTAs per SM)
       constexpr int HALF = PER / 2;
       const bool upd = !raw && !first;
       LastSym<R> sy;
