@@ -100,7 +100,7 @@ def test_fp64_curve_matches_oracle(N):
     assert z["D_max"][-1] > 0.1          # the stored curve reaches well into damage
 
 
-@pytest.mark.parametrize("N", [64])
+@pytest.mark.parametrize("N", [64, 128])
 def test_mixed_curve_matches_oracle(N):
     z, meta = _golden(N)
     n = len(z["S"])
