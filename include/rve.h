@@ -208,8 +208,8 @@ int rve_step_increment_adaptive(rve_t* h, int max_cuts, rve_step_info* info);
 int rve_homogenized_stress(const rve_t* h, double sigma[6]);
 int rve_homogenized_strain(const rve_t* h, double eps[6]);
 
-/* Copies a field of the last converged increment to dst (device pointer),
- * FP64, component-major.  which: 0 strain (Mandel, nc comps), 1 stress
+/* Copies a field of the last converged increment to dst (device or host
+ * memory; the call returns once the copy is done), FP64, component-major.  which: 0 strain (Mandel, nc comps), 1 stress
  * (Mandel, 6 comps), 2 damage D (1), 3 non-local abar (J comps), 4 eps_p (1),
  * 5 plastic strain (Mandel, 6 comps), 6 porosity f (1; 0 outside GTN
  * phases).  For GTN phases field 2 holds f* and field 4 eps_0^p. */

@@ -292,7 +292,15 @@ def rve_get_sizes(h):
 
 
 def rve_get_field(h, which, dst):
-    _check(lib().rve_get_field(h, int(which), _ptr(dst), dst.numel()), "rve_get_field")
+    """dst: a CUDA float64 tensor, or a host float64 buffer (numpy array or
+    CPU tensor)."""
+    if hasattr(dst, "data_ptr") and dst.is_cuda:
+        _check(lib().rve_get_field(h, int(which), _ptr(dst), dst.numel()), "rve_get_field")
+        return dst
+    if str(getattr(dst, "dtype", "")) not in ("float64", "torch.float64"):
+        raise ValueError("rve_get_field writes float64")
+    addr, nbytes = _host_buffer(dst)
+    _check(lib().rve_get_field(h, int(which), ctypes.c_void_p(addr), nbytes // 8), "rve_get_field")
     return dst
 
 

@@ -1494,7 +1494,8 @@ int rve_get_field(const rve_t* h, int which, double* dst, size_t n) {
   }
   if (n < cnt) return RVE_ERR_ARG;
   if (cnt == 0) return RVE_OK;
-  CK(cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  // dst may be device or host memory (the copy kind follows the address)
+  CK(cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyDefault, h->st));
   CK(cudaStreamSynchronize(h->st));
   return RVE_OK;
 }

@@ -437,6 +437,29 @@ def _run_pair(cfg, prec, fields=False):
     return (recs, infos, fl) if fields else (recs, infos)
 
 
+def test_get_field_to_host_and_device_memory():
+    """rve_get_field copies into device or host memory alike (numpy array,
+    pageable and pinned CPU tensors), and rejects a buffer too small."""
+    cfg = I.config_2d_disc(16, ell_vox=2.0, n_incr=2, dE=1e-3)
+    V = 16 * 16
+    with pkg.RVE(cfg, precision=0) as r:
+        r.step()
+        r.step()
+        for which, n in ((0, 3 * V), (1, 6 * V), (2, V), (3, V), (4, V), (5, 6 * V), (6, V)):
+            d = torch.empty(n, device="cuda", dtype=torch.float64)
+            pkg.rve_get_field(r.h, which, d)
+            want = host(d)
+            a = np.full(n, np.nan)
+            pkg.rve_get_field(r.h, which, a)
+            assert np.array_equal(a, want), which
+            for pin in (False, True):
+                t = torch.full((n,), float("nan"), dtype=torch.float64, pin_memory=pin)
+                pkg.rve_get_field(r.h, which, t)
+                assert np.array_equal(t.numpy(), want), (which, pin)
+        with pytest.raises(pkg.RVEError):
+            pkg.rve_get_field(r.h, 1, np.zeros(6 * V - 1))
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("case", list(CASES))
 def test_increments_match_oracle(case, prec):
