@@ -55,10 +55,10 @@ typedef enum {
   RVE_ERR_NOT_CONVERGED = -5,  /* an iteration budget ran out; the state is
                                   left at the last converged increment */
   RVE_ERR_NUMERIC = -6,        /* NaN/Inf or Krylov breakdown */
-  RVE_ERR_LOAD_PATH_END = -7,  /* every increment of the load path is done */
-  RVE_ERR_TIMEOUT = -8         /* a device-side wait for a tile copy ran out
+  RVE_ERR_TIMEOUT = -7,        /* a device-side wait for a tile copy ran out
                                   of its budget (a hardware or driver fault);
                                   the handle should be freed */
+  RVE_ERR_LOAD_PATH_END = -8   /* every increment of the load path is done */
 } rve_status;
 
 /* Per-phase constitutive parameters (Section 2.1.2; Section 4 for the damage

@@ -23,8 +23,8 @@ RVE_ERR_CUDA = -3
 RVE_ERR_OOM = -4
 RVE_ERR_NOT_CONVERGED = -5
 RVE_ERR_NUMERIC = -6
-RVE_ERR_LOAD_PATH_END = -7
-RVE_ERR_TIMEOUT = -8
+RVE_ERR_TIMEOUT = -7
+RVE_ERR_LOAD_PATH_END = -8
 RVE_FP64 = 0
 RVE_MIXED = 1
 

@@ -78,6 +78,12 @@ def test_argument_errors_without_device(pkg):
     assert lib.rve_step_increment(None, None) == pkg.RVE_ERR_ARG
     assert lib.rve_step_increment_adaptive(None, 7, None) == pkg.RVE_ERR_ARG
     assert pkg.rve_status_string(pkg.RVE_ERR_TIMEOUT) == "device wait for a tile copy timed out"
+    assert pkg.rve_status_string(pkg.RVE_ERR_LOAD_PATH_END) == "load path finished"
+    # the binding's constants are the header's
+    h_text = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                               "rve.h")).read()
+    for name, val in re.findall(r"\b(RVE_(?:OK|ERR_\w+))\s*=\s*(-?\d+)", h_text):
+        assert getattr(pkg, name) == int(val), name
     lib.rve_free(None)
 
 
